@@ -1,0 +1,583 @@
+/*
+ * FP64 CPU oracle for the particles-on-demand (PonD) double-distribution BGK step
+ * of Hosseini, Bhadauria & Karlin, "Probing double distribution function models in
+ * the lattice Boltzmann method for highly compressible flows" (arXiv 2405.11489).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this code; only the
+ * tests, the smoke check and the CPU-baseline leg of the benchmark use it.  It shares
+ * no code, header, table or constant with the CUDA library: the lattice, the Hermite
+ * tensors and every formula are written out here again, in the paper's order.
+ *
+ * It is deliberately plain and slow: populations f_i, g_i are stored as they are
+ * (Q values per node, each node in its own frame lambda = (u, T)), and streaming
+ * applies the frame transformation to every stencil node separately before the
+ * Lagrange interpolation, exactly as Eq. (propagationInterpolated) is written.
+ * The only economy is a memo of the Grad coefficients of a source node in the current
+ * target frame, which is the same computation repeated for every population i.
+ *
+ * Units: lattice units, r = 1, delta_x = delta_t = 1, T_L = 1 (Sec. III, Table I).
+ * Build: gcc -O2 -ffp-contract=off (no fused multiply-add, so results are fixed by
+ * the source order), optionally -fopenmp (the node loop is embarrassingly parallel
+ * and each node's arithmetic is independent of the thread count).
+ *
+ * Readings taken where the paper is silent (each is listed with its reason in the
+ * design notes of the repository):
+ *   - discrete BGK: f* = f + omega (f_eq - f), omega = 1/(tau + 1/2), tau = mu/p;
+ *   - Grad expansion order N = 3 (all coefficients of total order <= 3);
+ *   - W(x - x_s) is evaluated at the departure point x - C_i(lambda_bar) dt;
+ *   - cubic (4-point) Lagrange interpolation by default, 3-point as an option;
+ *   - predictor-corrector: guess = previous frame of the node, metric
+ *     max(|du|/sqrt(T_bar), |dT|/T_bar), stop at tolerance or iteration cap, or after
+ *     exactly K iterations in fixed mode;
+ *   - collision in the frame of the final moments, after projecting into it;
+ *   - internal-energy split source: f -> f_eq inside the source, backward time
+ *     difference of u against the frame before the step, central space differences.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXQ1 5
+#define OR_MAXQ (OR_MAXQ1 * OR_MAXQ1)
+
+typedef struct {
+    int32_t nx, ny;
+    int32_t q1;            /* 4 -> D2Q16, 5 -> D2Q25 (Table I) */
+    int32_t split;         /* 0 total-energy split, 1 internal-energy split (Eq. Es) */
+    int32_t interp_order;  /* 3 -> 4-point cubic Lagrange, 2 -> 3-point quadratic */
+    int32_t bc_x, bc_y;    /* 0 periodic, 1 outflow (index clamp, zero gradient) */
+    double gamma, mu;      /* adiabatic exponent (Eq. spec_heat), dynamic viscosity (Eq. kin_visc) */
+    double pc_tol;
+    int32_t pc_max_iter;
+    int32_t pc_fixed_iters; /* > 0: exactly this many predictor-corrector iterations */
+} or_config;
+
+/* ---------------------------------------------------------------------------------- */
+/* Table I: one-dimensional Gauss-Hermite quadratures with r T_L = 1.                  */
+/* ---------------------------------------------------------------------------------- */
+int or_lattice_1d(int q1, double *c, double *w)
+{
+    if (q1 == 4) {
+        /* D1Q4: c = {+-sqrt(3 - sqrt 6), +-sqrt(3 + sqrt 6)}, w = {(3 + sqrt 6)/12, (3 - sqrt 6)/12} */
+        double cin = sqrt(3.0 - sqrt(6.0)), cout = sqrt(3.0 + sqrt(6.0));
+        double win = (3.0 + sqrt(6.0)) / 12.0, wout = (3.0 - sqrt(6.0)) / 12.0;
+        c[0] = -cout; c[1] = -cin; c[2] = cin; c[3] = cout;
+        w[0] = wout;  w[1] = win;  w[2] = win; w[3] = wout;
+        return 4;
+    }
+    if (q1 == 5) {
+        /* D1Q5: c = {0, +-sqrt(5 - sqrt 10), +-sqrt(5 + sqrt 10)},
+         *       w = {8/15, (7 + 2 sqrt 10)/60, (7 - 2 sqrt 10)/60} (larger weight on the inner node) */
+        double cin = sqrt(5.0 - sqrt(10.0)), cout = sqrt(5.0 + sqrt(10.0));
+        double w0 = 8.0 / 15.0, win = (7.0 + 2.0 * sqrt(10.0)) / 60.0, wout = (7.0 - 2.0 * sqrt(10.0)) / 60.0;
+        c[0] = -cout; c[1] = -cin; c[2] = 0.0; c[3] = cin; c[4] = cout;
+        w[0] = wout;  w[1] = win;  w[2] = w0;  w[3] = win; w[4] = wout;
+        return 5;
+    }
+    return 0;
+}
+
+/* Tensor-product 2-D lattice: population i = b*q1 + a has c_i = (c_a, c_b), w_i = w_a w_b. */
+typedef struct {
+    int q1, Q;
+    double cx[OR_MAXQ], cy[OR_MAXQ], w[OR_MAXQ];
+} or_lattice;
+
+static void make_lattice(int q1, or_lattice *L)
+{
+    double c[OR_MAXQ1], w[OR_MAXQ1];
+    or_lattice_1d(q1, c, w);
+    L->q1 = q1;
+    L->Q = q1 * q1;
+    for (int b = 0; b < q1; ++b)
+        for (int a = 0; a < q1; ++a) {
+            int i = b * q1 + a;
+            L->cx[i] = c[a];
+            L->cy[i] = c[b];
+            L->w[i] = w[a] * w[b];
+        }
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Hermite tensors H^(n)(xi), n <= 3, in D = 2 (probabilists' normalisation, r T_L = 1) */
+/* ---------------------------------------------------------------------------------- */
+typedef struct {
+    double h0, h1[2], h2[2][2], h3[2][2][2];
+} or_tensors;
+
+static double kron(int a, int b) { return a == b ? 1.0 : 0.0; }
+
+static void hermite_tensors(double xi_x, double xi_y, or_tensors *H)
+{
+    double xi[2] = {xi_x, xi_y};
+    H->h0 = 1.0;
+    for (int a = 0; a < 2; ++a) H->h1[a] = xi[a];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) H->h2[a][b] = xi[a] * xi[b] - kron(a, b);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int g = 0; g < 2; ++g)
+                H->h3[a][b][g] = xi[a] * xi[b] * xi[g]
+                               - xi[a] * kron(b, g) - xi[b] * kron(a, g) - xi[g] * kron(a, b);
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Frame transformation M_{lambda}^{lambda_bar}, Eq. (gradGeneralTransform), N = 3.    */
+/* a_n = sum_j f_j H^(n)((C_j(lambda) - u_bar)/sqrt(T_bar)); the populations of the    */
+/* target frame are f_i = w_i sum_n a_n : H^(n)(c_i) / n!.                             */
+/* ---------------------------------------------------------------------------------- */
+typedef struct { double ux, uy, T; } or_frame;
+
+static void grad_coefficients(const or_lattice *L, const double *pops, int stride,
+                              or_frame src, or_frame dst, or_tensors *A)
+{
+    memset(A, 0, sizeof(*A));
+    double sTs = sqrt(src.T), sTd = sqrt(dst.T);
+    for (int j = 0; j < L->Q; ++j) {
+        double Cx = sTs * L->cx[j] + src.ux;       /* C_j(lambda) = sqrt(T) c_j + u */
+        double Cy = sTs * L->cy[j] + src.uy;
+        double xix = (Cx - dst.ux) / sTd;
+        double xiy = (Cy - dst.uy) / sTd;
+        or_tensors H;
+        hermite_tensors(xix, xiy, &H);
+        double fj = pops[(size_t)j * stride];
+        A->h0 += fj * H.h0;
+        for (int a = 0; a < 2; ++a) A->h1[a] += fj * H.h1[a];
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) A->h2[a][b] += fj * H.h2[a][b];
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int g = 0; g < 2; ++g) A->h3[a][b][g] += fj * H.h3[a][b][g];
+    }
+}
+
+/* Full Frobenius contraction of every rank (no symmetry shortcut), divided by n!. */
+static double grad_population(const or_lattice *L, const or_tensors *A, int i)
+{
+    or_tensors H;
+    hermite_tensors(L->cx[i], L->cy[i], &H);
+    double s0 = A->h0 * H.h0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int a = 0; a < 2; ++a) s1 += A->h1[a] * H.h1[a];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) s2 += A->h2[a][b] * H.h2[a][b];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int g = 0; g < 2; ++g) s3 += A->h3[a][b][g] * H.h3[a][b][g];
+    return L->w[i] * (s0 + s1 + s2 / 2.0 + s3 / 6.0);
+}
+
+/* Exported for the tests: transform Q populations from frame src to frame dst. */
+void or_grad_transform(int q1, const double *pops_src, double sux, double suy, double sT,
+                       double dux, double duy, double dT, double *pops_dst)
+{
+    or_lattice L;
+    make_lattice(q1, &L);
+    or_frame s = {sux, suy, sT}, d = {dux, duy, dT};
+    or_tensors A;
+    grad_coefficients(&L, pops_src, 1, s, d, &A);
+    for (int i = 0; i < L.Q; ++i) pops_dst[i] = grad_population(&L, &A, i);
+}
+
+/* Exported for the tests: the Grad coefficient tensors in frame dst, flattened as
+ * a0, a1[x,y], a2[xx,xy,yx,yy], a3[xxx,xxy,xyx,xyy,yxx,yxy,yyx,yyy] (15 values). */
+void or_grad_coefficients(int q1, const double *pops_src, double sux, double suy, double sT,
+                          double dux, double duy, double dT, double *out15)
+{
+    or_lattice L;
+    make_lattice(q1, &L);
+    or_frame s = {sux, suy, sT}, d = {dux, duy, dT};
+    or_tensors A;
+    grad_coefficients(&L, pops_src, 1, s, d, &A);
+    int k = 0;
+    out15[k++] = A.h0;
+    for (int a = 0; a < 2; ++a) out15[k++] = A.h1[a];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) out15[k++] = A.h2[a][b];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int g = 0; g < 2; ++g) out15[k++] = A.h3[a][b][g];
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Equilibria in the local frame (Sec. III.A, Eqs. f_eq and the g_eq of each split).   */
+/* ---------------------------------------------------------------------------------- */
+static double cv_of(double gamma) { return 1.0 / (gamma - 1.0); }   /* Eq. spec_heat, r = 1 */
+
+/* f_eq_i = rho w_i in the frame lambda = (u, T) (Sec. III.A). */
+static double feq_pop(const or_lattice *L, int i, double rho) { return rho * L->w[i]; }
+
+/* g_eq_i = (U'/rho + |v|^2/2) f_eq (total split) or (U'/rho + |v - u|^2/2) f_eq (internal
+ * split) at v = C_i(lambda); U' = U - rho D T / 2 = rho (c_v - 1) T for D = 2. */
+static double geq_pop(const or_lattice *L, int i, int split, double rho, or_frame fr, double cv)
+{
+    double sT = sqrt(fr.T);
+    double Cx = sT * L->cx[i] + fr.ux, Cy = sT * L->cy[i] + fr.uy;
+    double Uprime_over_rho = (cv - 1.0) * fr.T;
+    double kin;
+    if (split == 0)
+        kin = 0.5 * (Cx * Cx + Cy * Cy);
+    else
+        kin = 0.5 * ((Cx - fr.ux) * (Cx - fr.ux) + (Cy - fr.uy) * (Cy - fr.uy));
+    return (Uprime_over_rho + kin) * feq_pop(L, i, rho);
+}
+
+/* Exported: equilibrium populations for fields rho, u, T (the state set by set_state). */
+int or_init(const or_config *cfg, const double *rho, const double *ux, const double *uy,
+            const double *T, double *f, double *g, double *fux, double *fuy, double *fT)
+{
+    or_lattice L;
+    make_lattice(cfg->q1, &L);
+    double cv = cv_of(cfg->gamma);
+    size_t N = (size_t)cfg->nx * cfg->ny;
+    for (size_t n = 0; n < N; ++n) {
+        or_frame fr = {ux[n], uy[n], T[n]};
+        for (int i = 0; i < L.Q; ++i) {
+            f[(size_t)i * N + n] = feq_pop(&L, i, rho[n]);
+            g[(size_t)i * N + n] = geq_pop(&L, i, cfg->split, rho[n], fr, cv);
+        }
+        fux[n] = ux[n];
+        fuy[n] = uy[n];
+        fT[n] = T[n];
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Moments (Sec. II): rho = sum f, rho u = sum C f; total split E = sum g; internal    */
+/* split U = sum g, E = U + rho u^2/2.  T from E = rho c_v T + rho u^2 / 2.            */
+/* ---------------------------------------------------------------------------------- */
+typedef struct { double rho, ux, uy, T, E; } or_moments;
+
+static or_moments moments_of(const or_lattice *L, const double *f, const double *g, int stride,
+                             or_frame fr, int split, double cv)
+{
+    double sT = sqrt(fr.T);
+    double rho = 0.0, jx = 0.0, jy = 0.0, G = 0.0;
+    for (int i = 0; i < L->Q; ++i) {
+        double fi = f[(size_t)i * stride], gi = g[(size_t)i * stride];
+        double Cx = sT * L->cx[i] + fr.ux, Cy = sT * L->cy[i] + fr.uy;
+        rho += fi;
+        jx += Cx * fi;
+        jy += Cy * fi;
+        G += gi;
+    }
+    or_moments m;
+    m.rho = rho;
+    m.ux = jx / rho;
+    m.uy = jy / rho;
+    double u2 = m.ux * m.ux + m.uy * m.uy;
+    if (split == 0) {
+        m.E = G;
+        m.T = (G / rho - 0.5 * u2) / cv;
+    } else {
+        m.E = G + 0.5 * rho * u2;
+        m.T = G / (rho * cv);
+    }
+    return m;
+}
+
+/* Exported: rho, u, T of every node from its populations in its own frame. */
+int or_moments_field(const or_config *cfg, const double *f, const double *g, const double *fux,
+                     const double *fuy, const double *fT, double *rho, double *ux, double *uy,
+                     double *T, double *E)
+{
+    or_lattice L;
+    make_lattice(cfg->q1, &L);
+    double cv = cv_of(cfg->gamma);
+    size_t N = (size_t)cfg->nx * cfg->ny;
+    for (size_t n = 0; n < N; ++n) {
+        or_frame fr = {fux[n], fuy[n], fT[n]};
+        or_moments m = moments_of(&L, f + n, g + n, (int)N, fr, cfg->split, cv);
+        rho[n] = m.rho;
+        ux[n] = m.ux;
+        uy[n] = m.uy;
+        T[n] = m.T;
+        if (E) E[n] = m.E;
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Boundaries and Lagrange interpolation kernels                                       */
+/* ---------------------------------------------------------------------------------- */
+static int bc_map(int j, int n, int bc)
+{
+    if (bc == 0) {              /* periodic */
+        int r = j % n;
+        return r < 0 ? r + n : r;
+    }
+    if (j < 0) return 0;        /* outflow: zero-gradient copy of the edge node */
+    if (j > n - 1) return n - 1;
+    return j;
+}
+
+/* Lagrange weights of a p-point stencil around the departure coordinate xd; returns the
+ * first stencil node.  Cubic: nodes floor(xd)-1 .. floor(xd)+2.  Quadratic: nodes
+ * m-1 .. m+1 with m = floor(xd + 1/2). */
+static int lagrange_stencil(double xd, int order, double *wts)
+{
+    if (order == 3) {
+        double fl = floor(xd);
+        double t = xd - fl;                      /* position relative to node floor(xd), in [0,1) */
+        /* nodes at -1, 0, 1, 2 */
+        wts[0] = -t * (t - 1.0) * (t - 2.0) / 6.0;
+        wts[1] = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
+        wts[2] = -(t + 1.0) * t * (t - 2.0) / 2.0;
+        wts[3] = (t + 1.0) * t * (t - 1.0) / 6.0;
+        return (int)fl - 1;
+    } else {
+        double m = floor(xd + 0.5);
+        double t = xd - m;                       /* in [-1/2, 1/2) */
+        /* nodes at -1, 0, 1 */
+        wts[0] = t * (t - 1.0) / 2.0;
+        wts[1] = (1.0 - t) * (1.0 + t);
+        wts[2] = t * (t + 1.0) / 2.0;
+        return (int)m - 1;
+    }
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Semi-Lagrangian streaming at one node in a given target frame,                      */
+/* Eq. (propagationInterpolated): {f_i, g_i}(x) = sum_s W(x - C_i dt - x_s) M{f,g}(x_s) */
+/* ---------------------------------------------------------------------------------- */
+#define OR_MEMO 1024
+typedef struct {
+    int64_t key[OR_MEMO];
+    or_tensors Af[OR_MEMO], Ag[OR_MEMO];
+} or_memo;
+
+typedef struct {
+    const or_config *cfg;
+    const or_lattice *L;
+    const double *f, *g, *fux, *fuy, *fT;   /* post-collision state of the previous step */
+} or_src;
+
+static void memo_clear(or_memo *M)
+{
+    for (int k = 0; k < OR_MEMO; ++k) M->key[k] = -1;
+}
+
+/* Grad coefficients of source node (sx, sy) in the target frame, memoised per target frame. */
+static void source_coefficients(const or_src *S, or_memo *M, int sx, int sy, or_frame dst,
+                                const or_tensors **Af, const or_tensors **Ag)
+{
+    int nx = S->cfg->nx;
+    size_t N = (size_t)nx * S->cfg->ny;
+    int64_t node = (int64_t)sy * nx + sx;
+    int slot = (int)(((sx & 1023) + 37 * (sy & 1023)) & (OR_MEMO - 1));
+    if (M->key[slot] != node) {
+        or_frame src = {S->fux[node], S->fuy[node], S->fT[node]};
+        grad_coefficients(S->L, S->f + node, (int)N, src, dst, &M->Af[slot]);
+        grad_coefficients(S->L, S->g + node, (int)N, src, dst, &M->Ag[slot]);
+        M->key[slot] = node;
+    }
+    *Af = &M->Af[slot];
+    *Ag = &M->Ag[slot];
+}
+
+static void stream_node(const or_src *S, or_memo *M, int x, int y, or_frame bar, double *P, double *G)
+{
+    const or_config *cfg = S->cfg;
+    const or_lattice *L = S->L;
+    int p = cfg->interp_order == 3 ? 4 : 3;
+    double sT = sqrt(bar.T);
+    memo_clear(M);
+    for (int i = 0; i < L->Q; ++i) {
+        double Cx = sT * L->cx[i] + bar.ux, Cy = sT * L->cy[i] + bar.uy;
+        double xd = (double)x - Cx * 1.0, yd = (double)y - Cy * 1.0;   /* delta_t = 1 */
+        double wx[4], wy[4];
+        int bx = lagrange_stencil(xd, cfg->interp_order, wx);
+        int by = lagrange_stencil(yd, cfg->interp_order, wy);
+        double fi = 0.0, gi = 0.0;
+        for (int ky = 0; ky < p; ++ky) {
+            int sy = bc_map(by + ky, cfg->ny, cfg->bc_y);
+            for (int kx = 0; kx < p; ++kx) {
+                int sx = bc_map(bx + kx, cfg->nx, cfg->bc_x);
+                const or_tensors *Af, *Ag;
+                source_coefficients(S, M, sx, sy, bar, &Af, &Ag);
+                double W = wx[kx] * wy[ky];
+                fi += W * grad_population(L, Af, i);
+                gi += W * grad_population(L, Ag, i);
+            }
+        }
+        P[i] = fi;
+        G[i] = gi;
+    }
+}
+
+/* Exported for the tests: stream at node (x, y) in a prescribed frame. */
+int or_stream_node(const or_config *cfg, const double *f, const double *g, const double *fux,
+                   const double *fuy, const double *fT, int x, int y, double ux, double uy,
+                   double T, double *P, double *G)
+{
+    or_lattice L;
+    make_lattice(cfg->q1, &L);
+    or_src S = {cfg, &L, f, g, fux, fuy, fT};
+    or_memo *M = (or_memo *)malloc(sizeof(or_memo));
+    if (!M) return -2;
+    or_frame bar = {ux, uy, T};
+    stream_node(&S, M, x, y, bar, P, G);
+    free(M);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* BGK collision in the frame of the final moments (Eq. boltz_eq discretised).         */
+/* ---------------------------------------------------------------------------------- */
+static void collide_node(const or_lattice *L, const or_config *cfg, const double *P, const double *G,
+                         or_frame bar, or_moments m, double *fo, double *go)
+{
+    double cv = cv_of(cfg->gamma);
+    or_frame star = {m.ux, m.uy, m.T};
+    or_tensors Af, Ag;
+    grad_coefficients(L, P, 1, bar, star, &Af);   /* project the streamed populations into lambda* */
+    grad_coefficients(L, G, 1, bar, star, &Ag);
+    double rho = m.rho;
+    double tau = cfg->mu / (rho * m.T);             /* Eq. kin_visc: tau = mu / p, p = rho T */
+    double omega = 1.0 / (tau + 0.5);
+    for (int i = 0; i < L->Q; ++i) {
+        double fp = grad_population(L, &Af, i);
+        double gp = grad_population(L, &Ag, i);
+        double fe = feq_pop(L, i, rho);
+        double ge = geq_pop(L, i, cfg->split, rho, star, cv);
+        fo[i] = fp + omega * (fe - fp);
+        go[i] = gp + omega * (ge - gp);
+    }
+}
+
+static int nonphysical(or_moments m)
+{
+    return !(m.rho > 0.0) || !(m.T > 0.0) || isnan(m.ux) || isnan(m.uy) || isnan(m.E);
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Internal-energy split source (Eq. int_g_evolution, Appendix A G term):              */
+/*   G_i = -rho w_i (C_i - u) . (d_t u + C_i . grad u), added to g after collision.    */
+/* ---------------------------------------------------------------------------------- */
+static void internal_source(const or_config *cfg, const or_lattice *L, double *g, const double *ux1,
+                            const double *uy1, const double *T1, const double *rho1,
+                            const double *ux0, const double *uy0)
+{
+    int nx = cfg->nx, ny = cfg->ny;
+    size_t N = (size_t)nx * ny;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t n = (size_t)y * nx + x;
+            size_t xp = (size_t)y * nx + bc_map(x + 1, nx, cfg->bc_x);
+            size_t xm = (size_t)y * nx + bc_map(x - 1, nx, cfg->bc_x);
+            size_t yp = (size_t)bc_map(y + 1, ny, cfg->bc_y) * nx + x;
+            size_t ym = (size_t)bc_map(y - 1, ny, cfg->bc_y) * nx + x;
+            double dxux = 0.5 * (ux1[xp] - ux1[xm]), dyux = 0.5 * (ux1[yp] - ux1[ym]);
+            double dxuy = 0.5 * (uy1[xp] - uy1[xm]), dyuy = 0.5 * (uy1[yp] - uy1[ym]);
+            double dtux = ux1[n] - ux0[n], dtuy = uy1[n] - uy0[n];   /* delta_t = 1 */
+            double sT = sqrt(T1[n]);
+            for (int i = 0; i < L->Q; ++i) {
+                double Cx = sT * L->cx[i] + ux1[n], Cy = sT * L->cy[i] + uy1[n];
+                double ax = dtux + Cx * dxux + Cy * dyux;     /* d_t u_x + C . grad u_x */
+                double ay = dtuy + Cx * dxuy + Cy * dyuy;
+                double Gi = -rho1[n] * L->w[i] * ((Cx - ux1[n]) * ax + (Cy - uy1[n]) * ay);
+                g[(size_t)i * N + n] += Gi * 1.0;              /* delta_t = 1 */
+            }
+        }
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* One time step.  Input state (f, g, frames) at time n, output state at n + 1.        */
+/* iters (optional, per node): predictor-corrector iterations used.                    */
+/* Returns: 0, or -4 if a non-physical state was met, or -5 if some node did not       */
+/* converge within pc_max_iter (state still advanced).  first_bad receives the first   */
+/* non-physical node (or -1).                                                          */
+/* ---------------------------------------------------------------------------------- */
+int or_step(const or_config *cfg, const double *f, const double *g, const double *fux,
+            const double *fuy, const double *fT, double *fo, double *go, double *oux,
+            double *ouy, double *oT, int32_t *iters, int64_t *first_bad)
+{
+    or_lattice L;
+    make_lattice(cfg->q1, &L);
+    double cv = cv_of(cfg->gamma);
+    int nx = cfg->nx, ny = cfg->ny;
+    size_t N = (size_t)nx * ny;
+    or_src S = {cfg, &L, f, g, fux, fuy, fT};
+    int64_t nonconv = 0, bad = -1;
+    double *rho1 = (double *)malloc(N * sizeof(double));
+    if (!rho1) return -2;
+
+#pragma omp parallel reduction(+ : nonconv)
+    {
+        or_memo *M = (or_memo *)malloc(sizeof(or_memo));
+        double P[OR_MAXQ], G[OR_MAXQ], fo_n[OR_MAXQ], go_n[OR_MAXQ];
+#pragma omp for schedule(static)
+        for (int64_t n = 0; n < (int64_t)N; ++n) {
+            int x = (int)(n % nx), y = (int)(n / nx);
+            or_frame bar = {fux[n], fuy[n], fT[n]};        /* predictor: previous frame */
+            or_moments m;
+            int k = 0, stop = 0, badnode = 0;
+            while (!stop) {
+                stream_node(&S, M, x, y, bar, P, G);
+                m = moments_of(&L, P, G, 1, bar, cfg->split, cv);
+                ++k;
+                if (nonphysical(m)) { badnode = 1; break; }
+                double du = sqrt((m.ux - bar.ux) * (m.ux - bar.ux) + (m.uy - bar.uy) * (m.uy - bar.uy));
+                double change = fmax(du / sqrt(bar.T), fabs(m.T - bar.T) / bar.T);
+                if (cfg->pc_fixed_iters > 0) {
+                    stop = (k >= cfg->pc_fixed_iters);
+                } else if (change <= cfg->pc_tol) {
+                    stop = 1;
+                } else if (k >= cfg->pc_max_iter) {
+                    stop = 1;
+                    nonconv += 1;
+                }
+                if (!stop) {                               /* corrector: frame of the moments */
+                    bar.ux = m.ux;
+                    bar.uy = m.uy;
+                    bar.T = m.T;
+                }
+            }
+            if (iters) iters[n] = k;
+            if (badnode) {
+#pragma omp critical
+                { if (bad < 0 || n < bad) bad = n; }
+                for (int i = 0; i < L.Q; ++i) { fo[(size_t)i * N + n] = NAN; go[(size_t)i * N + n] = NAN; }
+                oux[n] = m.ux; ouy[n] = m.uy; oT[n] = m.T; rho1[n] = m.rho;
+                continue;
+            }
+            collide_node(&L, cfg, P, G, bar, m, fo_n, go_n);
+            for (int i = 0; i < L.Q; ++i) {
+                fo[(size_t)i * N + n] = fo_n[i];
+                go[(size_t)i * N + n] = go_n[i];
+            }
+            oux[n] = m.ux;
+            ouy[n] = m.uy;
+            oT[n] = m.T;
+            rho1[n] = m.rho;
+        }
+        free(M);
+    }
+    if (cfg->split == 1 && bad < 0)
+        internal_source(cfg, &L, go, oux, ouy, oT, rho1, fux, fuy);
+    free(rho1);
+    if (first_bad) *first_bad = bad;
+    if (bad >= 0) return -4;
+    if (nonconv > 0) return -5;
+    return 0;
+}
+
+/* Exported for the tests: predictor-corrector-free collision of streamed populations P, G
+ * living on the lattice of frame (bux, buy, bT): moments, projection into their frame,
+ * BGK relaxation.  Writes the post-collision populations and their frame (ux, uy, T). */
+int or_collide_node(const or_config *cfg, const double *P, const double *G, double bux,
+                    double buy, double bT, double *fo, double *go, double *frame_out)
+{
+    or_lattice L;
+    make_lattice(cfg->q1, &L);
+    or_frame bar = {bux, buy, bT};
+    or_moments m = moments_of(&L, P, G, 1, bar, cfg->split, cv_of(cfg->gamma));
+    if (nonphysical(m)) return -4;
+    collide_node(&L, cfg, P, G, bar, m, fo, go);
+    frame_out[0] = m.ux;
+    frame_out[1] = m.uy;
+    frame_out[2] = m.T;
+    return 0;
+}

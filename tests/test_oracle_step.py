@@ -1,0 +1,170 @@
+"""Pins of the oracle's streaming, predictor-corrector and collision (Sec. III.A.2,
+Eq. propagationInterpolated; BGK of Eq. boltz_eq with tau = mu/p, Eq. kin_visc)."""
+import math
+
+import numpy as np
+import pytest
+
+
+def _perturbed_state(orc, cfg, rng, amp=0.05, uniform_frame=False):
+    ny, nx = cfg.ny, cfg.nx
+    rho = 1.0 + amp * rng.standard_normal((ny, nx))
+    if uniform_frame:
+        ux = np.full((ny, nx), 0.4)
+        uy = np.full((ny, nx), -0.25)
+        T = np.full((ny, nx), 0.8)
+    else:
+        ux = 0.4 + amp * rng.standard_normal((ny, nx))
+        uy = -0.25 + amp * rng.standard_normal((ny, nx))
+        T = 0.8 * (1.0 + amp * rng.standard_normal((ny, nx)))
+    st = orc.init_state(cfg, rho, ux, uy, T)
+    # add a non-equilibrium part inside the Grad span (third-order Hermite content)
+    Q = cfg.q1 * cfg.q1
+    st.f = st.f * (1.0 + amp * 0.2 * rng.standard_normal((Q, ny, nx)))
+    st.g = st.g * (1.0 + amp * 0.2 * rng.standard_normal((Q, ny, nx)))
+    return st
+
+
+def _totals(orc, cfg, st):
+    rho, ux, uy, T, E = orc.moments(cfg, st)
+    return np.array([rho.sum(), (rho * ux).sum(), (rho * uy).sum(), E.sum()])
+
+
+@pytest.mark.parametrize("lattice", [16, 25])
+@pytest.mark.parametrize("split", ["total", "internal"])
+def test_uniform_supersonic_flow_stays_uniform(orc, lattice, split):
+    """A uniform state at Ma = 3 is a fixed point of the whole step, converging in one
+    predictor-corrector iteration (the benchmark spec pin; Sec. III.A)."""
+    gamma, T = 1.4, 0.6
+    u = 3.0 * math.sqrt(gamma * T)
+    cfg = orc.make_config(7, 5, lattice=lattice, split=split, gamma=gamma, mu=0.01)
+    st = orc.init_state(cfg, 1.3, u * math.cos(0.3), u * math.sin(0.3), T)
+    st0 = st.copy()
+    for _ in range(3):
+        r = orc.step(cfg, st)
+        assert r.status == 0
+        assert np.all(r.iters == 1)
+        st = r.state
+    assert np.allclose(st.f, st0.f, rtol=1e-13, atol=0)
+    assert np.allclose(st.g, st0.g, rtol=1e-13, atol=0)
+    assert np.allclose(st.ux, st0.ux, rtol=1e-13) and np.allclose(st.T, st0.T, rtol=1e-13)
+
+
+@pytest.mark.parametrize("order,deg", [(3, 3), (2, 2)])
+def test_interpolation_reproduces_polynomials(orc, order, deg):
+    """With one frame everywhere the transform is the identity on equilibria, so the
+    streamed population is the Lagrange interpolant at the departure point, which is
+    exact for polynomials of the stencil's degree."""
+    nx = ny = 24
+    cfg = orc.make_config(nx, ny, bc_x="outflow", bc_y="outflow", interp_order=order)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+
+    def rho_fn(x, y):
+        return 2.0 + 0.01 * (x - 12) + 0.002 * (y - 12) ** 2 + (0.0003 * (x - 11) ** 3 if deg >= 3 else 0.0)
+
+    frame = (0.37, -0.61, 0.9)
+    st = orc.init_state(cfg, rho_fn(x, y), frame[0], frame[1], frame[2])
+    cx, cy, w = orc.lattice_2d(16)
+    P, G = orc.stream_node(cfg, st, 12, 11, frame)
+    Cx = math.sqrt(frame[2]) * cx + frame[0]
+    Cy = math.sqrt(frame[2]) * cy + frame[1]
+    expect = rho_fn(12 - Cx, 11 - Cy) * w
+    assert np.allclose(P, expect, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("split", ["total", "internal"])
+def test_collision_conserves_per_node(orc, split):
+    """Projection into the frame of the moments plus BGK keeps rho, rho u and the energy
+    of the streamed populations (Sec. II conserved moments) to round-off."""
+    rng = np.random.default_rng(21)
+    cfg = orc.make_config(1, 1, split=split, mu=0.02)
+    cx, cy, w = orc.lattice_2d(16)
+    for _ in range(10):
+        frame = (rng.uniform(-2, 2), rng.uniform(-2, 2), rng.uniform(0.3, 2.0))
+        st = orc.init_state(cfg, rng.uniform(0.5, 2.0), frame[0] + 0.1, frame[1] - 0.1,
+                            frame[2] * 1.1)
+        P = st.f[:, 0, 0] * (1 + 0.05 * rng.standard_normal(16))
+        G = st.g[:, 0, 0] * (1 + 0.05 * rng.standard_normal(16))
+        fo, go, star = orc.collide_node(cfg, P, G, frame)
+        sT = math.sqrt(frame[2])
+        Cx, Cy = sT * cx + frame[0], sT * cy + frame[1]
+        tT = math.sqrt(star[2])
+        Sx, Sy = tT * cx + star[0], tT * cy + star[1]
+        assert abs(fo.sum() - P.sum()) < 1e-13 * P.sum()
+        assert abs((fo * Sx).sum() - (P * Cx).sum()) < 1e-12 * P.sum() * 3
+        assert abs((fo * Sy).sum() - (P * Cy).sum()) < 1e-12 * P.sum() * 3
+        assert abs(go.sum() - G.sum()) < 1e-12 * abs(G.sum())
+        # the stored frame is the frame of the post-collision moments
+        st2 = orc.State(fo.reshape(16, 1, 1), go.reshape(16, 1, 1), np.full((1, 1), star[0]),
+                        np.full((1, 1), star[1]), np.full((1, 1), star[2]))
+        r, vx, vy, T, E = orc.moments(cfg, st2)
+        assert abs(vx[0, 0] - star[0]) < 1e-12 and abs(T[0, 0] - star[2]) < 1e-12 * star[2]
+
+
+def test_equilibrium_is_a_collision_fixed_point(orc):
+    cfg = orc.make_config(1, 1, mu=0.02)
+    frame = (0.8, -1.1, 0.7)
+    st = orc.init_state(cfg, 1.7, *frame)
+    fo, go, star = orc.collide_node(cfg, st.f[:, 0, 0], st.g[:, 0, 0], frame)
+    assert np.allclose(fo, st.f[:, 0, 0], rtol=1e-13)
+    assert np.allclose(go, st.g[:, 0, 0], rtol=1e-13)
+    assert np.allclose(star, frame, rtol=1e-13)
+
+
+@pytest.mark.parametrize("lattice", [16, 25])
+def test_global_conservation_uniform_frames(orc, lattice):
+    """With one frame on every node and one predictor-corrector iteration, the Lagrange
+    weights of every source node sum to one over the targets, so a periodic step
+    conserves total mass, momentum and energy to round-off."""
+    rng = np.random.default_rng(22)
+    cfg = orc.make_config(12, 10, lattice=lattice, mu=0.03, pc_fixed_iters=1)
+    st = _perturbed_state(orc, cfg, rng, amp=0.1, uniform_frame=True)
+    before = _totals(orc, cfg, st)
+    after = _totals(orc, cfg, orc.step(cfg, st).state)
+    assert np.all(np.abs(after - before) <= 1e-13 * np.abs(before).max() * cfg.nx * cfg.ny / 10)
+
+
+def test_conservation_drift_is_second_order(orc):
+    """With non-uniform frames the interpolation is not exactly conservative; the drift of
+    the totals shrinks like the square of the perturbation amplitude."""
+    drifts = []
+    for amp in (0.02, 0.01):
+        rng = np.random.default_rng(23)
+        cfg = orc.make_config(12, 10, mu=0.03)
+        st = _perturbed_state(orc, cfg, rng, amp=amp)
+        before = _totals(orc, cfg, st)
+        after = _totals(orc, cfg, orc.step(cfg, st).state)
+        drifts.append(np.abs(after - before).max())
+    ratio = drifts[0] / drifts[1]
+    assert 3.0 < ratio < 5.5, drifts
+
+
+def test_predictor_corrector_fixed_point(orc):
+    """At convergence the stored frame is the frame of the moments of the populations
+    streamed with it (to the tolerance), and fixed mode runs exactly K iterations."""
+    rng = np.random.default_rng(24)
+    cfg = orc.make_config(9, 7, mu=0.03, pc_tol=1e-13, pc_max_iter=30)
+    st = _perturbed_state(orc, cfg, rng, amp=0.05)
+    r = orc.step(cfg, st)
+    assert r.status == 0 and r.iters.max() > 1
+    for (x, y) in ((0, 0), (4, 3), (8, 6)):
+        frame = (r.state.ux[y, x], r.state.uy[y, x], r.state.T[y, x])
+        P, G = orc.stream_node(cfg, st, x, y, frame)
+        fo, go, star = orc.collide_node(cfg, P, G, frame)
+        assert abs(star[0] - frame[0]) < 1e-11 and abs(star[2] - frame[2]) < 1e-11
+    for K in (1, 2, 4):
+        cfgk = orc.make_config(9, 7, mu=0.03, pc_fixed_iters=K)
+        rk = orc.step(cfgk, st)
+        assert np.all(rk.iters == K)
+
+
+def test_nonconvergence_and_nonphysical_status(orc):
+    rng = np.random.default_rng(25)
+    cfg = orc.make_config(6, 5, mu=0.03, pc_tol=0.0, pc_max_iter=2)
+    st = _perturbed_state(orc, cfg, rng, amp=0.05)
+    r = orc.step(cfg, st)
+    assert r.status == -5 and np.all(r.iters == 2)
+    bad = st.copy()
+    bad.g = -bad.g                           # negative energy everywhere -> T < 0
+    r = orc.step(cfg, bad)
+    assert r.status == -4 and r.first_bad >= 0
