@@ -1,0 +1,389 @@
+"""Benchmark of the PonD DDF-BGK step on GB300.
+
+Workload (one "step"): one PonD time step of the periodic 256 x 256 decay configuration —
+a shear wave u_y = 0.05 sin(2 pi x / 256) on rho = 1, T = 1 plus a Gaussian isobaric
+thermal pulse (dT/T = 1e-3, width 16 cells), with background flow u_x = Ma sqrt(gamma)
+for the four Mach numbers 0.5, 1, 1.5, 2 (four independent 256^2 grids), D2Q16, total
+energy split, mixed precision (FP32 arithmetic, FP64 frames).  Synthetic, seeded inputs.
+
+Metric: MLUPS = node updates per second / 1e6 over the whole job (all ranks).  The line
+also carries the plain-FP64 GPU step on the same workload, the L1 error of the mixed path
+against the FP64 path, the FP32-pipe roofline of the step kernel, the end-to-end rate
+through the C-ABI with host buffers, and the FP64 oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): each rank advances its own copy of the workload (independent
+problems, no collective on the data path); value = all ranks' node updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2405_11489_gb300 import workloads as W  # noqa: E402
+
+NX = NY = 256
+MACHS = (0.5, 1.0, 1.5, 2.0)
+GAMMA = 1.4
+MU = 0.05
+METRIC = "PonD-DDF MLUPS, mixed-prec vs plain FP64 at stated L1 err; serving p50/p99 latency"
+WORKLOAD = ("periodic 256x256 shear wave (u_y = 0.05 sin 2pi x/L) + Gaussian thermal pulse "
+            "(dT/T = 1e-3, width 16), background Ma 0.5/1/1.5/2 (4 grids), D2Q16 total split")
+# FP32-pipe peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (max SM clock).
+SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+# Algorithmic FP32 work of one node update (D2Q16): per predictor-corrector iteration and
+# population, a 16-tap interpolation of 20 Hermite coefficients plus the frame move,
+# reconstruction and moment sums (~800 flop); plus ~1000 flop per update for staging and
+# collision.  K = measured mean iterations.
+FLOP_PER_POP_ITER = 800.0
+FLOP_PER_UPDATE = 1000.0
+
+
+def case_fields(ma):
+    shear = W.shear_wave(n=NX, ma=ma, amp=0.05, gamma=GAMMA, mu=MU)
+    pulse = W.thermal_pulse(n=NX, amp=1e-3, width=16.0, gamma=GAMMA, mu=MU, ma=ma)
+    return pulse.rho, shear.ux, shear.uy, pulse.T
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def l2_flusher(torch, device):
+    buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)  # > 129 MB L2
+    def flush():
+        buf.zero_()
+    return flush
+
+
+def make_sims(pond, precision, device, stream):
+    sims = []
+    for ma in MACHS:
+        cfg = pond.Config(nx=NX, ny=NY, precision=precision, gamma=GAMMA, mu=MU)
+        s = pond.Simulation(cfg, device=device, stream=stream)
+        s.set_state(*case_fields(ma))
+        sims.append(s)
+    return sims
+
+
+def time_steps(torch, sims, stream, steps, warmup, flush):
+    """Per-launch CUDA-event times of pond_step(1) on every grid, L2 flushed between steps."""
+    for _ in range(warmup):
+        for s in sims:
+            s.step(1)
+    torch.cuda.synchronize()
+    per_launch = []
+    starts, ends = [], []
+    for _ in range(steps):
+        flush()
+        for s in sims:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(1)
+            e1.record(stream)
+            starts.append(e0)
+            ends.append(e1)
+    torch.cuda.synchronize()
+    for e0, e1 in zip(starts, ends):
+        per_launch.append(e0.elapsed_time(e1))
+    return per_launch
+
+
+def mean_iters(sims):
+    tot = it = 0
+    for s in sims:
+        rc, st = s.stats()
+        tot += st.node_updates
+        it += st.pc_iters_total
+    return it / max(tot, 1)
+
+
+def l1_error(pond, device, stream, nsteps=200):
+    """Per-field relative L1 error of the mixed path against the FP64 path (which matches
+    the oracle to 1e-12 in the parity tests) on the Ma = 1 grid after nsteps."""
+    out = {}
+    res = {}
+    for prec in ("fp32", "fp64"):
+        s = pond.Simulation(pond.Config(nx=NX, ny=NY, precision=prec, gamma=GAMMA, mu=MU),
+                            device=device, stream=stream)
+        s.set_state(*case_fields(1.0))
+        s.step(nsteps)
+        res[prec] = s.moments()
+        s.close()
+    names = ("rho", "ux", "uy", "T")
+    for n, a, b in zip(names, res["fp32"], res["fp64"]):
+        out[n] = float(np.mean(np.abs(a - b)) / np.mean(np.abs(b)))
+    # the perturbations themselves: error relative to the signal (deviation from the mean)
+    for n, a, b in zip(names, res["fp32"], res["fp64"]):
+        dev = np.mean(np.abs(b - b.mean()))
+        out[n + "_vs_signal"] = float(np.mean(np.abs(a - b)) / dev) if dev > 0 else None
+    return {"steps": nsteps, "rel_l1": out}
+
+
+def e2e_rate(torch, pond, device, steps, warmup):
+    """MLUPS through the public C-ABI with host buffers: every step uploads the step's input
+    fields from pinned host memory (pond_set_state), advances one time step (pond_step) and
+    reads the resulting fields back (pond_get_moments), all inside the timed region."""
+    s = pond.Simulation(pond.Config(nx=NX, ny=NY, precision="fp32", gamma=GAMMA, mu=MU), device=device)
+    fields = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case_fields(1.0)]
+    outs = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in range(4)]
+    host_in = [a.numpy() for a in fields]
+    lib = pond.load_library()
+
+    def one():
+        rc = lib.pond_set_state(s.handle, *[a.ctypes.data for a in host_in], 0)
+        assert rc == 0
+        assert lib.pond_step(s.handle, 1) == 0
+        rc = lib.pond_get_moments(s.handle, *[o.data_ptr() for o in outs], 0)
+        assert rc in (0, pond.POND_ENOCONV)
+        return outs[0][0, 0].item()
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    t = time.perf_counter() - t0
+    s.close()
+    nbytes_in = 4 * NX * NY * 8
+    nbytes_out = 4 * NX * NY * 8
+    return {"value": NX * NY * steps / t / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nbytes_in,
+            "d2h_bytes_per_step": nbytes_out,
+            "note": "per step: pond_set_state(host) + pond_step(1) + pond_get_moments(host), Ma = 1 grid"}
+
+
+def cpu_baseline(target_seconds=10.0):
+    """The FP64 oracle, as it stands, on the host cores: the Ma = 1 grid of the workload,
+    whole 256^2 field, as many time steps as fit in ~target_seconds (at least one)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    cfg = oracle.make_config(NX, NY, gamma=GAMMA, mu=MU, pc_tol=1e-12)
+    st = oracle.init_state(cfg, *case_fields(1.0))
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        st = oracle.step(cfg, st).state
+        n += 1
+        if time.perf_counter() - t0 > target_seconds:
+            break
+    t = time.perf_counter() - t0
+    return {"value": NX * NY * n / t / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "FP64 oracle, %d time step(s) of the Ma = 1 256x256 grid (OpenMP, %d threads)"
+                      % (n, cores)}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step is one full time step of one of the four
+    grids (rotating through the Mach numbers), so the run stays within a few minutes."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    cfgs, states = [], []
+    for ma in MACHS:
+        cfg = oracle.make_config(NX, NY, gamma=GAMMA, mu=MU, pc_tol=1e-12)
+        cfgs.append(cfg)
+        states.append(oracle.init_state(cfg, *case_fields(ma)))
+    counter = [0]
+    def one():
+        k = counter[0] % len(states)
+        states[k] = oracle.step(cfgs[k], states[k]).state
+        counter[0] += 1
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    t = time.perf_counter() - t0
+    v = NX * NY * args.steps / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "grids": len(MACHS)},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": "%d full time steps of single 256x256 grids (Ma cycling "
+                                       "0.5/1/1.5/2), FP64 oracle, OpenMP" % args.steps},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pond", choices=["pond", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed mixed-precision steps only (for profiler runs)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    from paper_2405_11489_gb300 import build as B
+    B.build()
+    from paper_2405_11489_gb300 import pond
+    pond.load_library()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    flush = l2_flusher(torch, device)
+    sims = make_sims(pond, "fp32", device, stream)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        per_launch = time_steps(torch, sims, stream, args.steps, args.warmup, flush)
+    step_ms = sum(per_launch) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+        dist.barrier()
+    K = mean_iters(sims)
+    for s in sims:
+        s.close()
+    nodes_per_step = len(MACHS) * NX * NY
+    value = world * nodes_per_step / (step_ms * 1e-3) / 1e6
+    launch_ms = sum(per_launch) / len(per_launch)
+    flops_per_launch = NX * NY * (FLOP_PER_POP_ITER * 16 * K + FLOP_PER_UPDATE)
+    achieved = flops_per_launch / (launch_ms * 1e-3) / 1e12
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    if args.quick:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": "MLUPS", "quick": True,
+                          "ms_per_step": step_ms, "pc_iters_mean": K, "launch_ms": launch_ms,
+                          "achieved_tflops": achieved}))
+        return 0
+    # plain FP64 GPU step on the same workload (fewer steps: it is ~two orders slower)
+    sims64 = make_sims(pond, "fp64", device, stream)
+    per64 = time_steps(torch, sims64, stream, max(2, args.steps // 10), 1, flush)
+    for s in sims64:
+        s.close()
+    fp64_ms = sum(per64) / max(2, args.steps // 10)
+    err = l1_error(pond, device, stream)
+    e2e = e2e_rate(torch, pond, device, steps=max(5, args.steps), warmup=3)
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("step_kernel_fp32_256x256_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "grids": len(MACHS),
+                   "precision": "mixed: FP32 arithmetic and non-equilibrium state, FP64 rho/u/T, "
+                                "compensated moment sums",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "pc_iters_mean": K,
+        "fp64": {"value": nodes_per_step / (fp64_ms * 1e-3) / 1e6, "unit": "MLUPS",
+                 "ms_per_step": fp64_ms, "speedup_mixed_over_fp64": fp64_ms / step_ms},
+        "l1_err_mixed_vs_fp64": err,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "step_kernel<float,float,4,4,false>",
+                     "peak_basis": "FP32 pipe: 152 SM x 128 lanes x 2 flop x 2.07 GHz (unit counts)",
+                     "flops_per_launch": flops_per_launch, "launch_ms": launch_ms},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": len(per_launch),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,152 @@
+/*
+ * libpond — GB300 (sm_103a) CUDA implementation of the particles-on-demand (PonD)
+ * double-distribution-function BGK step for 2-D compressible flow, after
+ * Hosseini, Bhadauria & Karlin, arXiv 2405.11489, Sec. III.A (and Sec. II for the
+ * kinetic model).
+ *
+ * One time step per node (Sec. III.A): recover rho, rho u and the energy from the
+ * populations (Sec. II); take the local frame lambda = (u, T) and the lattice
+ * C_i = sqrt(T) c_i + u shifted and scaled from the Gauss-Hermite quadrature of Table I;
+ * stream f and g semi-Lagrangianly from the departure points x - C_i dt, interpolating
+ * the neighbours' populations after moving them into the receiving node's frame with the
+ * reduced Grad transform (Eqs. gradGeneralTransform, propagationInterpolated); iterate
+ * this predictor-corrector until the frame converges; relax f and g to their equilibria
+ * (BGK, tau = mu / p, Eq. kin_visc).  The energy split is the total-energy split (Eq. Es,
+ * first line) by default, the internal-energy split (second line, with the source term of
+ * Eq. int_g_evolution) as an option.
+ *
+ * Units: lattice units (Sec. III), r = 1, dx = dt = 1, T_L = 1.
+ *
+ * Conventions for every entry point:
+ *  - Return value: a pond_status_t (0 = POND_OK, negative = error).  Kernel-side outcomes
+ *    (non-physical state, predictor-corrector non-convergence) are sticky: pond_step
+ *    returns as soon as the work is enqueued, and the next synchronising call
+ *    (pond_get_moments, pond_get_populations, pond_get_stats, pond_sync) reports them.
+ *  - Fields are row-major [ny][nx] arrays of double (x fastest); population arrays are
+ *    [Q][ny][nx] with population i = b * q1 + a (c_i = (c_a, c_b), q1 = 4 or 5).
+ *  - Ownership: the caller owns every buffer it passes in (host or device), including the
+ *    device workspace given to pond_create.  The library copies inputs, never keeps a
+ *    pointer to a caller's input or output buffer beyond the call, and never frees caller
+ *    memory.  pond_create allocates only the small host-side handle.
+ *  - Streams: all device work of a simulation is enqueued on the CUDA stream given to
+ *    pond_create (NULL = the legacy default stream).
+ *  - Thread safety: one pond_sim per host thread, or external synchronisation.
+ *  - Device: the workspace's device must be current when calling into a pond_sim.
+ */
+#ifndef POND_H
+#define POND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    POND_OK = 0,
+    POND_EINVAL = -1,          /* invalid argument or configuration */
+    POND_ENOMEM = -2,          /* workspace too small */
+    POND_ECUDA = -3,           /* a CUDA runtime call failed */
+    POND_ENONPHYSICAL = -4,    /* rho <= 0, T <= 0 or NaN met at some node (state not repaired) */
+    POND_ENOCONV = -5          /* predictor-corrector hit pc_max_iter at >= 1 node (state advanced) */
+} pond_status_t;
+
+enum { POND_D2Q16 = 16, POND_D2Q25 = 25 };                       /* Table I lattices */
+enum { POND_SPLIT_TOTAL = 0, POND_SPLIT_INTERNAL = 1 };           /* Eq. Es, lines 1 and 2 */
+enum { POND_FP64 = 0, POND_MIXED_FP32 = 1, POND_MIXED_FP16 = 2, POND_MIXED_BF16 = 3 };
+enum { POND_BC_PERIODIC = 0, POND_BC_OUTFLOW = 1 };
+
+typedef struct {
+    int32_t nx, ny;            /* grid; ny = 1 runs the quasi-1-D form (all y taps on row 0) */
+    int32_t lattice;           /* POND_D2Q16 (default) or POND_D2Q25 */
+    int32_t split;             /* POND_SPLIT_TOTAL (default) or POND_SPLIT_INTERNAL */
+    int32_t precision;         /* POND_FP64: FP64 storage and arithmetic.  POND_MIXED_*:
+                                  FP32 arithmetic, FP64 rho/u/T, moment sums compensated,
+                                  non-equilibrium state stored in FP32 / FP16 / BF16 */
+    int32_t interp_order;      /* 3: 4-point cubic Lagrange (default); 2: 3-point (Sec. III.A.2) */
+    int32_t bc_x, bc_y;        /* POND_BC_PERIODIC (index mod n) or POND_BC_OUTFLOW (clamp) */
+    double gamma;              /* adiabatic exponent, 1 < gamma <= 2 (c_v = 1/(gamma - 1)) */
+    double mu;                 /* dynamic viscosity > 0; tau = mu / (rho T) per node */
+    double pc_tol;             /* predictor-corrector tolerance on max(|du|/sqrt(T), |dT|/T) */
+    int32_t pc_max_iter;       /* iteration cap (1..64) */
+    int32_t pc_fixed_iters;    /* > 0: exactly this many iterations, no tolerance test */
+    int32_t tile_x, tile_y;    /* 0 = automatic; otherwise threads per block in x and y */
+    int32_t halo;              /* 0 = automatic; staged halo cells per side (>= 3) */
+} pond_config;
+
+typedef struct {
+    int64_t steps;             /* time steps taken since the last pond_set_state */
+    int64_t node_updates;      /* nx * ny * steps */
+    int64_t pc_iters_total;    /* sum over node updates of predictor-corrector iterations */
+    int32_t pc_iters_max;      /* largest iteration count of any node update */
+    int32_t status;            /* sticky kernel-side status (pond_status_t) */
+    int64_t nonconv_updates;   /* node updates that hit pc_max_iter */
+    int64_t first_bad_node;    /* first node (y * nx + x) found non-physical, or -1 */
+    int64_t halo_fallbacks;    /* populations whose stencil left the staged tile (global gathers) */
+} pond_stats;
+
+typedef struct pond_sim pond_sim;
+
+/* Fill *cfg with the defaults (D2Q16, total split, mixed FP32, cubic, periodic,
+ * gamma 1.4, mu 1e-3, pc_tol 1e-6 (mixed) / 1e-12 (FP64), pc_max_iter 20) for nx x ny. */
+int pond_config_default(pond_config *cfg, int32_t nx, int32_t ny);
+
+/* Bytes of device workspace a simulation with this configuration needs (two copies of the
+ * state, a moment staging area and a status block).  For admission by free HBM. */
+int pond_workspace_bytes(const pond_config *cfg, size_t *bytes);
+
+/* Create a simulation on the current device.  dev_workspace: caller-owned device memory
+ * of at least pond_workspace_bytes bytes, 256-byte aligned; cuda_stream: a cudaStream_t
+ * (or NULL).  *out receives the handle.  POND_EINVAL on a bad configuration,
+ * POND_ENOMEM if bytes is too small. */
+int pond_create(const pond_config *cfg, void *dev_workspace, size_t bytes, void *cuda_stream,
+                pond_sim **out);
+
+/* Set the macroscopic state: equilibrium populations f_i = rho w_i, g_i = g_eq_i in each
+ * node's own frame (Sec. III.A).  rho, ux, uy, T: [ny][nx] doubles, host pointers
+ * (on_device = 0) or device pointers (on_device = 1).  Requires rho > 0, T > 0
+ * (checked on the host for host input; device input is checked by the next step).
+ * Resets statistics and the sticky status. */
+int pond_set_state(pond_sim *sim, const double *rho, const double *ux, const double *uy,
+                   const double *T, int on_device);
+
+/* Set populations directly: f, g [Q][ny][nx] in the frames (ux, uy, T) [ny][nx].  The
+ * library keeps their Hermite coefficients up to total order 3 in each node's frame, which
+ * is all that the frame transformation (N = 3) passes on.  Host or device pointers. */
+int pond_set_populations(pond_sim *sim, const double *f, const double *g, const double *ux,
+                         const double *uy, const double *T, int on_device);
+
+/* Advance nsteps >= 0 time steps, asynchronously on the simulation's stream. */
+int pond_step(pond_sim *sim, int32_t nsteps);
+
+/* Moments of the current populations: rho, ux, uy, T [ny][nx] (any pointer may be NULL).
+ * Host (on_device = 0) or device pointers.  Synchronises the stream and returns the
+ * sticky status. */
+int pond_get_moments(pond_sim *sim, double *rho, double *ux, double *uy, double *T,
+                     int on_device);
+
+/* Current populations f, g [Q][ny][nx] and their frames (ux, uy, T) [ny][nx], each node in
+ * its own frame.  Synchronises; returns the sticky status. */
+int pond_get_populations(pond_sim *sim, double *f, double *g, double *ux, double *uy,
+                         double *T, int on_device);
+
+/* Statistics since the last pond_set_state*.  Synchronises; returns the sticky status. */
+int pond_get_stats(pond_sim *sim, pond_stats *stats);
+
+/* Wait for the simulation's queued work; returns the sticky status. */
+int pond_sync(pond_sim *sim);
+
+/* Free the handle (not the caller's workspace).  Waits for queued work first. */
+int pond_destroy(pond_sim *sim);
+
+/* Static description of a status code. */
+const char *pond_strerror(int status);
+
+/* Library version string. */
+const char *pond_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POND_H */

@@ -1,0 +1,448 @@
+// C-ABI of libpond (declared in include/pond.h): configuration checks, workspace layout,
+// the time-step loop and host <-> device transfers.  No device memory is allocated here:
+// the caller provides the workspace.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "pond.h"
+#include "pond_aux.cuh"
+#include "pond_launch.h"
+#include "pond_step.cuh"
+
+using namespace pond;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t storage_bytes(int precision)
+{
+    switch (precision) {
+        case POND_FP64: return 8;
+        case POND_MIXED_FP32: return 4;
+        default: return 2;
+    }
+}
+
+// Table I quadratures (Gauss-Hermite, r T_L = 1) and the derived Hermite values.
+Lattice make_lattice(int q1)
+{
+    Lattice L;
+    std::memset(&L, 0, sizeof(L));
+    L.q1 = q1;
+    if (q1 == 4) {
+        const double ci = std::sqrt(3.0 - std::sqrt(6.0)), co = std::sqrt(3.0 + std::sqrt(6.0));
+        const double wi = (3.0 + std::sqrt(6.0)) / 12.0, wo = (3.0 - std::sqrt(6.0)) / 12.0;
+        const double c[4] = {-co, -ci, ci, co}, w[4] = {wo, wi, wi, wo};
+        for (int a = 0; a < 4; ++a) { L.c[a] = c[a]; L.w[a] = w[a]; }
+        L.cmax = co;
+    } else {
+        const double ci = std::sqrt(5.0 - std::sqrt(10.0)), co = std::sqrt(5.0 + std::sqrt(10.0));
+        const double w0 = 8.0 / 15.0, wi = (7.0 + 2.0 * std::sqrt(10.0)) / 60.0;
+        const double wo = (7.0 - 2.0 * std::sqrt(10.0)) / 60.0;
+        const double c[5] = {-co, -ci, 0.0, ci, co}, w[5] = {wo, wi, w0, wi, wo};
+        for (int a = 0; a < 5; ++a) { L.c[a] = c[a]; L.w[a] = w[a]; }
+        L.cmax = co;
+    }
+    const double fact[4] = {1.0, 1.0, 2.0, 6.0};
+    for (int a = 0; a < q1; ++a) {
+        const double x = L.c[a];
+        const double he[4] = {1.0, x, x * x - 1.0, x * x * x - 3.0 * x};
+        for (int p = 0; p < 4; ++p) {
+            L.he[a][p] = he[p];
+            L.hn[a][p] = he[p] / fact[p];
+            L.hef[a][p] = (float)L.he[a][p];
+            L.hnf[a][p] = (float)L.hn[a][p];
+        }
+        L.cf[a] = (float)L.c[a];
+        L.wf[a] = (float)L.w[a];
+    }
+    return L;
+}
+
+struct Layout {
+    size_t mac[2], neq[2], status, total;
+};
+
+Layout layout_of(const pond_config& c)
+{
+    const size_t N = (size_t)c.nx * (size_t)c.ny;
+    Layout l;
+    size_t off = 0;
+    for (int k = 0; k < 2; ++k) { l.mac[k] = off; off = align_up(off + NMAC * N * sizeof(double)); }
+    for (int k = 0; k < 2; ++k) { l.neq[k] = off; off = align_up(off + NNEQ * N * storage_bytes(c.precision)); }
+    l.status = off;
+    off = align_up(off + sizeof(DevStatus));
+    l.total = off;
+    return l;
+}
+
+int check_config(const pond_config* c)
+{
+    if (!c) return POND_EINVAL;
+    if (c->nx < 1 || c->ny < 1) return POND_EINVAL;
+    if ((long long)c->nx * (long long)c->ny > (1ll << 31)) return POND_EINVAL;
+    if (c->lattice != POND_D2Q16 && c->lattice != POND_D2Q25) return POND_EINVAL;
+    if (c->split != POND_SPLIT_TOTAL && c->split != POND_SPLIT_INTERNAL) return POND_EINVAL;
+    if (c->precision < POND_FP64 || c->precision > POND_MIXED_BF16) return POND_EINVAL;
+    if (c->interp_order != 2 && c->interp_order != 3) return POND_EINVAL;
+    if ((c->bc_x != 0 && c->bc_x != 1) || (c->bc_y != 0 && c->bc_y != 1)) return POND_EINVAL;
+    if (!(c->gamma > 1.0 && c->gamma <= 2.0)) return POND_EINVAL;   // U' >= 0 in 2-D needs gamma <= 2
+    if (!(c->mu > 0.0) || !std::isfinite(c->mu)) return POND_EINVAL;
+    if (!(c->pc_tol >= 0.0)) return POND_EINVAL;
+    if (c->pc_max_iter < 1 || c->pc_max_iter > 64) return POND_EINVAL;
+    if (c->pc_fixed_iters < 0 || c->pc_fixed_iters > 64) return POND_EINVAL;
+    if (c->tile_x < 0 || c->tile_y < 0 || c->halo < 0 || c->halo > 64) return POND_EINVAL;
+    if (c->tile_x || c->tile_y) {
+        int t = c->tile_x * c->tile_y;
+        if (c->tile_x < 1 || c->tile_y < 1 || t != kStepThreads) return POND_EINVAL;
+        if (c->ny == 1 && c->tile_y != 1) return POND_EINVAL;
+    }
+    return POND_OK;
+}
+
+}  // namespace
+
+struct pond_sim {
+    pond_config cfg;
+    cudaStream_t stream;
+    char* ws;
+    Layout lay;
+    int cur;
+    long long steps;
+    Lattice lat;
+    int tx, ty, box_w, box_h;
+    size_t smem;
+    bool one_d;
+    DevStatus host_status;
+};
+
+namespace {
+
+double* mac_ptr(pond_sim* s, int k) { return reinterpret_cast<double*>(s->ws + s->lay.mac[k]); }
+void* neq_ptr(pond_sim* s, int k) { return s->ws + s->lay.neq[k]; }
+DevStatus* status_ptr(pond_sim* s) { return reinterpret_cast<DevStatus*>(s->ws + s->lay.status); }
+
+AuxParams aux_params(pond_sim* s, int k)
+{
+    AuxParams a;
+    std::memset(&a, 0, sizeof(a));
+    a.lat = s->lat;
+    a.nx = s->cfg.nx;
+    a.ny = s->cfg.ny;
+    a.bc_x = s->cfg.bc_x;
+    a.bc_y = s->cfg.bc_y;
+    a.split = s->cfg.split;
+    a.N = (long long)s->cfg.nx * s->cfg.ny;
+    a.cv = 1.0 / (s->cfg.gamma - 1.0);
+    a.mac = mac_ptr(s, k);
+    a.neq = neq_ptr(s, k);
+    a.mac_prev = mac_ptr(s, 1 - k);
+    a.status = status_ptr(s);
+    return a;
+}
+
+#define POND_BY_PRECISION(prec, FN, ...)                                  \
+    ((prec) == POND_FP64 ? FN##_f64(__VA_ARGS__)                          \
+     : (prec) == POND_MIXED_FP32 ? FN##_f32(__VA_ARGS__)                  \
+     : (prec) == POND_MIXED_FP16 ? FN##_f16(__VA_ARGS__) : FN##_bf16(__VA_ARGS__))
+
+// Step launchers indexed [precision][q1 == 5][one_d].
+const StepFn kStep[4][2][2] = {
+    {{step_f64_q4_2d, step_f64_q4_1d}, {step_f64_q5_2d, step_f64_q5_1d}},
+    {{step_f32_q4_2d, step_f32_q4_1d}, {step_f32_q5_2d, step_f32_q5_1d}},
+    {{step_f16_q4_2d, step_f16_q4_1d}, {step_f16_q5_2d, step_f16_q5_1d}},
+    {{step_bf16_q4_2d, step_bf16_q4_1d}, {step_bf16_q5_2d, step_bf16_q5_1d}},
+};
+const SmemFn kSmem[4][2][2] = {
+    {{smem_f64_q4_2d, smem_f64_q4_1d}, {smem_f64_q5_2d, smem_f64_q5_1d}},
+    {{smem_f32_q4_2d, smem_f32_q4_1d}, {smem_f32_q5_2d, smem_f32_q5_1d}},
+    {{smem_f16_q4_2d, smem_f16_q4_1d}, {smem_f16_q5_2d, smem_f16_q5_1d}},
+    {{smem_bf16_q4_2d, smem_bf16_q4_1d}, {smem_bf16_q5_2d, smem_bf16_q5_1d}},
+};
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return POND_OK;
+    std::fprintf(stderr, "libpond: CUDA error %s\n", cudaGetErrorString(e));
+    return POND_ECUDA;
+}
+
+int reset_status(pond_sim* s)
+{
+    DevStatus z;
+    std::memset(&z, 0, sizeof(z));
+    z.first_bad = ~0ull;
+    s->steps = 0;
+    return cuda_status(cudaMemcpyAsync(status_ptr(s), &z, sizeof(z), cudaMemcpyHostToDevice, s->stream));
+}
+
+// Synchronise and translate the sticky device status.
+int sync_status(pond_sim* s)
+{
+    cudaError_t e = cudaMemcpyAsync(&s->host_status, status_ptr(s), sizeof(DevStatus),
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (s->host_status.flags & 1) return POND_ENONPHYSICAL;
+    if (s->host_status.flags & 2) return POND_ENOCONV;
+    return POND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pond_version(void) { return "libpond 0.1 (sm_103a)"; }
+
+const char* pond_strerror(int status)
+{
+    switch (status) {
+        case POND_OK: return "ok";
+        case POND_EINVAL: return "invalid argument or configuration";
+        case POND_ENOMEM: return "workspace too small";
+        case POND_ECUDA: return "CUDA runtime error";
+        case POND_ENONPHYSICAL: return "non-physical state (rho <= 0, T <= 0 or NaN)";
+        case POND_ENOCONV: return "predictor-corrector did not converge at some node";
+        default: return "unknown status";
+    }
+}
+
+int pond_config_default(pond_config* cfg, int32_t nx, int32_t ny)
+{
+    if (!cfg) return POND_EINVAL;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->nx = nx;
+    cfg->ny = ny;
+    cfg->lattice = POND_D2Q16;
+    cfg->split = POND_SPLIT_TOTAL;
+    cfg->precision = POND_MIXED_FP32;
+    cfg->interp_order = 3;
+    cfg->bc_x = POND_BC_PERIODIC;
+    cfg->bc_y = POND_BC_PERIODIC;
+    cfg->gamma = 1.4;
+    cfg->mu = 1e-3;
+    cfg->pc_tol = 1e-6;
+    cfg->pc_max_iter = 20;
+    cfg->pc_fixed_iters = 0;
+    return check_config(cfg);
+}
+
+int pond_workspace_bytes(const pond_config* cfg, size_t* bytes)
+{
+    int rc = check_config(cfg);
+    if (rc != POND_OK) return rc;
+    if (!bytes) return POND_EINVAL;
+    *bytes = layout_of(*cfg).total;
+    return POND_OK;
+}
+
+int pond_create(const pond_config* cfg, void* dev_workspace, size_t bytes, void* cuda_stream,
+                pond_sim** out)
+{
+    if (!out) return POND_EINVAL;
+    *out = nullptr;
+    int rc = check_config(cfg);
+    if (rc != POND_OK) return rc;
+    if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign)) return POND_EINVAL;
+    Layout lay = layout_of(*cfg);
+    if (bytes < lay.total) return POND_ENOMEM;
+    pond_sim* s = new (std::nothrow) pond_sim;
+    if (!s) return POND_ENOMEM;
+    std::memset(s, 0, sizeof(*s));
+    s->cfg = *cfg;
+    s->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    s->ws = reinterpret_cast<char*>(dev_workspace);
+    s->lay = lay;
+    s->cur = 0;
+    s->lat = make_lattice(cfg->lattice == POND_D2Q16 ? 4 : 5);
+    s->one_d = (cfg->ny == 1);
+    if (s->one_d) {
+        s->tx = kStepThreads;
+        s->ty = 1;
+    } else {
+        s->tx = cfg->tile_x ? cfg->tile_x : 32;
+        s->ty = cfg->tile_y ? cfg->tile_y : kStepThreads / 32;
+    }
+    const int extent = cfg->halo ? 2 * cfg->halo + 2 : 12;
+    s->box_w = s->tx + extent;
+    s->box_h = s->one_d ? 1 : s->ty + extent;
+    const size_t rbytes = cfg->precision == POND_FP64 ? 8 : 4;
+    s->smem = (size_t)s->box_w * s->box_h * 2 * NCOEF * rbytes;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    int smem_optin = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess && s->smem + 1024 > (size_t)smem_optin) {
+        delete s;
+        return POND_EINVAL;   // box too large for shared memory: lower halo or tile
+    }
+    if (e == cudaSuccess)
+        e = kSmem[cfg->precision][s->lat.q1 == 5][s->one_d](cfg->interp_order, s->smem);
+    if (e == cudaSuccess) {
+        rc = reset_status(s);
+        if (rc != POND_OK) { delete s; return rc; }
+        e = cudaMemsetAsync(s->ws, 0, lay.status, s->stream);
+    }
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_status(e);
+    }
+    *out = s;
+    return POND_OK;
+}
+
+int pond_set_state(pond_sim* s, const double* rho, const double* ux, const double* uy, const double* T,
+                   int on_device)
+{
+    if (!s || !rho || !ux || !uy || !T) return POND_EINVAL;
+    const long long N = (long long)s->cfg.nx * s->cfg.ny;
+    int rc = reset_status(s);
+    if (rc != POND_OK) return rc;
+    const double *drho = rho, *dux = ux, *duy = uy, *dT = T;
+    if (!on_device) {
+        for (long long n = 0; n < N; ++n)
+            if (!(rho[n] > 0.0) || !(T[n] > 0.0) || !std::isfinite(rho[n]) || !std::isfinite(T[n]) ||
+                !std::isfinite(ux[n]) || !std::isfinite(uy[n]))
+                return POND_EINVAL;
+        double* stage = mac_ptr(s, 1 - s->cur);   // the idle frame buffer stages the input
+        const double* src[4] = {rho, ux, uy, T};
+        for (int k = 0; k < 4; ++k) {
+            cudaError_t e = cudaMemcpyAsync(stage + k * N, src[k], N * sizeof(double),
+                                            cudaMemcpyHostToDevice, s->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        drho = stage; dux = stage + N; duy = stage + 2 * N; dT = stage + 3 * N;
+    }
+    AuxParams a = aux_params(s, s->cur);
+    return cuda_status(POND_BY_PRECISION(s->cfg.precision, init, a, drho, dux, duy, dT, s->stream));
+}
+
+int pond_set_populations(pond_sim* s, const double* f, const double* g, const double* ux, const double* uy,
+                         const double* T, int on_device)
+{
+    if (!s || !f || !g || !ux || !uy || !T) return POND_EINVAL;
+    if (!on_device) return POND_EINVAL;   // populations move through device buffers only
+    int rc = reset_status(s);
+    if (rc != POND_OK) return rc;
+    AuxParams a = aux_params(s, s->cur);
+    return cuda_status(POND_BY_PRECISION(s->cfg.precision, set_pops, a, f, g, ux, uy, T, s->stream));
+}
+
+int pond_step(pond_sim* s, int32_t nsteps)
+{
+    if (!s || nsteps < 0) return POND_EINVAL;
+    const pond_config& c = s->cfg;
+    const long long N = (long long)c.nx * c.ny;
+    StepParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.lat = s->lat;
+    p.nx = c.nx;
+    p.ny = c.ny;
+    p.bc_x = c.bc_x;
+    p.bc_y = c.bc_y;
+    p.split = c.split;
+    p.pc_max_iter = c.pc_max_iter;
+    p.pc_fixed = c.pc_fixed_iters;
+    p.box_w = s->box_w;
+    p.box_h = s->box_h;
+    p.N = N;
+    p.cv = 1.0 / (c.gamma - 1.0);
+    p.inv_cv = c.gamma - 1.0;
+    p.mu = c.mu;
+    p.pc_tol = c.pc_tol;
+    p.status = status_ptr(s);
+    Launch l;
+    l.block = dim3(s->tx, s->ty, 1);
+    l.grid = dim3((c.nx + s->tx - 1) / s->tx, (c.ny + s->ty - 1) / s->ty, 1);
+    l.smem = s->smem;
+    l.stream = s->stream;
+    for (int k = 0; k < nsteps; ++k) {
+        p.mac_in = mac_ptr(s, s->cur);
+        p.neq_in = neq_ptr(s, s->cur);
+        p.mac_out = mac_ptr(s, 1 - s->cur);
+        p.neq_out = neq_ptr(s, 1 - s->cur);
+        cudaError_t e = kStep[c.precision][s->lat.q1 == 5][s->one_d](p, c.interp_order, l);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (c.split == POND_SPLIT_INTERNAL) {
+            AuxParams a = aux_params(s, 1 - s->cur);   // new state; mac_prev = state before the step
+            e = POND_BY_PRECISION(c.precision, internal_source, a, s->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        s->cur = 1 - s->cur;
+        s->steps += 1;
+    }
+    return POND_OK;
+}
+
+int pond_get_moments(pond_sim* s, double* rho, double* ux, double* uy, double* T, int on_device)
+{
+    if (!s) return POND_EINVAL;
+    const long long N = (long long)s->cfg.nx * s->cfg.ny;
+    AuxParams a = aux_params(s, s->cur);
+    cudaError_t e;
+    if (on_device) {
+        e = POND_BY_PRECISION(s->cfg.precision, moments, a, rho, ux, uy, T, s->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    } else {
+        double* stage = mac_ptr(s, 1 - s->cur);
+        e = POND_BY_PRECISION(s->cfg.precision, moments, a, stage, stage + N, stage + 2 * N, stage + 3 * N,
+                              s->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        double* dst[4] = {rho, ux, uy, T};
+        for (int k = 0; k < 4; ++k) {
+            if (!dst[k]) continue;
+            e = cudaMemcpyAsync(dst[k], stage + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+    }
+    return sync_status(s);
+}
+
+int pond_get_populations(pond_sim* s, double* f, double* g, double* ux, double* uy, double* T, int on_device)
+{
+    if (!s) return POND_EINVAL;
+    if (!on_device) return POND_EINVAL;
+    AuxParams a = aux_params(s, s->cur);
+    cudaError_t e = POND_BY_PRECISION(s->cfg.precision, get_pops, a, f, g, ux, uy, T, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return sync_status(s);
+}
+
+int pond_get_stats(pond_sim* s, pond_stats* st)
+{
+    if (!s || !st) return POND_EINVAL;
+    int rc = sync_status(s);
+    if (rc == POND_ECUDA) return rc;
+    const DevStatus& d = s->host_status;
+    std::memset(st, 0, sizeof(*st));
+    st->steps = s->steps;
+    st->node_updates = s->steps * (long long)s->cfg.nx * s->cfg.ny;
+    st->pc_iters_total = (int64_t)d.iters_total;
+    st->pc_iters_max = (int32_t)d.iters_max;
+    st->status = rc;
+    st->nonconv_updates = (int64_t)d.nonconv;
+    st->first_bad_node = d.first_bad == ~0ull ? -1 : (int64_t)d.first_bad;
+    st->halo_fallbacks = (int64_t)d.fallbacks;
+    return rc;
+}
+
+int pond_sync(pond_sim* s)
+{
+    if (!s) return POND_EINVAL;
+    return sync_status(s);
+}
+
+int pond_destroy(pond_sim* s)
+{
+    if (!s) return POND_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    delete s;
+    return cuda_status(e);
+}
+
+}  // extern "C"

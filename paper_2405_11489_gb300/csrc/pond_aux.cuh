@@ -1,0 +1,189 @@
+// Auxiliary kernels of libpond: equilibrium initialisation, population import/export,
+// moments of the current state, and the internal-energy-split source pass.
+#pragma once
+
+#include "pond_device.cuh"
+
+namespace pond {
+
+struct AuxParams {
+    Lattice lat;
+    int nx, ny, bc_x, bc_y, split;
+    long long N;
+    double cv;
+    double* mac;        // [4][N] rho, u_x, u_y, T
+    void* neq;          // [19][N] storage type
+    const double* mac_prev;  // internal source: frames before the step
+    DevStatus* status;
+};
+
+// Equilibrium state from rho, u, T (device arrays [N]): f_i = rho w_i, g_i = g_eq_i in the
+// node's own frame (Sec. III.A) -> all non-equilibrium coefficients zero.
+template <class S>
+__global__ void init_kernel(AuxParams p, const double* rho, const double* ux, const double* uy,
+                            const double* T)
+{
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    double r = rho[n], vx = ux[n], vy = uy[n], t = T[n];
+    if (!(r > 0.0) || !(t > 0.0) || isnan(vx) || isnan(vy) || isinf(vx) || isinf(vy) || isinf(r) || isinf(t)) {
+        atomicOr(&p.status->flags, 1);
+        atomicMin(&p.status->first_bad, (unsigned long long)n);
+    }
+    p.mac[n] = r;
+    p.mac[p.N + n] = vx;
+    p.mac[2 * p.N + n] = vy;
+    p.mac[3 * p.N + n] = t;
+    S* q = reinterpret_cast<S*>(p.neq);
+    for (int m = 0; m < NNEQ; ++m) sto_put<S, double>(q + (long long)m * p.N + n, 0.0);
+}
+
+// Populations f, g [Q][N] in frames (ux, uy, T) -> Hermite coefficients of order <= 3.
+template <class S>
+__global__ void set_pops_kernel(AuxParams p, const double* f, const double* g, const double* ux,
+                                const double* uy, const double* T)
+{
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const Lattice& L = p.lat;
+    const int q1 = L.q1;
+    double A[NCOEF] = {0}, B[NCOEF] = {0};
+    for (int b = 0; b < q1; ++b)
+        for (int a = 0; a < q1; ++a) {
+            long long i = (long long)(b * q1 + a) * p.N + n;
+            double fi = f[i], gi = g[i];
+            for (int pp = 0; pp <= 3; ++pp)
+                for (int qq = 0; qq <= 3 - pp; ++qq) {
+                    double h = L.he[a][pp] * L.he[b][qq];
+                    A[slot(pp, qq)] += fi * h;
+                    B[slot(pp, qq)] += gi * h;
+                }
+        }
+    double vx = ux[n], vy = uy[n], t = T[n];
+    double rho = A[0];
+    if (!(rho > 0.0) || !(t > 0.0) || isnan(vx) || isnan(vy)) {
+        atomicOr(&p.status->flags, 1);
+        atomicMin(&p.status->first_bad, (unsigned long long)n);
+    }
+    p.mac[n] = rho;
+    p.mac[p.N + n] = vx;
+    p.mac[2 * p.N + n] = vy;
+    p.mac[3 * p.N + n] = t;
+    GEq e = g_equilibrium(p.split, p.cv, rho, vx, vy, t, sqrt(t));
+    B[slot(0, 0)] -= e.b00;
+    B[slot(1, 0)] -= e.b10;
+    B[slot(0, 1)] -= e.b01;
+    B[slot(2, 0)] -= e.b20;
+    B[slot(0, 2)] -= e.b20;
+    S* q = reinterpret_cast<S*>(p.neq);
+    for (int m = 1; m < NCOEF; ++m) sto_put<S, double>(q + (long long)(m - 1) * p.N + n, A[m]);
+    for (int m = 0; m < NCOEF; ++m) sto_put<S, double>(q + (long long)(9 + m) * p.N + n, B[m]);
+}
+
+// Full own-frame coefficients of node n (FP64).
+template <class S>
+__device__ __forceinline__ void node_coefficients(const AuxParams& p, long long n, double* A, double* B,
+                                                  double& rho, double& ux, double& uy, double& T)
+{
+    const S* q = reinterpret_cast<const S*>(p.neq);
+    rho = p.mac[n];
+    ux = p.mac[p.N + n];
+    uy = p.mac[2 * p.N + n];
+    T = p.mac[3 * p.N + n];
+    A[0] = rho;
+    for (int m = 1; m < NCOEF; ++m) A[m] = sto_load<S>(q + (long long)(m - 1) * p.N + n);
+    for (int m = 0; m < NCOEF; ++m) B[m] = sto_load<S>(q + (long long)(9 + m) * p.N + n);
+    GEq e = g_equilibrium(p.split, p.cv, rho, ux, uy, T, sqrt(T));
+    B[slot(0, 0)] += e.b00;
+    B[slot(1, 0)] += e.b10;
+    B[slot(0, 1)] += e.b01;
+    B[slot(2, 0)] += e.b20;
+    B[slot(0, 2)] += e.b20;
+}
+
+// Moments of the populations (Sec. II): rho = A_00, rho u = rho u_frame + sqrt(T) (A_10, A_01),
+// total split E = B_00, T = (E/rho - |u|^2/2)/c_v; internal split T = B_00/(rho c_v).
+template <class S>
+__global__ void moments_kernel(AuxParams p, double* out_rho, double* out_ux, double* out_uy,
+                               double* out_T)
+{
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    double A[NCOEF], B[NCOEF], rho, ux, uy, T;
+    node_coefficients<S>(p, n, A, B, rho, ux, uy, T);
+    double sT = sqrt(T);
+    double vx = ux + sT * A[slot(1, 0)] / rho;
+    double vy = uy + sT * A[slot(0, 1)] / rho;
+    double t = (p.split == 0) ? (B[0] / rho - 0.5 * (vx * vx + vy * vy)) / p.cv : B[0] / (rho * p.cv);
+    if (out_rho) out_rho[n] = rho;
+    if (out_ux) out_ux[n] = vx;
+    if (out_uy) out_uy[n] = vy;
+    if (out_T) out_T[n] = t;
+}
+
+// Populations in each node's own frame: f_i = w_i sum A_pq He_p(c_a) He_q(c_b) / (p! q!).
+template <class S>
+__global__ void get_pops_kernel(AuxParams p, double* f, double* g, double* oux, double* ouy, double* oT)
+{
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const Lattice& L = p.lat;
+    double A[NCOEF], B[NCOEF], rho, ux, uy, T;
+    node_coefficients<S>(p, n, A, B, rho, ux, uy, T);
+    const int q1 = L.q1;
+    for (int b = 0; b < q1; ++b)
+        for (int a = 0; a < q1; ++a) {
+            double sf = 0.0, sg = 0.0;
+            for (int pp = 0; pp <= 3; ++pp)
+                for (int qq = 0; qq <= 3 - pp; ++qq) {
+                    double h = L.hn[a][pp] * L.hn[b][qq];
+                    sf += A[slot(pp, qq)] * h;
+                    sg += B[slot(pp, qq)] * h;
+                }
+            long long i = (long long)(b * q1 + a) * p.N + n;
+            double w = L.w[a] * L.w[b];
+            if (f) f[i] = w * sf;
+            if (g) g[i] = w * sg;
+        }
+    if (oux) oux[n] = ux;
+    if (ouy) ouy[n] = uy;
+    if (oT) oT[n] = T;
+}
+
+// Internal-energy split source (Eq. int_g_evolution; Appendix A, G term) after the step:
+//   G_i = -rho w_i (C_i - u) . (d_t u + C_i . grad u)   (f -> f_eq inside the source),
+// d_t u by the backward difference against the frame before the step, grad u by central
+// differences of the new frames (boundary-mapped).  In Hermite coefficients of the node's
+// frame the source is G_00 = -rho T div u, G_10 = -rho sqrt(T) Du_x, G_01 = -rho sqrt(T) Du_y,
+// G_20 = -2 rho T d_x u_x, G_11 = -rho T (d_y u_x + d_x u_y), G_02 = -2 rho T d_y u_y
+// (Du = d_t u + u . grad u), and it is added to the non-equilibrium part of g.
+template <class S>
+__global__ void internal_source_kernel(AuxParams p)
+{
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const int x = (int)(n % p.nx), y = (int)(n / p.nx);
+    const long long N = p.N;
+    const double* ux1 = p.mac + N;
+    const double* uy1 = p.mac + 2 * N;
+    long long xp = (long long)y * p.nx + bc_map(x + 1, p.nx, p.bc_x);
+    long long xm = (long long)y * p.nx + bc_map(x - 1, p.nx, p.bc_x);
+    long long yp = (long long)bc_map(y + 1, p.ny, p.bc_y) * p.nx + x;
+    long long ym = (long long)bc_map(y - 1, p.ny, p.bc_y) * p.nx + x;
+    double dxux = 0.5 * (ux1[xp] - ux1[xm]), dyux = 0.5 * (ux1[yp] - ux1[ym]);
+    double dxuy = 0.5 * (uy1[xp] - uy1[xm]), dyuy = 0.5 * (uy1[yp] - uy1[ym]);
+    double rho = p.mac[n], ux = ux1[n], uy = uy1[n], T = p.mac[3 * N + n];
+    double dtux = ux - p.mac_prev[N + n], dtuy = uy - p.mac_prev[2 * N + n];
+    double Dux = dtux + ux * dxux + uy * dyux;
+    double Duy = dtuy + ux * dxuy + uy * dyuy;
+    double rT = rho * T, rsT = rho * sqrt(T);
+    S* q = reinterpret_cast<S*>(p.neq);
+    double G[6] = {-rT * (dxux + dyuy), -rsT * Dux, -rsT * Duy, -2.0 * rT * dxux,
+                   -rT * (dyux + dxuy), -2.0 * rT * dyuy};
+    for (int m = 0; m < 6; ++m) {
+        S* a = q + (long long)(9 + m) * N + n;
+        sto_put<S, double>(a, sto_load<S>(a) + G[m]);
+    }
+}
+
+}  // namespace pond

@@ -1,0 +1,57 @@
+// Launch entry points of the kernels.  Step kernels are instantiated per storage precision,
+// lattice and grid dimensionality, auxiliary kernels per precision, each set in its own
+// translation unit so that the build runs in parallel.
+#pragma once
+
+#include "pond_device.cuh"
+
+namespace pond {
+
+struct StepParams;
+struct AuxParams;
+
+// Threads per CTA of the step kernel (tile_x * tile_y).
+constexpr int kStepThreads = 256;
+
+struct Launch {
+    dim3 grid, block;
+    size_t smem;
+    cudaStream_t stream;
+};
+
+typedef cudaError_t (*StepFn)(const StepParams& p, int order, const Launch& l);
+typedef cudaError_t (*SmemFn)(int order, size_t bytes);
+
+#define POND_DECLARE_STEP(TAG)                                               \
+    cudaError_t step_##TAG(const StepParams& p, int order, const Launch& l); \
+    cudaError_t smem_##TAG(int order, size_t bytes);
+
+#define POND_DECLARE_STEP_ALL(PREC) \
+    POND_DECLARE_STEP(PREC##_q4_2d) \
+    POND_DECLARE_STEP(PREC##_q4_1d) \
+    POND_DECLARE_STEP(PREC##_q5_2d) \
+    POND_DECLARE_STEP(PREC##_q5_1d)
+
+POND_DECLARE_STEP_ALL(f64)
+POND_DECLARE_STEP_ALL(f32)
+POND_DECLARE_STEP_ALL(f16)
+POND_DECLARE_STEP_ALL(bf16)
+
+#define POND_DECLARE_AUX(PREC)                                                                   \
+    cudaError_t init_##PREC(const AuxParams& p, const double* rho, const double* ux,             \
+                            const double* uy, const double* T, cudaStream_t s);                  \
+    cudaError_t set_pops_##PREC(const AuxParams& p, const double* f, const double* g,            \
+                                const double* ux, const double* uy, const double* T,             \
+                                cudaStream_t s);                                                 \
+    cudaError_t moments_##PREC(const AuxParams& p, double* rho, double* ux, double* uy,          \
+                               double* T, cudaStream_t s);                                       \
+    cudaError_t get_pops_##PREC(const AuxParams& p, double* f, double* g, double* ux,            \
+                                double* uy, double* T, cudaStream_t s);                          \
+    cudaError_t internal_source_##PREC(const AuxParams& p, cudaStream_t s);
+
+POND_DECLARE_AUX(f64)
+POND_DECLARE_AUX(f32)
+POND_DECLARE_AUX(f16)
+POND_DECLARE_AUX(bf16)
+
+}  // namespace pond

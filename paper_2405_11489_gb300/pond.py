@@ -1,0 +1,313 @@
+"""Thin ctypes binding of libpond (include/pond.h).
+
+Argument marshalling only: every step of the PonD path runs in the library's CUDA
+kernels.  PyTorch supplies device memory (the workspace and device-side arrays) and the
+CUDA stream.  There is no CPU fallback: if the shared library has not been built, or no
+CUDA device is present, the calls raise.
+
+The functions carry the C names (``pond_create``, ``pond_set_state``, ``pond_step``,
+``pond_get_moments``, ``pond_get_populations``, ``pond_get_stats``, ``pond_destroy`` ...);
+``Simulation`` wraps one ``pond_sim`` with its workspace.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.environ.get("POND_LIB") or os.path.join(_HERE, "_build", "libpond.so")
+
+POND_OK, POND_EINVAL, POND_ENOMEM, POND_ECUDA, POND_ENONPHYSICAL, POND_ENOCONV = 0, -1, -2, -3, -4, -5
+POND_D2Q16, POND_D2Q25 = 16, 25
+POND_SPLIT_TOTAL, POND_SPLIT_INTERNAL = 0, 1
+POND_FP64, POND_MIXED_FP32, POND_MIXED_FP16, POND_MIXED_BF16 = 0, 1, 2, 3
+POND_BC_PERIODIC, POND_BC_OUTFLOW = 0, 1
+
+PRECISIONS = {"fp64": POND_FP64, "fp32": POND_MIXED_FP32, "fp16": POND_MIXED_FP16,
+              "bf16": POND_MIXED_BF16}
+SPLITS = {"total": POND_SPLIT_TOTAL, "internal": POND_SPLIT_INTERNAL}
+BCS = {"periodic": POND_BC_PERIODIC, "outflow": POND_BC_OUTFLOW}
+
+# Symbols the header declares (checked by the ABI test).
+EXPORTS = ("pond_config_default", "pond_workspace_bytes", "pond_create", "pond_set_state",
+           "pond_set_populations", "pond_step", "pond_get_moments", "pond_get_populations",
+           "pond_get_stats", "pond_sync", "pond_destroy", "pond_strerror", "pond_version")
+
+
+class pond_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("lattice", ctypes.c_int32),
+                ("split", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("interp_order", ctypes.c_int32), ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+                ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("pc_tol", ctypes.c_double),
+                ("pc_max_iter", ctypes.c_int32), ("pc_fixed_iters", ctypes.c_int32),
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("halo", ctypes.c_int32)]
+
+
+class pond_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("node_updates", ctypes.c_int64),
+                ("pc_iters_total", ctypes.c_int64), ("pc_iters_max", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("nonconv_updates", ctypes.c_int64),
+                ("first_bad_node", ctypes.c_int64), ("halo_fallbacks", ctypes.c_int64)]
+
+
+class PondError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (what, strerror(status), status))
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpond.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError("libpond is not built (%s missing): run "
+                               "`python -m paper_2405_11489_gb300.build`" % path)
+        lib = ctypes.CDLL(path)
+        vp, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+        P = ctypes.POINTER
+        lib.pond_config_default.argtypes = [P(pond_config), i32, i32]
+        lib.pond_workspace_bytes.argtypes = [P(pond_config), P(sz)]
+        lib.pond_create.argtypes = [P(pond_config), vp, sz, vp, P(vp)]
+        lib.pond_set_state.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int]
+        lib.pond_set_populations.argtypes = [vp] + [vp] * 5 + [ctypes.c_int]
+        lib.pond_step.argtypes = [vp, i32]
+        lib.pond_get_moments.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int]
+        lib.pond_get_populations.argtypes = [vp] + [vp] * 5 + [ctypes.c_int]
+        lib.pond_get_stats.argtypes = [vp, P(pond_stats)]
+        lib.pond_sync.argtypes = [vp]
+        lib.pond_destroy.argtypes = [vp]
+        lib.pond_strerror.argtypes = [ctypes.c_int]
+        lib.pond_strerror.restype = ctypes.c_char_p
+        lib.pond_version.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("pond_strerror", "pond_version"):
+                getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return load_library().pond_strerror(status).decode()
+    except RuntimeError:
+        return "status %d" % status
+
+
+def _check(rc, what, allow=()):
+    if rc != POND_OK and rc not in allow:
+        raise PondError(rc, what)
+    return rc
+
+
+# ---------------------------------------------------------------------------------------
+# Functions with the C names (argument marshalling only)
+# ---------------------------------------------------------------------------------------
+def pond_config_default(nx: int, ny: int) -> pond_config:
+    cfg = pond_config()
+    _check(load_library().pond_config_default(ctypes.byref(cfg), nx, ny), "pond_config_default")
+    return cfg
+
+
+def pond_workspace_bytes(cfg: pond_config) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load_library().pond_workspace_bytes(ctypes.byref(cfg), ctypes.byref(n)), "pond_workspace_bytes")
+    return n.value
+
+
+def pond_create(cfg: pond_config, workspace_ptr: int, nbytes: int, stream_ptr: int) -> int:
+    h = ctypes.c_void_p(0)
+    _check(load_library().pond_create(ctypes.byref(cfg), ctypes.c_void_p(workspace_ptr), nbytes,
+                                      ctypes.c_void_p(stream_ptr), ctypes.byref(h)), "pond_create")
+    return h.value
+
+
+def pond_set_state(h, rho, ux, uy, T, on_device: int) -> int:
+    return load_library().pond_set_state(h, rho, ux, uy, T, on_device)
+
+
+def pond_set_populations(h, f, g, ux, uy, T, on_device: int) -> int:
+    return load_library().pond_set_populations(h, f, g, ux, uy, T, on_device)
+
+
+def pond_step(h, nsteps: int) -> int:
+    return load_library().pond_step(h, nsteps)
+
+
+def pond_get_moments(h, rho, ux, uy, T, on_device: int) -> int:
+    return load_library().pond_get_moments(h, rho, ux, uy, T, on_device)
+
+
+def pond_get_populations(h, f, g, ux, uy, T, on_device: int) -> int:
+    return load_library().pond_get_populations(h, f, g, ux, uy, T, on_device)
+
+
+def pond_get_stats(h):
+    st = pond_stats()
+    rc = load_library().pond_get_stats(h, ctypes.byref(st))
+    return rc, st
+
+
+def pond_sync(h) -> int:
+    return load_library().pond_sync(h)
+
+
+def pond_destroy(h) -> int:
+    return load_library().pond_destroy(h)
+
+
+# ---------------------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------------------
+@dataclass
+class Config:
+    nx: int
+    ny: int
+    lattice: int = 16
+    split: str = "total"
+    precision: str = "fp32"
+    interp_order: int = 3
+    bc_x: str = "periodic"
+    bc_y: str = "periodic"
+    gamma: float = 1.4
+    mu: float = 1e-3
+    pc_tol: float | None = None
+    pc_max_iter: int = 20
+    pc_fixed_iters: int = 0
+    tile_x: int = 0
+    tile_y: int = 0
+    halo: int = 0
+
+    def to_c(self) -> pond_config:
+        tol = self.pc_tol if self.pc_tol is not None else (1e-12 if self.precision == "fp64" else 1e-6)
+        return pond_config(nx=self.nx, ny=self.ny, lattice=self.lattice, split=SPLITS[self.split],
+                           precision=PRECISIONS[self.precision], interp_order=self.interp_order,
+                           bc_x=BCS[self.bc_x], bc_y=BCS[self.bc_y], gamma=self.gamma, mu=self.mu,
+                           pc_tol=tol, pc_max_iter=self.pc_max_iter,
+                           pc_fixed_iters=self.pc_fixed_iters, tile_x=self.tile_x,
+                           tile_y=self.tile_y, halo=self.halo)
+
+    @property
+    def Q(self) -> int:
+        return self.lattice
+
+
+def _dptr(t) -> int:
+    return int(t.data_ptr())
+
+
+class Simulation:
+    """One pond_sim with a caller-owned (PyTorch) device workspace."""
+
+    def __init__(self, cfg: Config, device="cuda:0", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpond needs a CUDA device")
+        self.torch = torch
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._c = cfg.to_c()
+        with torch.cuda.device(self.device):
+            self.ws_bytes = pond_workspace_bytes(self._c)
+            self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+            base = _dptr(self.workspace)
+            self._ws_ptr = (base + 255) // 256 * 256
+            self.handle = pond_create(self._c, self._ws_ptr, self.ws_bytes, self.stream.cuda_stream)
+
+    # -- state in -------------------------------------------------------------------------
+    def set_state(self, rho, ux, uy, T):
+        """Fields [ny][nx]: numpy (host copy inside the library) or CUDA tensors (float64)."""
+        torch = self.torch
+        shape = (self.cfg.ny, self.cfg.nx)
+        if isinstance(rho, torch.Tensor):
+            arrs = [a.to(device=self.device, dtype=torch.float64).contiguous().reshape(shape)
+                    for a in (rho, ux, uy, T)]
+            with torch.cuda.device(self.device):
+                rc = pond_set_state(self.handle, *[_dptr(a) for a in arrs], 1)
+                self._keep = arrs
+        else:
+            arrs = [np.ascontiguousarray(np.broadcast_to(a, shape), dtype=np.float64) for a in (rho, ux, uy, T)]
+            with torch.cuda.device(self.device):
+                rc = pond_set_state(self.handle, *[a.ctypes.data for a in arrs], 0)
+        _check(rc, "pond_set_state")
+
+    def set_populations(self, f, g, ux, uy, T):
+        """Populations [Q][ny][nx] in the frames (ux, uy, T) [ny][nx] (numpy or tensors)."""
+        torch = self.torch
+        Q = self.cfg.lattice
+        shape = (self.cfg.ny, self.cfg.nx)
+        def dev(a, s):
+            return torch.as_tensor(np.asarray(a) if not isinstance(a, torch.Tensor) else a,
+                                   dtype=torch.float64).to(self.device).contiguous().reshape(s)
+        arrs = [dev(f, (Q,) + shape), dev(g, (Q,) + shape)] + [dev(a, shape) for a in (ux, uy, T)]
+        with torch.cuda.device(self.device):
+            rc = pond_set_populations(self.handle, *[_dptr(a) for a in arrs], 1)
+            self.stream.synchronize()
+        _check(rc, "pond_set_populations")
+
+    # -- stepping -------------------------------------------------------------------------
+    def step(self, n: int = 1):
+        with self.torch.cuda.device(self.device):
+            _check(pond_step(self.handle, n), "pond_step")
+
+    # -- state out ------------------------------------------------------------------------
+    def moments(self, on_device: bool = False, allow=(POND_ENOCONV,)):
+        """(rho, ux, uy, T) as numpy arrays (host) or CUDA tensors (on_device)."""
+        torch = self.torch
+        shape = (self.cfg.ny, self.cfg.nx)
+        with torch.cuda.device(self.device):
+            if on_device:
+                out = [torch.empty(shape, dtype=torch.float64, device=self.device) for _ in range(4)]
+                rc = pond_get_moments(self.handle, *[_dptr(a) for a in out], 1)
+            else:
+                out = [np.empty(shape) for _ in range(4)]
+                rc = pond_get_moments(self.handle, *[a.ctypes.data for a in out], 0)
+        self.last_status = rc
+        _check(rc, "pond_get_moments", allow)
+        return tuple(out)
+
+    def populations(self, allow=(POND_ENOCONV,)):
+        """(f, g, ux, uy, T) as numpy arrays, each node in its own frame."""
+        torch = self.torch
+        Q = self.cfg.lattice
+        ny, nx = self.cfg.ny, self.cfg.nx
+        with torch.cuda.device(self.device):
+            f = torch.empty((Q, ny, nx), dtype=torch.float64, device=self.device)
+            g = torch.empty_like(f)
+            fr = [torch.empty((ny, nx), dtype=torch.float64, device=self.device) for _ in range(3)]
+            rc = pond_get_populations(self.handle, _dptr(f), _dptr(g), *[_dptr(a) for a in fr], 1)
+        self.last_status = rc
+        _check(rc, "pond_get_populations", allow)
+        return tuple(a.cpu().numpy() for a in [f, g] + fr)
+
+    def stats(self):
+        with self.torch.cuda.device(self.device):
+            rc, st = pond_get_stats(self.handle)
+        return rc, st
+
+    def sync(self):
+        with self.torch.cuda.device(self.device):
+            return pond_sync(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            with self.torch.cuda.device(self.device):
+                pond_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

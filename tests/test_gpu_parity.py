@@ -1,0 +1,208 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+FP64 mode in fixed-iteration predictor-corrector mode must match the oracle to a relative
+L-infinity error of 1e-12 per field (rel = max|gpu - oracle| / max|oracle|), on grids that
+span several tiles and leave ragged tails, with both boundary types, both lattices, both
+energy splits, both interpolation orders, the shared-memory and the global-gather (halo
+fallback) paths and degenerate grid shapes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pond():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_11489_gb300 import build, pond as P
+    build.build()
+    P.load_library()
+    return P
+
+
+def rel_linf(a, b):
+    scale = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0))
+
+
+def random_state(orc, ocfg, seed, amp=0.05, ux0=0.3, uy0=-0.2, T0=0.8, neq=0.01):
+    """Smooth random fields plus a random non-equilibrium part in each node's own frame."""
+    rng = np.random.default_rng(seed)
+    ny, nx = ocfg.ny, ocfg.nx
+    y, x = np.mgrid[0:ny, 0:nx]
+    def smooth(phase):
+        return (np.sin(2 * math.pi * (x / max(nx, 1) + phase[0])) *
+                np.cos(2 * math.pi * (y / max(ny, 1) + phase[1])))
+    rho = 1.0 + amp * smooth(rng.uniform(0, 1, 2)) + 0.2 * amp * rng.standard_normal((ny, nx))
+    ux = ux0 + amp * smooth(rng.uniform(0, 1, 2))
+    uy = uy0 + amp * smooth(rng.uniform(0, 1, 2))
+    T = T0 * (1 + amp * smooth(rng.uniform(0, 1, 2)))
+    st = orc.init_state(ocfg, rho, ux, uy, T)
+    Q = ocfg.q1 * ocfg.q1
+    st.f = st.f * (1 + neq * rng.standard_normal((Q, ny, nx)))
+    st.g = st.g * (1 + neq * rng.standard_normal((Q, ny, nx)))
+    return st
+
+
+def make_pair(pond, orc, nx, ny, lattice=16, split="total", order=3, bc=("periodic", "periodic"),
+              K=2, tol=1e-12, precision="fp64", halo=0, gamma=1.4, mu=0.02, maxit=20):
+    ocfg = orc.make_config(nx, ny, lattice=lattice, split=split, interp_order=order, bc_x=bc[0],
+                           bc_y=bc[1], gamma=gamma, mu=mu, pc_tol=tol, pc_max_iter=maxit,
+                           pc_fixed_iters=K)
+    gcfg = pond.Config(nx=nx, ny=ny, lattice=lattice, split=split, precision=precision,
+                       interp_order=order, bc_x=bc[0], bc_y=bc[1], gamma=gamma, mu=mu, pc_tol=tol,
+                       pc_max_iter=maxit, pc_fixed_iters=K, halo=halo)
+    return ocfg, pond.Simulation(gcfg)
+
+
+def vel_err(a, b, speed):
+    """Velocity components are compared on the flow's velocity scale (a component that is
+    zero in exact arithmetic has no relative error of its own)."""
+    return float(np.max(np.abs(a - b)) / speed)
+
+
+def compare(orc, ocfg, sim, st, tol, what=""):
+    rho, ux, uy, T, E = orc.moments(ocfg, st)
+    g_rho, g_ux, g_uy, g_T = sim.moments()
+    speed = max(np.max(np.abs(ux)), np.max(np.abs(uy)), np.sqrt(np.max(T)))
+    errs = {"rho": rel_linf(g_rho, rho), "ux": vel_err(g_ux, ux, speed),
+            "uy": vel_err(g_uy, uy, speed), "T": rel_linf(g_T, T)}
+    f, g, fux, fuy, fT = sim.populations()
+    errs["f"] = rel_linf(f, st.f)
+    errs["g"] = rel_linf(g, st.g)
+    errs["frame"] = max(vel_err(fux, st.ux, speed), vel_err(fuy, st.uy, speed), rel_linf(fT, st.T))
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, "%s: %s" % (what, errs)
+    return errs
+
+
+def run_both(orc, ocfg, sim, st, nsteps):
+    sim.set_populations(st.f, st.g, st.ux, st.uy, st.T)
+    for _ in range(nsteps):
+        st = orc.step(ocfg, st).state
+    sim.step(nsteps)
+    return st
+
+
+CASES = [
+    # nx, ny, lattice, split, order, bcs
+    (37, 11, 16, "total", 3, ("periodic", "periodic")),
+    (45, 9, 16, "total", 3, ("outflow", "outflow")),
+    (33, 6, 16, "internal", 3, ("periodic", "outflow")),
+    (29, 10, 25, "total", 3, ("periodic", "periodic")),
+    (26, 7, 25, "internal", 3, ("outflow", "periodic")),
+    (31, 9, 16, "total", 2, ("periodic", "periodic")),
+]
+
+
+@pytest.mark.parametrize("nx,ny,lattice,split,order,bc", CASES)
+def test_fp64_fixed_k_matches_oracle(pond, orc, nx, ny, lattice, split, order, bc):
+    ocfg, sim = make_pair(pond, orc, nx, ny, lattice, split, order, bc, K=3)
+    st = random_state(orc, ocfg, seed=nx * ny)
+    st = run_both(orc, ocfg, sim, st, 3)
+    compare(orc, ocfg, sim, st, FP64_TOL, "case %s" % ((nx, ny, lattice, split, order, bc),))
+    sim.close()
+
+
+def test_fp64_set_state_equilibrium_start(pond, orc):
+    ocfg, sim = make_pair(pond, orc, 40, 12, K=2)
+    rng = np.random.default_rng(5)
+    rho = 1 + 0.05 * rng.standard_normal((12, 40))
+    ux = 0.5 + 0.05 * rng.standard_normal((12, 40))
+    uy = -0.1 + 0.05 * rng.standard_normal((12, 40))
+    T = 0.7 + 0.02 * rng.standard_normal((12, 40))
+    st = orc.init_state(ocfg, rho, ux, uy, T)
+    sim.set_state(rho, ux, uy, T)
+    compare(orc, ocfg, sim, st, 1e-15, "init")
+    for _ in range(4):
+        st = orc.step(ocfg, st).state
+    sim.step(4)
+    compare(orc, ocfg, sim, st, FP64_TOL, "4 steps")
+    sim.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 2), (1, 7), (6, 1), (2, 33), (130, 1)])
+def test_fp64_degenerate_grids(pond, orc, nx, ny):
+    ocfg, sim = make_pair(pond, orc, nx, ny, K=2, bc=("periodic", "outflow"))
+    st = random_state(orc, ocfg, seed=7 + nx + ny)
+    st = run_both(orc, ocfg, sim, st, 2)
+    compare(orc, ocfg, sim, st, FP64_TOL, "grid %dx%d" % (nx, ny))
+    sim.close()
+
+
+def test_fp64_global_gather_fallback(pond, orc):
+    """A staged box too small for the stencils sends every population to the global-memory
+    gather path; the result must not change."""
+    ocfg, sim = make_pair(pond, orc, 40, 12, K=2, halo=1)
+    st = random_state(orc, ocfg, seed=3, ux0=1.5, T0=1.0)
+    st = run_both(orc, ocfg, sim, st, 2)
+    compare(orc, ocfg, sim, st, FP64_TOL, "fallback")
+    rc, stats = sim.stats()
+    assert stats.halo_fallbacks > 0
+    sim.close()
+
+
+def test_fp64_convergence_mode(pond, orc):
+    """Iterating to the tolerance: iteration counts may differ at the margin, results agree
+    to ~tolerance."""
+    ocfg, sim = make_pair(pond, orc, 36, 10, K=0, tol=1e-12, maxit=30)
+    st = random_state(orc, ocfg, seed=9)
+    sim.set_populations(st.f, st.g, st.ux, st.uy, st.T)
+    iters = 0
+    for _ in range(3):
+        r = orc.step(ocfg, st)
+        st = r.state
+        iters += int(r.iters.sum())
+    sim.step(3)
+    compare(orc, ocfg, sim, st, 1e-10, "converged")
+    rc, stats = sim.stats()
+    assert rc == 0
+    assert abs(stats.pc_iters_total - iters) <= 0.02 * iters
+    sim.close()
+
+
+def test_fp64_sod_400x4_matches_oracle(pond, orc):
+    """The Sod configuration (400 x 4, y periodic, x outflow), 400 steps, FP64."""
+    from paper_2405_11489_gb300 import workloads as W
+    c = W.sod(nx=400, ny=4, mu=1e-4 * 0.2 * 400)
+    ocfg = orc.make_config(c.nx, c.ny, gamma=c.gamma, mu=c.mu, bc_x=c.bc_x, bc_y=c.bc_y,
+                           pc_fixed_iters=3)
+    st = orc.init_state(ocfg, c.rho, c.ux, c.uy, c.T)
+    sim = pond.Simulation(pond.Config(nx=c.nx, ny=c.ny, precision="fp64", gamma=c.gamma, mu=c.mu,
+                                      bc_x=c.bc_x, bc_y=c.bc_y, pc_fixed_iters=3))
+    sim.set_state(c.rho, c.ux, c.uy, c.T)
+    for _ in range(c.steps):
+        st = orc.step(ocfg, st).state
+    sim.step(c.steps)
+    compare(orc, ocfg, sim, st, 1e-11, "sod")
+    sim.close()
+
+
+def test_nonphysical_state_is_reported(pond, orc):
+    ocfg, sim = make_pair(pond, orc, 12, 8, K=2)
+    st = random_state(orc, ocfg, seed=4)
+    sim.set_populations(st.f, -st.g, st.ux, st.uy, st.T)   # negative energy -> T < 0
+    sim.step(1)
+    rc, stats = sim.stats()
+    assert rc == pond.POND_ENONPHYSICAL and stats.first_bad_node >= 0
+    with pytest.raises(pond.PondError):
+        sim.set_state(np.ones((8, 12)), np.zeros((8, 12)), np.zeros((8, 12)), -np.ones((8, 12)))
+    sim.close()
+
+
+def test_nonconvergence_is_reported(pond, orc):
+    ocfg, sim = make_pair(pond, orc, 12, 8, K=0, tol=0.0, maxit=2)
+    st = random_state(orc, ocfg, seed=6)
+    sim.set_populations(st.f, st.g, st.ux, st.uy, st.T)
+    sim.step(1)
+    rc, stats = sim.stats()
+    assert rc == pond.POND_ENOCONV and stats.nonconv_updates == 12 * 8
+    assert stats.pc_iters_max == 2
+    sim.close()
