@@ -62,8 +62,9 @@ typedef struct {
     int32_t lattice;           /* POND_D2Q16 (default) or POND_D2Q25 */
     int32_t split;             /* POND_SPLIT_TOTAL (default) or POND_SPLIT_INTERNAL */
     int32_t precision;         /* POND_FP64: FP64 storage and arithmetic.  POND_MIXED_*:
-                                  FP32 arithmetic, FP64 rho/u/T, moment sums compensated,
-                                  non-equilibrium state stored in FP32 / FP16 / BF16 */
+                                  FP32 arithmetic on deviations from a per-tile reference
+                                  equilibrium, FP64 rho/u/T and frame update, non-equilibrium
+                                  state stored in FP32 / FP16 / BF16 */
     int32_t interp_order;      /* 3: 4-point cubic Lagrange (default); 2: 3-point (Sec. III.A.2) */
     int32_t bc_x, bc_y;        /* POND_BC_PERIODIC (index mod n) or POND_BC_OUTFLOW (clamp) */
     double gamma;              /* adiabatic exponent, 1 < gamma <= 2 (c_v = 1/(gamma - 1)) */
@@ -71,8 +72,11 @@ typedef struct {
     double pc_tol;             /* predictor-corrector tolerance on max(|du|/sqrt(T), |dT|/T) */
     int32_t pc_max_iter;       /* iteration cap (1..64) */
     int32_t pc_fixed_iters;    /* > 0: exactly this many iterations, no tolerance test */
-    int32_t tile_x, tile_y;    /* 0 = automatic; otherwise threads per block in x and y */
-    int32_t halo;              /* 0 = automatic; staged halo cells per side (>= 3) */
+    int32_t tile_x, tile_y;    /* 0 = automatic (32 x 8; 256 x 1 when ny = 1); otherwise the
+                                  tile in nodes, tile_x * tile_y = 256 */
+    int32_t halo;              /* 0 = automatic (5); the staged box is the tile plus
+                                  2 * halo + 2 nodes per axis; stencils outside it are read
+                                  from global memory (slower, same result) */
 } pond_config;
 
 typedef struct {
@@ -93,7 +97,7 @@ typedef struct pond_sim pond_sim;
 int pond_config_default(pond_config *cfg, int32_t nx, int32_t ny);
 
 /* Bytes of device workspace a simulation with this configuration needs (two copies of the
- * state, a moment staging area and a status block).  For admission by free HBM. */
+ * state, see pond_state_bytes, and a status block).  For admission by free HBM. */
 int pond_workspace_bytes(const pond_config *cfg, size_t *bytes);
 
 /* Create a simulation on the current device.  dev_workspace: caller-owned device memory
@@ -113,7 +117,8 @@ int pond_set_state(pond_sim *sim, const double *rho, const double *ux, const dou
 
 /* Set populations directly: f, g [Q][ny][nx] in the frames (ux, uy, T) [ny][nx].  The
  * library keeps their Hermite coefficients up to total order 3 in each node's frame, which
- * is all that the frame transformation (N = 3) passes on.  Host or device pointers. */
+ * is all that the frame transformation (N = 3) passes on.  Device pointers only
+ * (on_device must be 1, else POND_EINVAL).  Resets statistics and the sticky status. */
 int pond_set_populations(pond_sim *sim, const double *f, const double *g, const double *ux,
                          const double *uy, const double *T, int on_device);
 
@@ -127,9 +132,22 @@ int pond_get_moments(pond_sim *sim, double *rho, double *ux, double *uy, double 
                      int on_device);
 
 /* Current populations f, g [Q][ny][nx] and their frames (ux, uy, T) [ny][nx], each node in
- * its own frame.  Synchronises; returns the sticky status. */
+ * its own frame (f_i = w_i sum A_pq He_p(c_ia) He_q(c_ib) / (p! q!)).  Device pointers only
+ * (on_device must be 1).  Synchronises; returns the sticky status. */
 int pond_get_populations(pond_sim *sim, double *f, double *g, double *ux, double *uy,
                          double *T, int on_device);
+
+/* Raw state (checkpoint / resume).  The state is mac = [4][ny][nx] FP64 (rho, u_x, u_y, T) and
+ * neq = [19][ny][nx] in the storage type of cfg->precision (8, 4, 2 or 2 bytes): the
+ * non-equilibrium Hermite coefficients of total order <= 3 of f (A_10, A_01, A_20, A_11, A_02,
+ * A_30, A_21, A_12, A_03) and of g (B_pq - B_pq^eq for (p,q) = 00, 10, 01, 20, 11, 02, 30, 21,
+ * 12, 03) in each node's own frame, A_pq = sum_i f_i He_p(c_ia) He_q(c_ib) (Sec. III.A.1).
+ * pond_state_bytes gives the two array sizes.  Export copies the current state into the
+ * caller's buffers (host or device) and synchronises; import copies it in (statistics and
+ * sticky status reset).  A checkpoint resumes bit-identically on the same build. */
+int pond_state_bytes(const pond_config *cfg, size_t *mac_bytes, size_t *neq_bytes);
+int pond_export_state(pond_sim *sim, double *mac, void *neq, int on_device);
+int pond_import_state(pond_sim *sim, const double *mac, const void *neq, int on_device);
 
 /* Statistics since the last pond_set_state*.  Synchronises; returns the sticky status. */
 int pond_get_stats(pond_sim *sim, pond_stats *stats);

@@ -268,7 +268,7 @@ int pond_create(const pond_config* cfg, void* dev_workspace, size_t bytes, void*
         s->tx = cfg->tile_x ? cfg->tile_x : 32;
         s->ty = cfg->tile_y ? cfg->tile_y : kStepThreads / 32;
     }
-    const int extent = cfg->halo ? 2 * cfg->halo + 2 : 12;
+    const int extent = 2 * (cfg->halo ? cfg->halo : 5) + 2;
     s->box_w = s->tx + extent;
     s->box_h = s->one_d ? 1 : s->ty + extent;
     const size_t rbytes = cfg->precision == POND_FP64 ? 8 : 4;
@@ -413,6 +413,43 @@ int pond_get_populations(pond_sim* s, double* f, double* g, double* ux, double* 
     return sync_status(s);
 }
 
+int pond_state_bytes(const pond_config* cfg, size_t* mac_bytes, size_t* neq_bytes)
+{
+    int rc = check_config(cfg);
+    if (rc != POND_OK) return rc;
+    if (!mac_bytes || !neq_bytes) return POND_EINVAL;
+    const size_t N = (size_t)cfg->nx * (size_t)cfg->ny;
+    *mac_bytes = NMAC * N * sizeof(double);
+    *neq_bytes = NNEQ * N * storage_bytes(cfg->precision);
+    return POND_OK;
+}
+
+int pond_export_state(pond_sim* s, double* mac, void* neq, int on_device)
+{
+    if (!s || !mac || !neq) return POND_EINVAL;
+    size_t mb = 0, nb = 0;
+    pond_state_bytes(&s->cfg, &mb, &nb);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpyAsync(mac, mac_ptr(s, s->cur), mb, kind, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(neq, neq_ptr(s, s->cur), nb, kind, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return sync_status(s);
+}
+
+int pond_import_state(pond_sim* s, const double* mac, const void* neq, int on_device)
+{
+    if (!s || !mac || !neq) return POND_EINVAL;
+    size_t mb = 0, nb = 0;
+    pond_state_bytes(&s->cfg, &mb, &nb);
+    int rc = reset_status(s);
+    if (rc != POND_OK) return rc;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(mac_ptr(s, s->cur), mac, mb, kind, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(neq_ptr(s, s->cur), neq, nb, kind, s->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s->stream);
+    return cuda_status(e);
+}
+
 int pond_get_stats(pond_sim* s, pond_stats* st)
 {
     if (!s || !st) return POND_EINVAL;
@@ -446,3 +483,4 @@ int pond_destroy(pond_sim* s)
 }
 
 }  // extern "C"
+

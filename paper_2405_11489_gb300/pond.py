@@ -35,7 +35,8 @@ BCS = {"periodic": POND_BC_PERIODIC, "outflow": POND_BC_OUTFLOW}
 # Symbols the header declares (checked by the ABI test).
 EXPORTS = ("pond_config_default", "pond_workspace_bytes", "pond_create", "pond_set_state",
            "pond_set_populations", "pond_step", "pond_get_moments", "pond_get_populations",
-           "pond_get_stats", "pond_sync", "pond_destroy", "pond_strerror", "pond_version")
+           "pond_get_stats", "pond_sync", "pond_destroy", "pond_strerror", "pond_version",
+           "pond_state_bytes", "pond_export_state", "pond_import_state")
 
 
 class pond_config(ctypes.Structure):
@@ -87,6 +88,9 @@ def load_library(path: str = LIB_PATH):
         lib.pond_get_stats.argtypes = [vp, P(pond_stats)]
         lib.pond_sync.argtypes = [vp]
         lib.pond_destroy.argtypes = [vp]
+        lib.pond_state_bytes.argtypes = [P(pond_config), P(sz), P(sz)]
+        lib.pond_export_state.argtypes = [vp, vp, vp, ctypes.c_int]
+        lib.pond_import_state.argtypes = [vp, vp, vp, ctypes.c_int]
         lib.pond_strerror.argtypes = [ctypes.c_int]
         lib.pond_strerror.restype = ctypes.c_char_p
         lib.pond_version.restype = ctypes.c_char_p
@@ -156,6 +160,21 @@ def pond_get_stats(h):
     st = pond_stats()
     rc = load_library().pond_get_stats(h, ctypes.byref(st))
     return rc, st
+
+
+def pond_state_bytes(cfg: pond_config):
+    m, n = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(load_library().pond_state_bytes(ctypes.byref(cfg), ctypes.byref(m), ctypes.byref(n)),
+           "pond_state_bytes")
+    return m.value, n.value
+
+
+def pond_export_state(h, mac, neq, on_device: int) -> int:
+    return load_library().pond_export_state(h, mac, neq, on_device)
+
+
+def pond_import_state(h, mac, neq, on_device: int) -> int:
+    return load_library().pond_import_state(h, mac, neq, on_device)
 
 
 def pond_sync(h) -> int:
@@ -290,6 +309,34 @@ class Simulation:
         self.last_status = rc
         _check(rc, "pond_get_populations", allow)
         return tuple(a.cpu().numpy() for a in [f, g] + fr)
+
+    def export_state(self, on_device: bool = True):
+        """Raw state (checkpoint): (mac, neq) as uint8 CUDA tensors (or numpy arrays)."""
+        torch = self.torch
+        mb, nb = pond_state_bytes(self._c)
+        with torch.cuda.device(self.device):
+            if on_device:
+                mac = torch.empty(mb, dtype=torch.uint8, device=self.device)
+                neq = torch.empty(nb, dtype=torch.uint8, device=self.device)
+                rc = pond_export_state(self.handle, _dptr(mac), _dptr(neq), 1)
+            else:
+                mac = np.empty(mb, dtype=np.uint8)
+                neq = np.empty(nb, dtype=np.uint8)
+                rc = pond_export_state(self.handle, mac.ctypes.data, neq.ctypes.data, 0)
+        _check(rc, "pond_export_state", (POND_ENOCONV,))
+        return mac, neq
+
+    def import_state(self, mac, neq):
+        torch = self.torch
+        with torch.cuda.device(self.device):
+            if isinstance(mac, torch.Tensor):
+                rc = pond_import_state(self.handle, _dptr(mac), _dptr(neq), 1)
+                self.stream.synchronize()
+            else:
+                mac = np.ascontiguousarray(mac)
+                neq = np.ascontiguousarray(neq)
+                rc = pond_import_state(self.handle, mac.ctypes.data, neq.ctypes.data, 0)
+        _check(rc, "pond_import_state")
 
     def stats(self):
         with self.torch.cuda.device(self.device):

@@ -206,3 +206,29 @@ def test_nonconvergence_is_reported(pond, orc):
     assert rc == pond.POND_ENOCONV and stats.nonconv_updates == 12 * 8
     assert stats.pc_iters_max == 2
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_resume_is_bit_identical(pond, orc, precision):
+    """Export after 3 steps, import into a fresh simulation, 3 more steps: identical to 6
+    straight steps (device and host checkpoints)."""
+    from paper_2405_11489_gb300 import workloads as W
+    c = W.shear_wave(n=48, ny=20, ma=1.0, amp=0.05, mu=0.05)
+    cfg = pond.Config(nx=c.nx, ny=c.ny, precision=precision, mu=c.mu)
+    a = pond.Simulation(cfg)
+    a.set_state(c.rho, c.ux, c.uy, c.T)
+    a.step(6)
+    ref = a.moments()
+    for on_device in (True, False):
+        b = pond.Simulation(cfg)
+        b.set_state(c.rho, c.ux, c.uy, c.T)
+        b.step(3)
+        mac, neq = b.export_state(on_device=on_device)
+        b.close()
+        d = pond.Simulation(cfg)
+        d.import_state(mac, neq)
+        d.step(3)
+        for x, y in zip(d.moments(), ref):
+            assert np.array_equal(x, y)
+        d.close()
+    a.close()
