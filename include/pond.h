@@ -158,6 +158,34 @@ int pond_sync(pond_sim *sim);
 /* Free the handle (not the caller's workspace).  Waits for queued work first. */
 int pond_destroy(pond_sim *sim);
 
+/* Allocation-free stepping.  (No counterpart in the paper: this is plumbing for callers.)
+ *
+ * Some callers cannot allocate device memory: an application that owns all GPU memory
+ * through its own pool and forbids any other allocation; a real-time loop that cannot
+ * afford the latency and implicit device synchronisation of cudaMalloc; a plugin or
+ * foreign-language host that holds only the state buffers it was given.  Such a caller
+ * cannot provide the workspace that pond_create needs.  pond_step_static advances nsteps
+ * time steps of a raw state (the layout of pond_state_bytes / pond_export_state) that lives
+ * in the caller's own device buffers mac and neq, in place, on cuda_stream, with the same
+ * kernels as pond_step, and allocates nothing: the second copy of the state and the status
+ * block live in one file-scope device array of the library, POND_STATIC_SCRATCH_BYTES
+ * (16 MiB) on every GPU that loads the library, held until the process exits.
+ *  - Size limit: the state must fit that array, state bytes = align256(4*8*N) +
+ *    align256(19*s*N) + 256 with N = nx*ny and s = 8/4/2/2 bytes (FP64/FP32/FP16/BF16),
+ *    i.e. N <= 91 178 (FP64), 155 341 (FP32), 239 669 (FP16/BF16); larger grids return
+ *    POND_ENOMEM without touching the GPU.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) and sets the step kernel's shared-memory limit; make that first
+ *    call before any stream capture on that device.
+ *  - Every call uses the same array and it keeps the last call's contents; the status
+ *    block is cleared at the start of each call.  Calls that overlap on the GPU (other
+ *    streams, other host threads) race on the array: serialise them.
+ *  - stats: if non-NULL the call synchronises cuda_stream, fills *stats for this call and
+ *    returns the sticky status; if NULL it returns once the work is enqueued. */
+#define POND_STATIC_SCRATCH_BYTES (16u << 20)
+int pond_step_static(const pond_config *cfg, double *mac, void *neq, int32_t nsteps,
+                     void *cuda_stream, pond_stats *stats);
+
 /* Static description of a status code. */
 const char *pond_strerror(int status);
 

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "pond.h"
@@ -484,3 +485,149 @@ int pond_destroy(pond_sim* s)
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free stepping (pond_step_static): the second copy of the state and the status
+// block live in this file-scope device array instead of a caller workspace.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_pond_static_scratch[POND_STATIC_SCRATCH_BYTES];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_address[kStaticMaxDevices];   // device address of the array, per device
+
+// Set-up, once per device with that device current: the array's name is a host-side
+// stand-in, so its device address must be looked up before a kernel can be given it.
+int static_scratch(int dev, void** out)
+{
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_address[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_pond_static_scratch);
+        if (e != cudaSuccess || !p) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
+        g_static_address[dev] = p;
+    }
+    *out = g_static_address[dev];
+    return POND_OK;
+}
+
+}  // namespace
+
+extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, int32_t nsteps,
+                                void* cuda_stream, pond_stats* stats)
+{
+    int rc = check_config(cfg);
+    if (rc != POND_OK) return rc;
+    if (!mac || !neq || nsteps < 0) return POND_EINVAL;
+    size_t mb = 0, nb = 0;
+    pond_state_bytes(cfg, &mb, &nb);
+    const size_t off_neq = align_up(mb), off_status = off_neq + align_up(nb);
+    if (off_status + align_up(sizeof(DevStatus)) > (size_t)POND_STATIC_SCRATCH_BYTES) return POND_ENOMEM;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= kStaticMaxDevices) return POND_EINVAL;
+    void* base = nullptr;
+    rc = static_scratch(dev, &base);
+    if (rc != POND_OK) return rc;
+    char* scratch = reinterpret_cast<char*>(base);
+    double* smac = reinterpret_cast<double*>(scratch);
+    void* sneq = scratch + off_neq;
+    DevStatus* st = reinterpret_cast<DevStatus*>(scratch + off_status);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+
+    // launch shape of the step kernel, as pond_create chooses it
+    const bool one_d = (cfg->ny == 1);
+    const int tx = one_d ? kStepThreads : (cfg->tile_x ? cfg->tile_x : 32);
+    const int ty = one_d ? 1 : (cfg->tile_y ? cfg->tile_y : kStepThreads / 32);
+    const int extent = 2 * (cfg->halo ? cfg->halo : 5) + 2;
+    const int box_w = tx + extent, box_h = one_d ? 1 : ty + extent;
+    const size_t smem = (size_t)box_w * box_h * 2 * NCOEF * (cfg->precision == POND_FP64 ? 8 : 4);
+    int smem_optin = 0;
+    e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (smem + 1024 > (size_t)smem_optin) return POND_EINVAL;
+    const Lattice lat = make_lattice(cfg->lattice == POND_D2Q16 ? 4 : 5);
+    e = kSmem[cfg->precision][lat.q1 == 5][one_d](cfg->interp_order, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+
+    // the array keeps the previous call's contents: clear the status block
+    e = cudaMemsetAsync(st, 0, sizeof(DevStatus), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&st->first_bad, 0xff, sizeof(st->first_bad), stream);
+    if (e != cudaSuccess) return cuda_status(e);
+
+    const long long N = (long long)cfg->nx * cfg->ny;
+    StepParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.lat = lat;
+    p.nx = cfg->nx;
+    p.ny = cfg->ny;
+    p.bc_x = cfg->bc_x;
+    p.bc_y = cfg->bc_y;
+    p.split = cfg->split;
+    p.pc_max_iter = cfg->pc_max_iter;
+    p.pc_fixed = cfg->pc_fixed_iters;
+    p.box_w = box_w;
+    p.box_h = box_h;
+    p.N = N;
+    p.cv = 1.0 / (cfg->gamma - 1.0);
+    p.inv_cv = cfg->gamma - 1.0;
+    p.mu = cfg->mu;
+    p.pc_tol = cfg->pc_tol;
+    p.status = st;
+    Launch l;
+    l.block = dim3(tx, ty, 1);
+    l.grid = dim3((cfg->nx + tx - 1) / tx, (cfg->ny + ty - 1) / ty, 1);
+    l.smem = smem;
+    l.stream = stream;
+    AuxParams a;
+    std::memset(&a, 0, sizeof(a));
+    a.lat = lat;
+    a.nx = cfg->nx;
+    a.ny = cfg->ny;
+    a.bc_x = cfg->bc_x;
+    a.bc_y = cfg->bc_y;
+    a.split = cfg->split;
+    a.N = N;
+    a.cv = p.cv;
+    a.status = st;
+    // ping-pong between the caller's buffers and the array
+    for (int k = 0; k < nsteps; ++k) {
+        const bool from_caller = (k % 2 == 0);
+        p.mac_in = from_caller ? mac : smac;
+        p.neq_in = from_caller ? neq : sneq;
+        p.mac_out = from_caller ? smac : mac;
+        p.neq_out = from_caller ? sneq : neq;
+        e = kStep[cfg->precision][lat.q1 == 5][one_d](p, cfg->interp_order, l);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (cfg->split == POND_SPLIT_INTERNAL) {
+            a.mac = p.mac_out;
+            a.neq = p.neq_out;
+            a.mac_prev = p.mac_in;
+            e = POND_BY_PRECISION(cfg->precision, internal_source, a, stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+    }
+    if (nsteps % 2 == 1) {   // the last step wrote into the array: copy the result back
+        e = cudaMemcpyAsync(mac, smac, mb, cudaMemcpyDeviceToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(neq, sneq, nb, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (!stats) return POND_OK;
+    DevStatus h;
+    e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    std::memset(stats, 0, sizeof(*stats));
+    stats->steps = nsteps;
+    stats->node_updates = (int64_t)nsteps * N;
+    stats->pc_iters_total = (int64_t)h.iters_total;
+    stats->pc_iters_max = (int32_t)h.iters_max;
+    stats->nonconv_updates = (int64_t)h.nonconv;
+    stats->first_bad_node = h.first_bad == ~0ull ? -1 : (int64_t)h.first_bad;
+    stats->halo_fallbacks = (int64_t)h.fallbacks;
+    stats->status = (h.flags & 1) ? POND_ENONPHYSICAL : (h.flags & 2) ? POND_ENOCONV : POND_OK;
+    return stats->status;
+}

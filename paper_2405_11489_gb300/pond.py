@@ -36,7 +36,7 @@ BCS = {"periodic": POND_BC_PERIODIC, "outflow": POND_BC_OUTFLOW}
 EXPORTS = ("pond_config_default", "pond_workspace_bytes", "pond_create", "pond_set_state",
            "pond_set_populations", "pond_step", "pond_get_moments", "pond_get_populations",
            "pond_get_stats", "pond_sync", "pond_destroy", "pond_strerror", "pond_version",
-           "pond_state_bytes", "pond_export_state", "pond_import_state")
+           "pond_state_bytes", "pond_export_state", "pond_import_state", "pond_step_static")
 
 
 class pond_config(ctypes.Structure):
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         lib.pond_state_bytes.argtypes = [P(pond_config), P(sz), P(sz)]
         lib.pond_export_state.argtypes = [vp, vp, vp, ctypes.c_int]
         lib.pond_import_state.argtypes = [vp, vp, vp, ctypes.c_int]
+        lib.pond_step_static.argtypes = [P(pond_config), vp, vp, i32, vp, P(pond_stats)]
         lib.pond_strerror.argtypes = [ctypes.c_int]
         lib.pond_strerror.restype = ctypes.c_char_p
         lib.pond_version.restype = ctypes.c_char_p
@@ -175,6 +176,18 @@ def pond_export_state(h, mac, neq, on_device: int) -> int:
 
 def pond_import_state(h, mac, neq, on_device: int) -> int:
     return load_library().pond_import_state(h, mac, neq, on_device)
+
+
+def pond_step_static(cfg: pond_config, mac_ptr: int, neq_ptr: int, nsteps: int, stream_ptr: int,
+                     want_stats: bool = True):
+    """Advance a raw state held in the caller's device buffers in place, allocating nothing
+    (the library's static device array holds the second state copy); returns (rc, stats)."""
+    st = pond_stats()
+    rc = load_library().pond_step_static(ctypes.byref(cfg), ctypes.c_void_p(mac_ptr),
+                                         ctypes.c_void_p(neq_ptr), nsteps,
+                                         ctypes.c_void_p(stream_ptr),
+                                         ctypes.byref(st) if want_stats else None)
+    return rc, st
 
 
 def pond_sync(h) -> int:
