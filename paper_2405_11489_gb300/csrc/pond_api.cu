@@ -272,8 +272,8 @@ int pond_create(const pond_config* cfg, void* dev_workspace, size_t bytes, void*
     const int extent = 2 * (cfg->halo ? cfg->halo : 5) + 2;
     s->box_w = s->tx + extent;
     s->box_h = s->one_d ? 1 : s->ty + extent;
-    const size_t rbytes = cfg->precision == POND_FP64 ? 8 : 4;
-    s->smem = (size_t)s->box_w * s->box_h * 2 * NCOEF * rbytes;
+    const int rbytes = cfg->precision == POND_FP64 ? 8 : 4;
+    s->smem = step_smem_bytes(rbytes, s->lat.q1, s->one_d, s->box_w, s->box_h, kStepThreads);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     int smem_optin = 0;
@@ -544,7 +544,8 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     const int ty = one_d ? 1 : (cfg->tile_y ? cfg->tile_y : kStepThreads / 32);
     const int extent = 2 * (cfg->halo ? cfg->halo : 5) + 2;
     const int box_w = tx + extent, box_h = one_d ? 1 : ty + extent;
-    const size_t smem = (size_t)box_w * box_h * 2 * NCOEF * (cfg->precision == POND_FP64 ? 8 : 4);
+    const size_t smem = step_smem_bytes(cfg->precision == POND_FP64 ? 8 : 4, cfg->lattice == POND_D2Q16 ? 4 : 5,
+                                        one_d, box_w, box_h, kStepThreads);
     int smem_optin = 0;
     e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return cuda_status(e);

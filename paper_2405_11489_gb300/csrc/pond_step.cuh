@@ -5,11 +5,7 @@
 //    departure points of its nodes), moves that node's Hermite coefficients of order <= 3
 //    into lambda_r (Eq. gradGeneralTransform, via the re-centring matrices) and stores, in
 //    shared memory, their DEVIATION from the reference node's equilibrium coefficients
-//    K = (rho_r, 0, ...) for f and B_eq(rho_r, u_r, T_r) for g.  Every large difference of
-//    equilibrium-dominated quantities (rho_s - rho_r, E_s - E_r, p_s u_s - p_r u_r,
-//    p_s T_s - p_r T_r) is formed in FP64; the rest are products of small shifts and are
-//    formed in the working precision R.  So in mixed precision the FP32 values carry only
-//    deviations, and the reference part is added back in FP64.
+//    K = (rho_r, 0, ...) for f and B_eq(rho_r, u_r, T_r) for g.
 // 2. Predictor-corrector (frame lambda_bar, guess = the node's previous frame).  For each
 //    population i = (a, b): departure point x - C_i(lambda_bar) dt, Lagrange weights,
 //    interpolation of the staged deviations (Eq. propagationInterpolated; the transform is
@@ -23,6 +19,17 @@
 //    their moments lambda* (reference part analytically, deviation part by re-centring) and
 //    relaxed there (BGK, tau = mu/p, omega = 1/(tau + 1/2)); rho, u*, T* (FP64) and the
 //    non-equilibrium coefficients are written.
+//
+// Precision.  rho, u, T are FP64 in memory.  Only their differences from the reference
+// (rho_s - rho_r, u_s - u_r, T_s - T_r) and the frame corrections are formed with FP64 adds;
+// every other large difference (E_s - E_r, p_s u_s - p_r u_r, p_s T_s - p_r T_r, the new
+// temperature) is expanded into products of those small differences with O(1) values and
+// evaluated in the working precision R, so in mixed precision FP32 only ever carries
+// deviations and no FP64 multiply, divide or square root is needed in the loops.
+//
+// Interpolation.  FP32 (shared-memory bound): for each a, the x pass is done once per row of
+// the union of the y stencils of all b and then added to the b's whose y stencil contains
+// the row.  FP64 (FP64-pipe bound): each population is interpolated directly.
 //
 // A stencil that leaves the staged box (a frame far outside the per-tile estimate) is read
 // from global memory instead, node by node, and counted.
@@ -45,12 +52,23 @@ struct StepParams {
     DevStatus* status;
 };
 
-// Tile reference state: the centre node's frame and its equilibrium-derived scalars (FP64).
+// Tile reference state: the centre node's frame (FP64) and derived values in R.
 template <class R>
 struct RefState {
-    double rho, ux, uy, T, E, P, PT, Pux, Puy;   // P = rho T; E = B_00^eq
-    double invT;                                 // 1 / T
-    R isT, invTR;                                // 1/sqrt(T), 1/T in R
+    double rho, ux, uy, T;
+    R rhoR, uxR, uyR, TR;
+    R ER;       // E_r (total split) or U_r (internal split) = B_00^eq of the reference node
+    R PR;       // p_r = rho_r T_r
+    R eR;       // E_r / rho_r (total) or c_v T_r (internal)
+    R isT;      // 1 / sqrt(T_r)
+    R invT;     // 1 / T_r
+    R cvR;
+};
+
+// Base frame of a moved equilibrium (see add_g_eq_dev): its pressure and 1/sqrt(T), 1/T.
+template <class R>
+struct BaseFrame {
+    R P, isT, invT;
 };
 
 // 1-D re-centring matrix with an accurately formed sigma = s^2 - 1 (see make_tau).
@@ -77,33 +95,66 @@ __device__ __forceinline__ R sqrt_r(R v)
     if constexpr (std::is_same<R, double>::value) return sqrt(v); else return sqrtf(v);
 }
 
-// 1/x for x > 0 to FP64 accuracy without a double division: FP32 estimate, two Newton steps.
-__device__ __forceinline__ double rcp64(double x)
+// g equilibrium of a node (Sec. II g_eq in its own frame), moved into a base frame by tx, ty,
+// minus the equilibrium of the base frame itself, for the slots (p,q) != (0,0) plus dE at
+// (0,0).  Added into G.  Node values: E or U (ES), p (PS), u (uxS, uyS), T (TS); differences
+// node - base: dP, dux, duy, dT; moving shifts dx, dy = (u - u_base)/sqrt(T_base) and
+// sig = T/T_base - 1.  Every term is a product of small differences with O(1) values.
+template <class R>
+__device__ __forceinline__ void add_g_eq_dev(int split, const BaseFrame<R>& bf, const Tau<R>& tx,
+                                             const Tau<R>& ty, R dx, R dy, R sig, R ES, R dE, R PS,
+                                             R uxS, R uyS, R dP, R dux, R duy, R TS, R dT, R* G)
 {
-    double r = (double)(1.0f / (float)x);
-    r = r * (2.0 - x * r);
-    r = r * (2.0 - x * r);
-    return r;
+    const R dPT = dP * TS + bf.P * dT;                    // p T - p_b T_b
+    const R PsR = PS * (R(1) + sig);                      // s^2 p
+    if (split == 0) {
+        const R PuxR = PS * uxS * bf.isT, PuyR = PS * uyS * bf.isT;   // s b10, s b01
+        const R dPux = dP * uxS + bf.P * dux;             // p u - p_b u_b
+        const R dPuy = dP * uyS + bf.P * duy;
+        G[slot(0, 0)] += dE;
+        G[slot(1, 0)] += dx * ES + dPux * bf.isT;
+        G[slot(0, 1)] += dy * ES + dPuy * bf.isT;
+        G[slot(2, 0)] += tx.t20 * ES + R(2) * dx * PuxR + dPT * bf.invT;
+        G[slot(0, 2)] += ty.t20 * ES + R(2) * dy * PuyR + dPT * bf.invT;
+        G[slot(1, 1)] += dx * dy * ES + dx * PuyR + dy * PuxR;
+        G[slot(3, 0)] += tx.t30 * ES + R(3) * tx.t20 * PuxR + R(3) * dx * PsR;
+        G[slot(0, 3)] += ty.t30 * ES + R(3) * ty.t20 * PuyR + R(3) * dy * PsR;
+        G[slot(2, 1)] += tx.t20 * dy * ES + tx.t20 * PuyR + R(2) * dx * dy * PuxR + dy * PsR;
+        G[slot(1, 2)] += ty.t20 * dx * ES + ty.t20 * PuxR + R(2) * dx * dy * PuyR + dx * PsR;
+    } else {
+        G[slot(0, 0)] += dE;
+        G[slot(1, 0)] += dx * ES;
+        G[slot(0, 1)] += dy * ES;
+        G[slot(2, 0)] += tx.t20 * ES + dPT * bf.invT;
+        G[slot(0, 2)] += ty.t20 * ES + dPT * bf.invT;
+        G[slot(1, 1)] += dx * dy * ES;
+        G[slot(3, 0)] += tx.t30 * ES + R(3) * dx * PsR;
+        G[slot(0, 3)] += ty.t30 * ES + R(3) * dy * PsR;
+        G[slot(2, 1)] += tx.t20 * dy * ES + dy * PsR;
+        G[slot(1, 2)] += ty.t20 * dx * ES + dx * PsR;
+    }
 }
 
 // Deviation of node nd's coefficients, moved into the reference frame, from the reference
-// node's equilibrium coefficients.
+// node's equilibrium coefficients (f into Df, g into Dg).
 template <class S, class R>
 __device__ __forceinline__ void source_dev(const StepParams& p, const RefState<R>& rf, long long nd,
                                            R* Df, R* Dg)
 {
     const long long N = p.N;
     const S* neq = reinterpret_cast<const S*>(p.neq_in);
-    const double rho = p.mac_in[nd], ux = p.mac_in[N + nd], uy = p.mac_in[2 * N + nd];
-    const double T = p.mac_in[3 * N + nd];
-    // shifts of this node's frame relative to the reference frame
-    const R dx = R(ux - rf.ux) * rf.isT;
-    const R dy = R(uy - rf.uy) * rf.isT;
-    const R sig = R(T - rf.T) * rf.invTR;            // T/T_r - 1
-    const R s = sqrt_r<R>(R(1) + sig);               // sqrt(T/T_r)
+    // the only FP64 operations: differences of the primitive variables from the reference
+    const R drho = R(p.mac_in[nd] - rf.rho);
+    const R dux = R(p.mac_in[N + nd] - rf.ux);
+    const R duy = R(p.mac_in[2 * N + nd] - rf.uy);
+    const R dT = R(p.mac_in[3 * N + nd] - rf.T);
+    const R rhoS = rf.rhoR + drho, uxS = rf.uxR + dux, uyS = rf.uyR + duy, TS = rf.TR + dT;
+    const R dx = dux * rf.isT, dy = duy * rf.isT;
+    const R sig = dT * rf.invT;                       // T/T_r - 1
+    const R s = sqrt_r<R>(R(1) + sig);                // sqrt(T/T_r)
     const Tau<R> tx = make_tau_sig<R>(s, dx, sig);
     const Tau<R> ty = make_tau_sig<R>(s, dy, sig);
-    // non-equilibrium parts, moved (small numbers: working precision)
+    // non-equilibrium parts, moved
     R A[NCOEF], B[NCOEF];
     A[0] = R(0);
 #pragma unroll
@@ -112,48 +163,31 @@ __device__ __forceinline__ void source_dev(const StepParams& p, const RefState<R
     for (int k = 0; k < NCOEF; ++k) B[k] = sto_get<S, R>(neq + (long long)(9 + k) * N + nd);
     retarget(tx, ty, A, Df);
     retarget(tx, ty, B, Dg);
-    // f equilibrium: rho tx_p0 ty_q0, minus K_f = rho_r at (0,0)
-    const R rr = R(rho);
+    // f equilibrium rho tx_p0 ty_q0 minus K_f = rho_r at (0,0)
     const R hx[4] = {R(1), tx.t10, tx.t20, tx.t30};
     const R hy[4] = {R(1), ty.t10, ty.t20, ty.t30};
-    Df[0] += R(rho - rf.rho);
+    Df[0] += drho;
 #pragma unroll
     for (int pp = 0; pp <= 3; ++pp)
 #pragma unroll
         for (int q = 0; q <= 3 - pp; ++q)
-            if (pp + q > 0) Df[slot(pp, q)] += rr * hx[pp] * hy[q];
-    // g equilibrium (Sec. II g_eq in the node's frame), moved, minus K_g
-    const double P = rho * T;
-    const R PuxR = R(P * ux) * rf.isT, PuyR = R(P * uy) * rf.isT;   // rho sqrt(T) u * s (moved b10)
-    const double dPT = P * T - rf.PT;
+            if (pp + q > 0) Df[slot(pp, q)] += rhoS * hx[pp] * hy[q];
+    // g equilibrium moved, minus K_g
+    const R dP = drho * TS + rf.rhoR * dT;           // p - p_r
+    const R PS = rf.PR + dP;
+    R ES, dE;
     if (p.split == 0) {
-        const double E = rho * (p.cv * T + 0.5 * (ux * ux + uy * uy));
-        const R Er = R(E);
-        Dg[slot(0, 0)] += R(E - rf.E);
-        Dg[slot(1, 0)] += dx * Er + R(P * ux - rf.Pux) * rf.isT;
-        Dg[slot(0, 1)] += dy * Er + R(P * uy - rf.Puy) * rf.isT;
-        Dg[slot(2, 0)] += tx.t20 * Er + R(2) * dx * PuxR + R(dPT * rf.invT);
-        Dg[slot(0, 2)] += ty.t20 * Er + R(2) * dy * PuyR + R(dPT * rf.invT);
-        Dg[slot(1, 1)] += dx * dy * Er + dx * PuyR + dy * PuxR;
-        const R PsR = R(P) * (R(1) + sig);          // s^2 P
-        Dg[slot(3, 0)] += tx.t30 * Er + R(3) * tx.t20 * PuxR + R(3) * dx * PsR;
-        Dg[slot(0, 3)] += ty.t30 * Er + R(3) * ty.t20 * PuyR + R(3) * dy * PsR;
-        Dg[slot(2, 1)] += tx.t20 * dy * Er + tx.t20 * PuyR + R(2) * dx * dy * PuxR + dy * PsR;
-        Dg[slot(1, 2)] += ty.t20 * dx * Er + ty.t20 * PuxR + R(2) * dx * dy * PuyR + dx * PsR;
+        const R eS = rf.cvR * TS + R(0.5) * (uxS * uxS + uyS * uyS);
+        ES = rhoS * eS;
+        // E - E_r = (rho - rho_r) e + rho_r (c_v (T - T_r) + (u - u_r).(u + u_r)/2)
+        dE = drho * eS + rf.rhoR * (rf.cvR * dT + R(0.5) * (dux * (R(2) * rf.uxR + dux) +
+                                                              duy * (R(2) * rf.uyR + duy)));
     } else {
-        const R Ur = R(p.cv * P);
-        const R PsR = R(P) * (R(1) + sig);
-        Dg[slot(0, 0)] += R(p.cv * (P - rf.P));
-        Dg[slot(1, 0)] += dx * Ur;
-        Dg[slot(0, 1)] += dy * Ur;
-        Dg[slot(2, 0)] += tx.t20 * Ur + R(dPT * rf.invT);
-        Dg[slot(0, 2)] += ty.t20 * Ur + R(dPT * rf.invT);
-        Dg[slot(1, 1)] += dx * dy * Ur;
-        Dg[slot(3, 0)] += tx.t30 * Ur + R(3) * dx * PsR;
-        Dg[slot(0, 3)] += ty.t30 * Ur + R(3) * dy * PsR;
-        Dg[slot(2, 1)] += tx.t20 * dy * Ur + dy * PsR;
-        Dg[slot(1, 2)] += ty.t20 * dx * Ur + dx * PsR;
+        ES = rf.cvR * PS;
+        dE = rf.cvR * dP;
     }
+    const BaseFrame<R> bf = {rf.PR, rf.isT, rf.invT};
+    add_g_eq_dev<R>(p.split, bf, tx, ty, dx, dy, sig, ES, dE, PS, uxS, uyS, dP, dux, duy, TS, dT, Dg);
 }
 
 // Per-population lattice values, kept in shared memory so that the population loops can run
@@ -200,6 +234,70 @@ __device__ __forceinline__ void make_gamma(const LatRow<R>& la, R wab, const Tau
         }
 }
 
+// Node-interleaved shared-memory records: 20 values per node, f in 0..9 and g in 10..19.
+template <class R>
+__device__ __forceinline__ void store20(R* dst, const R* v)
+{
+    if constexpr (std::is_same<R, float>::value) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            reinterpret_cast<float4*>(dst)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) reinterpret_cast<double2*>(dst)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+    }
+}
+
+// The ten values of distribution D (0 = f, 1 = g) of one record.
+template <class R, int D>
+__device__ __forceinline__ void load10(const R* rec, R* v)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        if constexpr (D == 0) {
+            const float4 a = reinterpret_cast<const float4*>(rec)[0];
+            const float4 b = reinterpret_cast<const float4*>(rec)[1];
+            const float2 c = reinterpret_cast<const float2*>(rec)[4];
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            v[8] = c.x; v[9] = c.y;
+        } else {
+            const float2 a = reinterpret_cast<const float2*>(rec)[5];
+            const float4 b = reinterpret_cast<const float4*>(rec)[3];
+            const float4 c = reinterpret_cast<const float4*>(rec)[4];
+            v[0] = a.x; v[1] = a.y;
+            v[2] = b.x; v[3] = b.y; v[4] = b.z; v[5] = b.w;
+            v[6] = c.x; v[7] = c.y; v[8] = c.z; v[9] = c.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const double2 t = reinterpret_cast<const double2*>(rec + D * NCOEF)[k];
+            v[2 * k] = t.x;
+            v[2 * k + 1] = t.y;
+        }
+    }
+}
+
+// w[j] for a runtime j < n <= 4 without indexing the register array dynamically.
+template <class R>
+__device__ __forceinline__ R pick(const R* w, int j, int n)
+{
+    R v = w[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        if (k < n) v = (j == k) ? w[k] : v;
+    return v;
+}
+
+// Bytes of dynamic shared memory of the step kernel: the staged box (20 values per node) and,
+// for the FP32 2-D kernel, a per-thread cache of the per-b factors V (10 values per b).
+__host__ __device__ constexpr size_t step_smem_bytes(int rbytes, int q1, bool one_d, int box_w,
+                                                     int box_h, int threads)
+{
+    return (size_t)box_w * box_h * 2 * NCOEF * rbytes +
+           ((rbytes == 4 && !one_d) ? (size_t)q1 * NCOEF * threads * 4 : 0);
+}
+
 template <class S, class R, int Q1, int P, bool ONE_D, int TPB>
 __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
 {
@@ -209,6 +307,7 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
     __shared__ int box[4];
     __shared__ LatRow<R> lat[Q1];
     __shared__ RefState<R> srf;
+    constexpr bool kSharedX = !ONE_D && std::is_same<R, float>::value;
 
     const int TX = blockDim.x, TY = blockDim.y;
     const int tid = threadIdx.y * TX + threadIdx.x;
@@ -247,20 +346,24 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
         rf.ux = p.mac_in[N + c];
         rf.uy = p.mac_in[2 * N + c];
         rf.T = p.mac_in[3 * N + c];
-        rf.P = rf.rho * rf.T;
-        rf.PT = rf.P * rf.T;
-        rf.Pux = rf.P * rf.ux;
-        rf.Puy = rf.P * rf.uy;
-        rf.E = (p.split == 0) ? rf.rho * (p.cv * rf.T + 0.5 * (rf.ux * rf.ux + rf.uy * rf.uy))
-                              : p.cv * rf.P;
-        rf.invT = rcp64(rf.T);
-        rf.invTR = R(rf.invT);
-        rf.isT = R(1) / sqrt_r<R>(R(rf.T));
+        const double P = rf.rho * rf.T;
+        const double E = (p.split == 0) ? rf.rho * (p.cv * rf.T + 0.5 * (rf.ux * rf.ux + rf.uy * rf.uy))
+                                        : p.cv * P;
+        rf.rhoR = R(rf.rho);
+        rf.uxR = R(rf.ux);
+        rf.uyR = R(rf.uy);
+        rf.TR = R(rf.T);
+        rf.ER = R(E);
+        rf.PR = R(P);
+        rf.eR = R(E / rf.rho);
+        rf.isT = R(1.0 / sqrt(rf.T));
+        rf.invT = R(1.0 / rf.T);
+        rf.cvR = R(p.cv);
         srf = rf;
     }
     __syncthreads();
     const RefState<R>& rf = srf;
-    const R sTr = sqrt_r<R>(R(rf.T));
+    const R sTr = R(1) / rf.isT;
 
     // ---- per-tile interpolation footprint --------------------------------------------------
     {
@@ -302,19 +405,19 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
     }
     const int ox = box[0], oy = box[1], bw = box[2], bh = box[3];
     const int bn = bw * bh;
+    // per-thread V cache after the box capacity (FP32 2-D kernel)
+    R* sV = sm + (size_t)p.box_w * p.box_h * 2 * NCOEF;
 
     // ---- staging: source deviations in the reference frame --------------------------------
+    // Node-interleaved layout: node i holds its 20 values (f: 0..9, g: 10..19) contiguously,
+    // so each tap of one distribution is three vector loads.
     for (int i = tid; i < bn; i += TPB) {
         int lx = i % bw, ly = i / bw;
         int sx = bc_map(ox + lx, p.nx, p.bc_x);
         int sy = ONE_D ? 0 : bc_map(oy + ly, p.ny, p.bc_y);
-        R Df[NCOEF], Dg[NCOEF];
-        source_dev<S, R>(p, rf, (long long)sy * p.nx + sx, Df, Dg);
-#pragma unroll
-        for (int m = 0; m < NCOEF; ++m) {
-            sm[m * bn + i] = Df[m];
-            sm[(NCOEF + m) * bn + i] = Dg[m];
-        }
+        R D[2 * NCOEF];
+        source_dev<S, R>(p, rf, (long long)sy * p.nx + sx, D, D + NCOEF);
+        store20<R>(sm + (size_t)i * 2 * NCOEF, D);
     }
     __syncthreads();
 
@@ -323,22 +426,28 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
     bool bad = false, nonconv = false;
     unsigned int fallbacks = 0;
     double ubx = ux0, uby = uy0, Tb = T0;
-    double rho = 1.0, unx = ux0, uny = uy0, Tn = T0;
+    double unx = ux0, uny = uy0, Tn = T0;
+    R drho = R(0), dubx = R(0), duby = R(0), durx = R(0), dury = R(0), dTr = R(0), dTb = R(0);
     R Af[NCOEF], Ag[NCOEF];   // deviation coefficients of the streamed populations in lambda_bar
 
     if (active) {
         while (true) {
-            const R sT = sqrt_r<R>(R(Tb));
+            // frame of this iteration relative to the reference (FP64 adds only)
+            const R rbx = R(rf.ux - ubx), rby = R(rf.uy - uby);   // u_r - u_bar
+            const R rbT = R(rf.T - Tb);                            // T_r - T_bar
+            const R sT = sqrt_r<R>(rf.TR - rbT);                   // sqrt(T_bar)
             const R isT = R(1) / sT;
-            const R sig_t = R(rf.T - Tb) * R(rcp64(Tb));      // T_r / T_bar - 1
-            const R s_t = sTr * isT;
-            const Tau<R> txr = make_tau_sig<R>(s_t, R(rf.ux - ubx) * isT, sig_t);
-            const Tau<R> tyr = make_tau_sig<R>(s_t, R(rf.uy - uby) * isT, sig_t);
-            const R ubxr = R(ubx), ubyr = R(uby);
+            const R iTb = isT * isT;
+            const R sig_t = rbT * iTb;                             // T_r / T_bar - 1
+            const Tau<R> txr = make_tau_sig<R>(sTr * isT, rbx * isT, sig_t);
+            const Tau<R> tyr = make_tau_sig<R>(sTr * isT, rby * isT, sig_t);
+            const R ubxr = rf.uxR - rbx, ubyr = rf.uyR - rby;      // u_bar
 #pragma unroll
             for (int m = 0; m < NCOEF; ++m) { Af[m] = R(0); Ag[m] = R(0); }
 
-            if constexpr (!ONE_D) {
+            if constexpr (!ONE_D && std::is_same<R, double>::value) {
+                // FP64: bound by the FP64 pipe, so each population is interpolated directly
+                // (16 taps x 20 values), which needs the fewest multiply-adds.
 #pragma unroll 1
                 for (int b = 0; b < Q1; ++b) {
                     const LatRow<R>& lb = lat[b];
@@ -361,31 +470,27 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
                         for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] = R(0);
                         if (tx0 >= 0 && tx0 + P <= bw && ty0 >= 0 && ty0 + P <= bh) {
 #pragma unroll
-                            for (int j = 0; j < P; ++j) {
-                                // one stencil row per fence: bounds the loads in flight
-                                asm volatile("" ::: "memory");
+                            for (int j = 0; j < P; ++j)
 #pragma unroll
                                 for (int ii = 0; ii < P; ++ii) {
                                     const R W = wy[j] * wx[ii];
-                                    const R* src = sm + (ty0 + j) * bw + tx0 + ii;
+                                    const R* src = sm + ((size_t)(ty0 + j) * bw + tx0 + ii) * 2 * NCOEF;
 #pragma unroll
-                                    for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] += W * src[m * bn];
+                                    for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] += W * src[m];
                                 }
-                            }
                         } else {
                             ++fallbacks;
+#pragma unroll 1
                             for (int j = 0; j < P; ++j)
+#pragma unroll 1
                                 for (int ii = 0; ii < P; ++ii) {
-                                    const R W = wy[j] * wx[ii];
+                                    const R W = pick<R>(wy, j, P) * pick<R>(wx, ii, P);
                                     const int sx = bc_map(x + jx + ii, p.nx, p.bc_x);
                                     const int sy = bc_map(y + jy + j, p.ny, p.bc_y);
-                                    R Df[NCOEF], Dg[NCOEF];
-                                    source_dev<S, R>(p, rf, (long long)sy * p.nx + sx, Df, Dg);
+                                    R D[2 * NCOEF];
+                                    source_dev<S, R>(p, rf, (long long)sy * p.nx + sx, D, D + NCOEF);
 #pragma unroll
-                                    for (int m = 0; m < NCOEF; ++m) {
-                                        Ri[m] += W * Df[m];
-                                        Ri[NCOEF + m] += W * Dg[m];
-                                    }
+                                    for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] += W * D[m];
                                 }
                         }
                         R f = R(0), g = R(0);
@@ -408,6 +513,111 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
                             Ag[slot(pp, q)] += Sg[pp] * lb.he[q];
                         }
                 }
+            } else if constexpr (kSharedX) {
+                // y stencils of all b and the per-b factors V (shared by every a and both
+                // distributions); V goes to this thread's shared-memory cache.
+                R wy[Q1][P];
+                int jy[Q1];
+                int rmin = 1 << 30, rmax = -(1 << 30);
+#pragma unroll
+                for (int b = 0; b < Q1; ++b) {
+                    jy[b] = lagrange<R, P>(-(sT * lat[b].c + ubyr), wy[b]);
+                    rmin = min(rmin, jy[b]);
+                    rmax = max(rmax, jy[b] + P - 1);
+                    R V[NCOEF];
+                    make_V<R>(lat[b], tyr, V);
+#pragma unroll
+                    for (int m = 0; m < NCOEF; ++m) sV[(b * NCOEF + m) * TPB + tid] = V[m];
+                }
+                const bool rows_in = (y + rmin - oy >= 0) && (y + rmax - oy < bh);
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+#pragma unroll 1
+                    for (int a = 0; a < Q1; ++a) {
+                        const LatRow<R>& la = lat[a];
+                        R wx[P];
+                        const int jx = lagrange<R, P>(-(sT * la.c + ubxr), wx);
+                        const int tx0 = x + jx - ox;
+                        // x pass once per row of the union of the y stencils, then the row is
+                        // added to the populations (a, b) whose y stencil contains it
+                        R acc[Q1][NCOEF];
+#pragma unroll
+                        for (int b = 0; b < Q1; ++b)
+#pragma unroll
+                            for (int m = 0; m < NCOEF; ++m) acc[b][m] = R(0);
+                        if (rows_in && tx0 >= 0 && tx0 + P <= bw) {
+                            const R* rowp = sm + ((size_t)(y + rmin - oy) * bw + tx0) * 2 * NCOEF;
+#pragma unroll 1
+                            for (int r = rmin; r <= rmax; ++r, rowp += (size_t)bw * 2 * NCOEF) {
+                                R X[NCOEF];
+                                {
+                                    R v[NCOEF];
+                                    if (d == 0) load10<R, 0>(rowp, v); else load10<R, 1>(rowp, v);
+#pragma unroll
+                                    for (int m = 0; m < NCOEF; ++m) X[m] = wx[0] * v[m];
+                                }
+#pragma unroll
+                                for (int ii = 1; ii < P; ++ii) {
+                                    R v[NCOEF];
+                                    const R* q = rowp + ii * 2 * NCOEF;
+                                    if (d == 0) load10<R, 0>(q, v); else load10<R, 1>(q, v);
+#pragma unroll
+                                    for (int m = 0; m < NCOEF; ++m) X[m] += wx[ii] * v[m];
+                                }
+#pragma unroll
+                                for (int b = 0; b < Q1; ++b) {
+                                    const int j = r - jy[b];
+                                    if ((unsigned)j < (unsigned)P) {     // warp-uniform in smooth flow
+                                        const R w = pick<R>(wy[b], j, P);
+#pragma unroll
+                                        for (int m = 0; m < NCOEF; ++m) acc[b][m] += w * X[m];
+                                    }
+                                }
+                            }
+                        } else {
+                            ++fallbacks;
+                            // global gathers; indices into the register arrays stay static
+#pragma unroll
+                            for (int b = 0; b < Q1; ++b)
+#pragma unroll 1
+                                for (int j = 0; j < P; ++j) {
+                                    const R wyj = pick<R>(wy[b], j, P);
+                                    const int sy = bc_map(y + jy[b] + j, p.ny, p.bc_y);
+#pragma unroll 1
+                                    for (int ii = 0; ii < P; ++ii) {
+                                        const R wxi = pick<R>(wx, ii, P);
+                                        const int sx = bc_map(x + jx + ii, p.nx, p.bc_x);
+                                        R D[2 * NCOEF];
+                                        source_dev<S, R>(p, rf, (long long)sy * p.nx + sx, D, D + NCOEF);
+#pragma unroll
+                                        for (int m = 0; m < NCOEF; ++m) acc[b][m] += wyj * wxi * D[d * NCOEF + m];
+                                    }
+                                }
+                        }
+                        // populations (a, b): f'_ab = gamma_ab . acc_b; their Hermite moments
+                        R Sq[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+                        for (int b = 0; b < Q1; ++b) {
+                            const LatRow<R>& lb = lat[b];
+                            R V[NCOEF], gam[NCOEF];
+#pragma unroll
+                            for (int m = 0; m < NCOEF; ++m) V[m] = sV[(b * NCOEF + m) * TPB + tid];
+                            make_gamma<R>(la, la.w * lb.w, txr, V, gam);
+                            R val = R(0);
+#pragma unroll
+                            for (int m = 0; m < NCOEF; ++m) val += gam[m] * acc[b][m];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) Sq[q] += val * lb.he[q];
+                        }
+#pragma unroll
+                        for (int pp = 0; pp <= 3; ++pp)
+#pragma unroll
+                            for (int q = 0; q <= 3 - pp; ++q) {
+                                if (d == 0) Af[slot(pp, q)] += la.he[pp] * Sq[q];
+                                else Ag[slot(pp, q)] += la.he[pp] * Sq[q];
+                            }
+                    }
+                }
             } else {
                 // quasi-1-D (ny = 1): every y tap reads row 0 and the y weights sum to one, so
                 // the interpolated coefficients depend on a only.
@@ -423,23 +633,24 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
                     if (tx0 >= 0 && tx0 + P <= bw) {
 #pragma unroll
                         for (int ii = 0; ii < P; ++ii) {
-                            const R W = wx[ii];
-                            const R* src = sm + tx0 + ii;
+                            R v[NCOEF];
+                            load10<R, 0>(sm + (size_t)(tx0 + ii) * 2 * NCOEF, v);
 #pragma unroll
-                            for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] += W * src[m * bn];
+                            for (int m = 0; m < NCOEF; ++m) Ri[m] += wx[ii] * v[m];
+                            load10<R, 1>(sm + (size_t)(tx0 + ii) * 2 * NCOEF, v);
+#pragma unroll
+                            for (int m = 0; m < NCOEF; ++m) Ri[NCOEF + m] += wx[ii] * v[m];
                         }
                     } else {
                         ++fallbacks;
+#pragma unroll 1
                         for (int ii = 0; ii < P; ++ii) {
-                            const R W = wx[ii];
+                            const R W = pick<R>(wx, ii, P);
                             const int sx = bc_map(x + jx + ii, p.nx, p.bc_x);
-                            R Df[NCOEF], Dg[NCOEF];
-                            source_dev<S, R>(p, rf, (long long)sx, Df, Dg);
+                            R D[2 * NCOEF];
+                            source_dev<S, R>(p, rf, (long long)sx, D, D + NCOEF);
 #pragma unroll
-                            for (int m = 0; m < NCOEF; ++m) {
-                                Ri[m] += W * Df[m];
-                                Ri[NCOEF + m] += W * Dg[m];
-                            }
+                            for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] += W * D[m];
                         }
                     }
                     R Sf[4] = {R(0), R(0), R(0), R(0)}, Sg[4] = {R(0), R(0), R(0), R(0)};
@@ -471,21 +682,28 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
                 }
             }
 
-            // ---- moments of the streamed populations (Sec. II) --------------------------------
-            // reference part exact in FP64, deviation part from the working precision
-            rho = rf.rho + (double)Af[slot(0, 0)];
-            const double E = rf.E + (double)Ag[slot(0, 0)];
-            const double irho = rcp64(rho);
-            const double sTd = (double)sT;
-            // rho (u - u_bar) = rho_r (u_r - u_bar) + sqrt(T_bar) sum c f'
-            unx = ubx + (rf.rho * (rf.ux - ubx) + sTd * (double)Af[slot(1, 0)]) * irho;
-            uny = uby + (rf.rho * (rf.uy - uby) + sTd * (double)Af[slot(0, 1)]) * irho;
-            if (p.split == 0) Tn = (E * irho - 0.5 * (unx * unx + uny * uny)) * p.inv_cv;
-            else Tn = E * irho * p.inv_cv;
+            // ---- moments of the streamed populations (Sec. II), as deviations --------------
+            drho = Af[slot(0, 0)];                                    // rho - rho_r
+            const R rhoR = rf.rhoR + drho;
+            const R irho = R(1) / rhoR;
+            // rho (u - u_bar) = rho_r (u_r - u_bar) + sqrt(T_bar) sum_i c_i f'_i
+            dubx = (rf.rhoR * rbx + sT * Af[slot(1, 0)]) * irho;      // u - u_bar
+            duby = (rf.rhoR * rby + sT * Af[slot(0, 1)]) * irho;
+            durx = dubx - rbx;                                        // u - u_r
+            dury = duby - rby;
+            // c_v (T - T_r) = (dE - e_r drho)/rho [- (u - u_r).(u + u_r)/2 for the total split]
+            R cvdT = (Ag[slot(0, 0)] - rf.eR * drho) * irho;
+            if (p.split == 0)
+                cvdT -= R(0.5) * (durx * (R(2) * rf.uxR + durx) + dury * (R(2) * rf.uyR + dury));
+            dTr = cvdT * R(p.inv_cv);                                 // T - T_r
+            dTb = dTr + rbT;                                          // T - T_bar
+            unx = ubx + (double)dubx;
+            uny = uby + (double)duby;
+            Tn = rf.T + (double)dTr;
             ++k;
-            if (!(rho > 0.0) || !(Tn > 0.0) || isnan(unx) || isnan(uny)) { bad = true; break; }
-            const float du = sqrtf((float)((unx - ubx) * (unx - ubx) + (uny - uby) * (uny - uby)));
-            const float change = fmaxf(du * rsqrtf((float)Tb), fabsf((float)(Tn - Tb) / (float)Tb));
+            if (!(rhoR > R(0)) || !(Tn > 0.0) || isnan(unx) || isnan(uny)) { bad = true; break; }
+            const float du = sqrtf((float)(dubx * dubx + duby * duby));
+            const float change = fmaxf(du * (float)isT, fabsf((float)(dTb * iTb)));
             bool stop;
             if (p.pc_fixed > 0) stop = (k >= p.pc_fixed);
             else if (change <= (float)p.pc_tol) stop = true;
@@ -499,67 +717,46 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
     // ---- collision in the frame of the final moments and write-back ---------------------------
     if (active) {
         S* nout = reinterpret_cast<S*>(p.neq_out);
-        p.mac_out[node] = rho;
+        p.mac_out[node] = rf.rho + (double)drho;
         p.mac_out[N + node] = unx;
         p.mac_out[2 * N + node] = uny;
         p.mac_out[3 * N + node] = Tn;
         if (!bad) {
-            const double iTn = rcp64(Tn);
-            const R isTn = R(1) / sqrt_r<R>(R(Tn));
-            // deviation part: lambda_bar -> lambda*
+            const R TnR = rf.TR + dTr;
+            const R isTn = R(1) / sqrt_r<R>(TnR);
+            const R iTn = isTn * isTn;
+            // deviation part: lambda_bar -> lambda*  (T_bar/T* - 1, (u_bar - u*)/sqrt(T*))
             {
-                const R sig = R(Tb - Tn) * R(iTn);
+                const R sig = -dTb * iTn;
                 const R s = sqrt_r<R>(R(1) + sig);
-                const Tau<R> tx = make_tau_sig<R>(s, R(ubx - unx) * isTn, sig);
-                const Tau<R> ty = make_tau_sig<R>(s, R(uby - uny) * isTn, sig);
+                const Tau<R> tx = make_tau_sig<R>(s, -dubx * isTn, sig);
+                const Tau<R> ty = make_tau_sig<R>(s, -duby * isTn, sig);
                 retarget(tx, ty, Af, Af);
                 retarget(tx, ty, Ag, Ag);
             }
             // reference part: K moved lambda_r -> lambda*, minus the equilibrium in lambda*
-            const R sig = R(rf.T - Tn) * R(iTn);                 // T_r/T* - 1
+            const R sig = -dTr * iTn;                                 // T_r/T* - 1
             const R s = sqrt_r<R>(R(1) + sig);
-            const R dx = R(rf.ux - unx) * isTn, dy = R(rf.uy - uny) * isTn;
+            const R dx = -durx * isTn, dy = -dury * isTn;             // (u_r - u*)/sqrt(T*)
             const Tau<R> tx = make_tau_sig<R>(s, dx, sig);
             const Tau<R> ty = make_tau_sig<R>(s, dy, sig);
-            const R rr = R(rf.rho);
             const R hx[4] = {R(1), tx.t10, tx.t20, tx.t30};
             const R hy[4] = {R(1), ty.t10, ty.t20, ty.t30};
 #pragma unroll
             for (int pp = 0; pp <= 3; ++pp)
 #pragma unroll
                 for (int q = 0; q <= 3 - pp; ++q)
-                    if (pp + q >= 2) Af[slot(pp, q)] += rr * hx[pp] * hy[q];
-            // g: T_{r->*}(K_g) - B_eq(rho, u*, T*) for the slots with p + q >= 1 (00 is zero by
-            // definition of T*); the large differences are formed in FP64.
-            const double Pn = rho * Tn;
-            const R PruxR = R(rf.Pux) * isTn, PruyR = R(rf.Puy) * isTn;   // s b10_r
-            if (p.split == 0) {
-                const R Er = R(rf.E);
-                Ag[slot(1, 0)] += dx * Er + R(rf.Pux - Pn * unx) * isTn;
-                Ag[slot(0, 1)] += dy * Er + R(rf.Puy - Pn * uny) * isTn;
-                Ag[slot(2, 0)] += tx.t20 * Er + R(2) * dx * PruxR + R((rf.PT - Pn * Tn) * iTn);
-                Ag[slot(0, 2)] += ty.t20 * Er + R(2) * dy * PruyR + R((rf.PT - Pn * Tn) * iTn);
-                Ag[slot(1, 1)] += dx * dy * Er + dx * PruyR + dy * PruxR;
-                const R PsR = R(rf.P) * (R(1) + sig);
-                Ag[slot(3, 0)] += tx.t30 * Er + R(3) * tx.t20 * PruxR + R(3) * dx * PsR;
-                Ag[slot(0, 3)] += ty.t30 * Er + R(3) * ty.t20 * PruyR + R(3) * dy * PsR;
-                Ag[slot(2, 1)] += tx.t20 * dy * Er + tx.t20 * PruyR + R(2) * dx * dy * PruxR + dy * PsR;
-                Ag[slot(1, 2)] += ty.t20 * dx * Er + ty.t20 * PruxR + R(2) * dx * dy * PruyR + dx * PsR;
-            } else {
-                const R Ur = R(rf.E);
-                const R PsR = R(rf.P) * (R(1) + sig);
-                Ag[slot(1, 0)] += dx * Ur;
-                Ag[slot(0, 1)] += dy * Ur;
-                Ag[slot(2, 0)] += tx.t20 * Ur + R((rf.PT - Pn * Tn) * iTn);
-                Ag[slot(0, 2)] += ty.t20 * Ur + R((rf.PT - Pn * Tn) * iTn);
-                Ag[slot(1, 1)] += dx * dy * Ur;
-                Ag[slot(3, 0)] += tx.t30 * Ur + R(3) * dx * PsR;
-                Ag[slot(0, 3)] += ty.t30 * Ur + R(3) * dy * PsR;
-                Ag[slot(2, 1)] += tx.t20 * dy * Ur + dy * PsR;
-                Ag[slot(1, 2)] += ty.t20 * dx * Ur + dx * PsR;
-            }
-            const double tau = p.mu * rcp64(rho) * iTn;            // tau = mu / (rho T)
-            const R keep = R(1) - R(1) / (R(tau) + R(0.5));        // 1 - omega
+                    if (pp + q >= 2) Af[slot(pp, q)] += rf.rhoR * hx[pp] * hy[q];
+            // g: the reference equilibrium moved into lambda*, minus the equilibrium of lambda*
+            // itself: the same expansion as for a staged node, with the reference as the node
+            // and lambda* (density rho) as the base; slot (0,0) is zero by definition of T*.
+            const R rhoN = rf.rhoR + drho;
+            const R dP = -(drho * TnR + rf.rhoR * dTr);               // p_r - p*
+            const BaseFrame<R> bf = {rf.PR - dP, isTn, iTn};          // p* = rho T*
+            add_g_eq_dev<R>(p.split, bf, tx, ty, dx, dy, sig, rf.ER, R(0), rf.PR, rf.uxR, rf.uyR,
+                            dP, -durx, -dury, rf.TR, -dTr, Ag);
+            const R tau = R(p.mu) / (rhoN * TnR);                     // tau = mu / (rho T)
+            const R keep = R(1) - R(1) / (tau + R(0.5));              // 1 - omega
             // f: A*_10 = A*_01 = 0 and B*_00 = B_00^eq hold by definition of lambda*.
             sto_put<S, R>(nout + 0 * N + node, R(0));
             sto_put<S, R>(nout + 1 * N + node, R(0));
