@@ -4,7 +4,8 @@ Workload (one "step"): one PonD time step of the periodic 256 x 256 decay config
 a shear wave u_y = 0.05 sin(2 pi x / 256) on rho = 1, T = 1 plus a Gaussian isobaric
 thermal pulse (dT/T = 1e-3, width 16 cells), with background flow u_x = Ma sqrt(gamma)
 for the four Mach numbers 0.5, 1, 1.5, 2 (four independent 256^2 grids), D2Q16, total
-energy split, mixed precision (FP32 arithmetic, FP64 frames).  Synthetic, seeded inputs.
+energy split, mixed precision (FP32 arithmetic, FP64 frames).  The four grids advance as one
+batch (pond_batch: one kernel launch per time step).  Synthetic, seeded inputs.
 
 Metric: MLUPS = node updates per second / 1e6 over the whole job (all ranks).  The line
 also carries the plain-FP64 GPU step on the same workload, the L1 error of the mixed path
@@ -132,31 +133,69 @@ def make_sims(pond, precision, device, stream):
         s = pond.Simulation(cfg, device=device, stream=stream)
         s.set_state(*case_fields(ma))
         sims.append(s)
-    return sims
+    return sims, pond.Batch(sims, stream=stream)
 
 
-def time_steps(torch, sims, stream, steps, warmup, flush):
-    """Per-launch CUDA-event times of pond_step(1) on every grid, L2 flushed between steps."""
+def time_steps(torch, batch, stream, steps, warmup, flush):
+    """CUDA-event time of every batched step (one launch over all grids), L2 flushed before
+    each timed step."""
     for _ in range(warmup):
-        for s in sims:
-            s.step(1)
+        batch.step(1)
     torch.cuda.synchronize()
-    per_launch = []
     starts, ends = [], []
     for _ in range(steps):
         flush()
-        for s in sims:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            s.step(1)
-            e1.record(stream)
-            starts.append(e0)
-            ends.append(e1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.step(1)
+        e1.record(stream)
+        starts.append(e0)
+        ends.append(e1)
     torch.cuda.synchronize()
-    for e0, e1 in zip(starts, ends):
-        per_launch.append(e0.elapsed_time(e1))
-    return per_launch
+    return [e0.elapsed_time(e1) for e0, e1 in zip(starts, ends)]
+
+
+def tube_batch_rates(torch, pond, device, steps=20):
+    """The 256 uneven quasi-1-D shock tubes (N ~ logU[200, 4000], seed 1), D2Q16 FP32:
+    MLUPS of a per-case launch loop, of one batched launch per step, and of the batched
+    steps replayed from a captured CUDA graph."""
+    cases = W.tube_batch(count=256, seed=1)
+    stream = torch.cuda.Stream(device)
+    sims = []
+    for c in cases:
+        s = pond.Simulation(pond.Config(nx=c.nx, ny=c.ny, precision="fp32", gamma=c.gamma, mu=c.mu,
+                                        bc_x=c.bc_x, bc_y=c.bc_y), device=device, stream=stream)
+        s.set_state(c.rho, c.ux, c.uy, c.T)
+        sims.append(s)
+    nodes = sum(c.nx * c.ny for c in cases)
+    out = {"cases": len(cases), "nodes": nodes}
+
+    def timed(fn):
+        fn(2)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        e1.synchronize()
+        return nodes * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
+
+    def loop(n):
+        for _ in range(n):
+            for s in sims:
+                s.step(1)
+    out["per_case_loop_mlups"] = timed(loop)
+    batch = pond.Batch(sims, stream=stream)
+    out["batched_launch_mlups"] = timed(batch.step)
+    batch.use_graph(steps)
+    out["batched_graph_mlups"] = timed(batch.step)
+    out["launches_per_step"] = {"per_case_loop": len(cases), "batched": 1}
+    batch.close()
+    for s in sims:
+        s.close()
+    return out
 
 
 def mean_iters(sims):
@@ -310,12 +349,12 @@ def main():
         dist.init_process_group("nccl", device_id=device)
 
     flush = l2_flusher(torch, device)
-    sims = make_sims(pond, "fp32", device, stream)
+    sims, batch = make_sims(pond, "fp32", device, stream)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        per_launch = time_steps(torch, sims, stream, args.steps, args.warmup, flush)
+        per_launch = time_steps(torch, batch, stream, args.steps, args.warmup, flush)
     step_ms = sum(per_launch) / args.steps
     if world > 1:
         t = torch.tensor([step_ms], dtype=torch.float64, device=device)
@@ -323,12 +362,13 @@ def main():
         step_ms = float(t.item())
         dist.barrier()
     K = mean_iters(sims)
+    batch.close()
     for s in sims:
         s.close()
     nodes_per_step = len(MACHS) * NX * NY
     value = world * nodes_per_step / (step_ms * 1e-3) / 1e6
     launch_ms = sum(per_launch) / len(per_launch)
-    flops_per_launch = NX * NY * (FLOP_PER_POP_ITER * 16 * K + FLOP_PER_UPDATE)
+    flops_per_launch = nodes_per_step * (FLOP_PER_POP_ITER * 16 * K + FLOP_PER_UPDATE)
     achieved = flops_per_launch / (launch_ms * 1e-3) / 1e12
     if rank != 0:
         if world > 1:
@@ -341,13 +381,15 @@ def main():
                           "achieved_tflops": achieved}))
         return 0
     # plain FP64 GPU step on the same workload (fewer steps: it is ~two orders slower)
-    sims64 = make_sims(pond, "fp64", device, stream)
-    per64 = time_steps(torch, sims64, stream, max(2, args.steps // 10), 1, flush)
+    sims64, batch64 = make_sims(pond, "fp64", device, stream)
+    per64 = time_steps(torch, batch64, stream, max(2, args.steps // 10), 1, flush)
+    batch64.close()
     for s in sims64:
         s.close()
     fp64_ms = sum(per64) / max(2, args.steps // 10)
     err = l1_error(pond, device, stream)
     e2e = e2e_rate(torch, pond, device, steps=max(5, args.steps), warmup=3)
+    tubes = tube_batch_rates(torch, pond, device)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
@@ -369,9 +411,10 @@ def main():
         "fp64": {"value": nodes_per_step / (fp64_ms * 1e-3) / 1e6, "unit": "MLUPS",
                  "ms_per_step": fp64_ms, "speedup_mixed_over_fp64": fp64_ms / step_ms},
         "l1_err_mixed_vs_fp64": err,
+        "tube_batch": tubes,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "step_kernel<float,float,4,4,false>",
+                     "kernel": "step_kernel<float,float,4,4,false,256> (batched over the 4 grids)",
                      "peak_basis": "FP32 pipe: 152 SM x 128 lanes x 2 flop x 2.07 GHz (unit counts)",
                      "flops_per_launch": flops_per_launch, "launch_ms": launch_ms},
         "cpu_baseline": cpu,

@@ -158,6 +158,30 @@ int pond_sync(pond_sim *sim);
 /* Free the handle (not the caller's workspace).  Waits for queued work first. */
 int pond_destroy(pond_sim *sim);
 
+/* Batched stepping (many simulations, one kernel launch per time step).
+ *
+ * A batch advances count simulations together: every time step is one launch of the step
+ * kernel over the tiles of all of them (plus one launch of the internal-split source pass if
+ * any member uses that split), so uneven cases share the GPU without per-case launches or
+ * tail effects.  The members must share precision, lattice, interpolation order, the 1-D
+ * (ny = 1) or 2-D class and the tile configuration; grid size, boundaries, split, gamma, mu
+ * and the predictor-corrector settings may differ.  dev_workspace (caller-owned device
+ * memory of pond_batch_workspace_bytes(count), 256-byte aligned) holds the case table.  The
+ * members' own handles stay valid and see the batch's steps (pond_get_moments etc.), but a
+ * member must not be stepped through pond_step while its batch exists.  The batch works on
+ * cuda_stream, so the caller orders it against the members' streams.
+ * pond_batch_use_graph(batch, k), k even and > 0, captures k time steps into a CUDA graph
+ * that pond_batch_step then replays (k = 0 returns to plain launches); it needs a non-NULL
+ * stream.  Errors: POND_EINVAL for mismatched members or bad arguments, POND_ENOMEM for a
+ * small workspace. */
+typedef struct pond_batch pond_batch;
+int pond_batch_workspace_bytes(int32_t count, size_t *bytes);
+int pond_batch_create(pond_sim *const *sims, int32_t count, void *dev_workspace, size_t bytes,
+                      void *cuda_stream, pond_batch **out);
+int pond_batch_step(pond_batch *batch, int32_t nsteps);
+int pond_batch_use_graph(pond_batch *batch, int32_t steps_per_graph);
+int pond_batch_destroy(pond_batch *batch);
+
 /* Allocation-free stepping.  (No counterpart in the paper: this is plumbing for callers.)
  *
  * Some callers cannot allocate device memory: an application that owns all GPU memory

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "pond.h"
 #include "pond_aux.cuh"
@@ -194,6 +195,26 @@ int sync_status(pond_sim* s)
     return POND_OK;
 }
 
+// Parameters of one case for the step kernel (buffers filled by the caller).
+void fill_case(const pond_config& c, DevStatus* status, CaseDesc& d)
+{
+    std::memset(&d, 0, sizeof(d));
+    d.nx = c.nx;
+    d.ny = c.ny;
+    d.bc_x = c.bc_x;
+    d.bc_y = c.bc_y;
+    d.split = c.split;
+    d.pc_max_iter = c.pc_max_iter;
+    d.pc_fixed = c.pc_fixed_iters;
+    d.N = (long long)c.nx * c.ny;
+    d.cv = 1.0 / (c.gamma - 1.0);
+    d.inv_cv = c.gamma - 1.0;
+    d.mu = c.mu;
+    d.pc_tol = c.pc_tol;
+    d.cur = 0;
+    d.status = status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -338,35 +359,22 @@ int pond_step(pond_sim* s, int32_t nsteps)
 {
     if (!s || nsteps < 0) return POND_EINVAL;
     const pond_config& c = s->cfg;
-    const long long N = (long long)c.nx * c.ny;
     StepParams p;
     std::memset(&p, 0, sizeof(p));
     p.lat = s->lat;
-    p.nx = c.nx;
-    p.ny = c.ny;
-    p.bc_x = c.bc_x;
-    p.bc_y = c.bc_y;
-    p.split = c.split;
-    p.pc_max_iter = c.pc_max_iter;
-    p.pc_fixed = c.pc_fixed_iters;
     p.box_w = s->box_w;
     p.box_h = s->box_h;
-    p.N = N;
-    p.cv = 1.0 / (c.gamma - 1.0);
-    p.inv_cv = c.gamma - 1.0;
-    p.mu = c.mu;
-    p.pc_tol = c.pc_tol;
-    p.status = status_ptr(s);
+    fill_case(c, status_ptr(s), p.one);
     Launch l;
     l.block = dim3(s->tx, s->ty, 1);
     l.grid = dim3((c.nx + s->tx - 1) / s->tx, (c.ny + s->ty - 1) / s->ty, 1);
     l.smem = s->smem;
     l.stream = s->stream;
     for (int k = 0; k < nsteps; ++k) {
-        p.mac_in = mac_ptr(s, s->cur);
-        p.neq_in = neq_ptr(s, s->cur);
-        p.mac_out = mac_ptr(s, 1 - s->cur);
-        p.neq_out = neq_ptr(s, 1 - s->cur);
+        p.one.mac[0] = mac_ptr(s, s->cur);
+        p.one.neq[0] = neq_ptr(s, s->cur);
+        p.one.mac[1] = mac_ptr(s, 1 - s->cur);
+        p.one.neq[1] = neq_ptr(s, 1 - s->cur);
         cudaError_t e = kStep[c.precision][s->lat.q1 == 5][s->one_d](p, c.interp_order, l);
         if (e != cudaSuccess) return cuda_status(e);
         if (c.split == POND_SPLIT_INTERNAL) {
@@ -486,6 +494,215 @@ int pond_destroy(pond_sim* s)
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------
+// Batched stepping
+// ---------------------------------------------------------------------------------------
+struct pond_batch {
+    std::vector<pond_sim*> sims;
+    cudaStream_t stream;
+    CaseDesc* d_cases;
+    int* d_tile_start;
+    int* d_aux_start;
+    int count, total_tiles, total_aux_blocks;
+    bool any_internal;
+    int flip;                      // parity of the steps taken since creation
+    int graph_steps, graph_flip;
+    cudaGraphExec_t graph;
+};
+
+namespace {
+
+size_t batch_layout(int32_t count, size_t* off_tiles, size_t* off_aux)
+{
+    size_t off = align_up((size_t)count * sizeof(CaseDesc));
+    *off_tiles = off;
+    off = align_up(off + (size_t)(count + 1) * sizeof(int));
+    *off_aux = off;
+    return align_up(off + (size_t)(count + 1) * sizeof(int));
+}
+
+cudaError_t batch_launch_step(pond_batch* b)
+{
+    pond_sim* s0 = b->sims[0];
+    StepParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.lat = s0->lat;
+    p.box_w = s0->box_w;
+    p.box_h = s0->box_h;
+    p.flip = b->flip;
+    p.ncase = b->count;
+    p.cases = b->d_cases;
+    p.tile_start = b->d_tile_start;
+    Launch l;
+    l.block = dim3(s0->tx, s0->ty, 1);
+    l.grid = dim3(b->total_tiles, 1, 1);
+    l.smem = s0->smem;
+    l.stream = b->stream;
+    const pond_config& c = s0->cfg;
+    cudaError_t e = kStep[c.precision][s0->lat.q1 == 5][s0->one_d](p, c.interp_order, l);
+    if (e == cudaSuccess && b->any_internal)
+        e = POND_BY_PRECISION(c.precision, internal_source_batch, b->d_cases, b->d_aux_start, b->count,
+                              b->flip, b->total_aux_blocks, b->stream);
+    return e;
+}
+
+void batch_advance_members(pond_batch* b, int steps)
+{
+    for (pond_sim* s : b->sims) {
+        if (steps % 2) s->cur = 1 - s->cur;
+        s->steps += steps;
+    }
+}
+
+}  // namespace
+
+extern "C" int pond_batch_workspace_bytes(int32_t count, size_t* bytes)
+{
+    if (count < 1 || !bytes) return POND_EINVAL;
+    size_t a, b;
+    *bytes = batch_layout(count, &a, &b);
+    return POND_OK;
+}
+
+extern "C" int pond_batch_create(pond_sim* const* sims, int32_t count, void* dev_workspace, size_t bytes,
+                                 void* cuda_stream, pond_batch** out)
+{
+    if (!out) return POND_EINVAL;
+    *out = nullptr;
+    if (!sims || count < 1 || !dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign))
+        return POND_EINVAL;
+    size_t off_tiles, off_aux;
+    if (bytes < batch_layout(count, &off_tiles, &off_aux)) return POND_ENOMEM;
+    const pond_sim* s0 = sims[0];
+    if (!s0) return POND_EINVAL;
+    std::vector<CaseDesc> cases(count);
+    std::vector<int> tile_start(count + 1), aux_start(count + 1);
+    bool any_internal = false;
+    int tiles = 0, aux = 0;
+    for (int i = 0; i < count; ++i) {
+        pond_sim* s = sims[i];
+        if (!s) return POND_EINVAL;
+        const pond_config& c = s->cfg;
+        if (c.precision != s0->cfg.precision || c.lattice != s0->cfg.lattice ||
+            c.interp_order != s0->cfg.interp_order || s->one_d != s0->one_d || s->tx != s0->tx ||
+            s->ty != s0->ty || s->box_w != s0->box_w || s->box_h != s0->box_h)
+            return POND_EINVAL;
+        fill_case(c, status_ptr(s), cases[i]);
+        cases[i].mac[0] = mac_ptr(s, s->cur);
+        cases[i].neq[0] = neq_ptr(s, s->cur);
+        cases[i].mac[1] = mac_ptr(s, 1 - s->cur);
+        cases[i].neq[1] = neq_ptr(s, 1 - s->cur);
+        cases[i].tiles_x = (c.nx + s->tx - 1) / s->tx;
+        const long long t = (long long)cases[i].tiles_x * ((c.ny + s->ty - 1) / s->ty);
+        const long long a = (cases[i].N + 255) / 256;
+        if ((long long)tiles + t > (1ll << 30) || (long long)aux + a > (1ll << 30)) return POND_EINVAL;
+        tile_start[i] = tiles;
+        aux_start[i] = aux;
+        tiles += (int)t;
+        aux += (int)a;
+        any_internal = any_internal || c.split == POND_SPLIT_INTERNAL;
+    }
+    tile_start[count] = tiles;
+    aux_start[count] = aux;
+    pond_batch* b = new (std::nothrow) pond_batch;
+    if (!b) return POND_ENOMEM;
+    b->sims.assign(sims, sims + count);
+    b->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    char* ws = reinterpret_cast<char*>(dev_workspace);
+    b->d_cases = reinterpret_cast<CaseDesc*>(ws);
+    b->d_tile_start = reinterpret_cast<int*>(ws + off_tiles);
+    b->d_aux_start = reinterpret_cast<int*>(ws + off_aux);
+    b->count = count;
+    b->total_tiles = tiles;
+    b->total_aux_blocks = aux;
+    b->any_internal = any_internal;
+    b->flip = 0;
+    b->graph_steps = 0;
+    b->graph_flip = 0;
+    b->graph = nullptr;
+    cudaError_t e = cudaMemcpyAsync(b->d_cases, cases.data(), count * sizeof(CaseDesc),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_tile_start, tile_start.data(), (count + 1) * sizeof(int),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_aux_start, aux_start.data(), (count + 1) * sizeof(int),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_status(e);
+    }
+    *out = b;
+    return POND_OK;
+}
+
+extern "C" int pond_batch_use_graph(pond_batch* b, int32_t steps_per_graph)
+{
+    if (!b || steps_per_graph < 0 || steps_per_graph % 2) return POND_EINVAL;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->graph_steps = 0;
+    if (steps_per_graph == 0) return POND_OK;
+    if (!b->stream) return POND_EINVAL;   // the legacy default stream cannot be captured
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int flip0 = b->flip;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < steps_per_graph && le == cudaSuccess; ++k) {
+        le = batch_launch_step(b);
+        b->flip ^= 1;
+    }
+    b->flip = flip0;
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_status(le != cudaSuccess ? le : e);
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return cuda_status(e);
+    }
+    b->graph_steps = steps_per_graph;
+    b->graph_flip = flip0;
+    return POND_OK;
+}
+
+extern "C" int pond_batch_step(pond_batch* b, int32_t nsteps)
+{
+    if (!b || nsteps < 0) return POND_EINVAL;
+    int left = nsteps;
+    while (left > 0) {
+        if (b->graph && left >= b->graph_steps && b->flip == b->graph_flip) {
+            cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+            batch_advance_members(b, b->graph_steps);   // even: the parity is unchanged
+            left -= b->graph_steps;
+            continue;
+        }
+        cudaError_t e = batch_launch_step(b);
+        if (e != cudaSuccess) return cuda_status(e);
+        b->flip ^= 1;
+        batch_advance_members(b, 1);
+        --left;
+    }
+    return POND_OK;
+}
+
+extern "C" int pond_batch_destroy(pond_batch* b)
+{
+    if (!b) return POND_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    delete b;
+    return cuda_status(e);
+}
+
+// ---------------------------------------------------------------------------------------
 // Allocation-free stepping (pond_step_static): the second copy of the state and the status
 // block live in this file-scope device array instead of a caller workspace.
 // ---------------------------------------------------------------------------------------
@@ -563,21 +780,9 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     StepParams p;
     std::memset(&p, 0, sizeof(p));
     p.lat = lat;
-    p.nx = cfg->nx;
-    p.ny = cfg->ny;
-    p.bc_x = cfg->bc_x;
-    p.bc_y = cfg->bc_y;
-    p.split = cfg->split;
-    p.pc_max_iter = cfg->pc_max_iter;
-    p.pc_fixed = cfg->pc_fixed_iters;
     p.box_w = box_w;
     p.box_h = box_h;
-    p.N = N;
-    p.cv = 1.0 / (cfg->gamma - 1.0);
-    p.inv_cv = cfg->gamma - 1.0;
-    p.mu = cfg->mu;
-    p.pc_tol = cfg->pc_tol;
-    p.status = st;
+    fill_case(*cfg, st, p.one);
     Launch l;
     l.block = dim3(tx, ty, 1);
     l.grid = dim3((cfg->nx + tx - 1) / tx, (cfg->ny + ty - 1) / ty, 1);
@@ -592,21 +797,21 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     a.bc_y = cfg->bc_y;
     a.split = cfg->split;
     a.N = N;
-    a.cv = p.cv;
+    a.cv = p.one.cv;
     a.status = st;
     // ping-pong between the caller's buffers and the array
     for (int k = 0; k < nsteps; ++k) {
         const bool from_caller = (k % 2 == 0);
-        p.mac_in = from_caller ? mac : smac;
-        p.neq_in = from_caller ? neq : sneq;
-        p.mac_out = from_caller ? smac : mac;
-        p.neq_out = from_caller ? sneq : neq;
+        p.one.mac[0] = from_caller ? mac : smac;
+        p.one.neq[0] = from_caller ? neq : sneq;
+        p.one.mac[1] = from_caller ? smac : mac;
+        p.one.neq[1] = from_caller ? sneq : neq;
         e = kStep[cfg->precision][lat.q1 == 5][one_d](p, cfg->interp_order, l);
         if (e != cudaSuccess) return cuda_status(e);
         if (cfg->split == POND_SPLIT_INTERNAL) {
-            a.mac = p.mac_out;
-            a.neq = p.neq_out;
-            a.mac_prev = p.mac_in;
+            a.mac = p.one.mac[1];
+            a.neq = p.one.neq[1];
+            a.mac_prev = p.one.mac[0];
             e = POND_BY_PRECISION(cfg->precision, internal_source, a, stream);
             if (e != cudaSuccess) return cuda_status(e);
         }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "pond_device.cuh"
+#include "pond_step.cuh"
 
 namespace pond {
 
@@ -158,32 +159,59 @@ __global__ void get_pops_kernel(AuxParams p, double* f, double* g, double* oux, 
 // G_20 = -2 rho T d_x u_x, G_11 = -rho T (d_y u_x + d_x u_y), G_02 = -2 rho T d_y u_y
 // (Du = d_t u + u . grad u), and it is added to the non-equilibrium part of g.
 template <class S>
-__global__ void internal_source_kernel(AuxParams p)
+__device__ __forceinline__ void internal_source_node(long long n, int nx, int ny, int bc_x, int bc_y,
+                                                     long long N, const double* mac,
+                                                     const double* mac_prev, void* neq)
 {
-    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= p.N) return;
-    const int x = (int)(n % p.nx), y = (int)(n / p.nx);
-    const long long N = p.N;
-    const double* ux1 = p.mac + N;
-    const double* uy1 = p.mac + 2 * N;
-    long long xp = (long long)y * p.nx + bc_map(x + 1, p.nx, p.bc_x);
-    long long xm = (long long)y * p.nx + bc_map(x - 1, p.nx, p.bc_x);
-    long long yp = (long long)bc_map(y + 1, p.ny, p.bc_y) * p.nx + x;
-    long long ym = (long long)bc_map(y - 1, p.ny, p.bc_y) * p.nx + x;
+    const int x = (int)(n % nx), y = (int)(n / nx);
+    const double* ux1 = mac + N;
+    const double* uy1 = mac + 2 * N;
+    long long xp = (long long)y * nx + bc_map(x + 1, nx, bc_x);
+    long long xm = (long long)y * nx + bc_map(x - 1, nx, bc_x);
+    long long yp = (long long)bc_map(y + 1, ny, bc_y) * nx + x;
+    long long ym = (long long)bc_map(y - 1, ny, bc_y) * nx + x;
     double dxux = 0.5 * (ux1[xp] - ux1[xm]), dyux = 0.5 * (ux1[yp] - ux1[ym]);
     double dxuy = 0.5 * (uy1[xp] - uy1[xm]), dyuy = 0.5 * (uy1[yp] - uy1[ym]);
-    double rho = p.mac[n], ux = ux1[n], uy = uy1[n], T = p.mac[3 * N + n];
-    double dtux = ux - p.mac_prev[N + n], dtuy = uy - p.mac_prev[2 * N + n];
+    double rho = mac[n], ux = ux1[n], uy = uy1[n], T = mac[3 * N + n];
+    double dtux = ux - mac_prev[N + n], dtuy = uy - mac_prev[2 * N + n];
     double Dux = dtux + ux * dxux + uy * dyux;
     double Duy = dtuy + ux * dxuy + uy * dyuy;
     double rT = rho * T, rsT = rho * sqrt(T);
-    S* q = reinterpret_cast<S*>(p.neq);
+    S* q = reinterpret_cast<S*>(neq);
     double G[6] = {-rT * (dxux + dyuy), -rsT * Dux, -rsT * Duy, -2.0 * rT * dxux,
                    -rT * (dyux + dxuy), -2.0 * rT * dyuy};
     for (int m = 0; m < 6; ++m) {
         S* a = q + (long long)(9 + m) * N + n;
         sto_put<S, double>(a, sto_load<S>(a) + G[m]);
     }
+}
+
+template <class S>
+__global__ void internal_source_kernel(AuxParams p)
+{
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    internal_source_node<S>(n, p.nx, p.ny, p.bc_x, p.bc_y, p.N, p.mac, p.mac_prev, p.neq);
+}
+
+// Batched form: block b works on nodes [256 (b - block_start[c]), ...) of case c (the last case
+// with block_start[c] <= b); cases of the total split return at once.
+template <class S>
+__global__ void internal_source_batch_kernel(const CaseDesc* cases, const int* block_start, int ncase,
+                                             int flip)
+{
+    int lo = 0, hi = ncase - 1;
+    const int b = (int)blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (block_start[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const CaseDesc& c = cases[lo];
+    if (c.split != 1) return;
+    const long long n = (long long)(b - block_start[lo]) * blockDim.x + threadIdx.x;
+    if (n >= c.N) return;
+    const int in = c.cur ^ flip;          // the state before the step; the new one is in ^ 1
+    internal_source_node<S>(n, c.nx, c.ny, c.bc_x, c.bc_y, c.N, c.mac[in ^ 1], c.mac[in], c.neq[in ^ 1]);
 }
 
 }  // namespace pond

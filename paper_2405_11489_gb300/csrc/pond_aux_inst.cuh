@@ -44,4 +44,11 @@ cudaError_t POND_CAT(internal_source, POND_PREC)(const AuxParams& p, cudaStream_
     return cudaGetLastError();
 }
 
+cudaError_t POND_CAT(internal_source_batch, POND_PREC)(const CaseDesc* cases, const int* block_start,
+                                                       int ncase, int flip, int blocks, cudaStream_t s)
+{
+    internal_source_batch_kernel<POND_S><<<blocks, 256, 0, s>>>(cases, block_start, ncase, flip);
+    return cudaGetLastError();
+}
+
 }  // namespace pond

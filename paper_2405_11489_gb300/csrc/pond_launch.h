@@ -9,6 +9,7 @@ namespace pond {
 
 struct StepParams;
 struct AuxParams;
+struct CaseDesc;
 
 // Threads per CTA of the step kernel (tile_x * tile_y).
 constexpr int kStepThreads = 256;
@@ -47,7 +48,9 @@ POND_DECLARE_STEP_ALL(bf16)
                                double* T, cudaStream_t s);                                       \
     cudaError_t get_pops_##PREC(const AuxParams& p, double* f, double* g, double* ux,            \
                                 double* uy, double* T, cudaStream_t s);                          \
-    cudaError_t internal_source_##PREC(const AuxParams& p, cudaStream_t s);
+    cudaError_t internal_source_##PREC(const AuxParams& p, cudaStream_t s);                        \
+    cudaError_t internal_source_batch_##PREC(const CaseDesc* cases, const int* block_start,        \
+                                             int ncase, int flip, int blocks, cudaStream_t s);
 
 POND_DECLARE_AUX(f64)
 POND_DECLARE_AUX(f32)

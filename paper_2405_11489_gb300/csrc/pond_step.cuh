@@ -39,18 +39,71 @@
 
 namespace pond {
 
-struct StepParams {
-    Lattice lat;
+// One simulation's parameters and state buffers.  A single launch carries one case by value;
+// a batched launch carries a device table of cases and the first tile of each.
+struct CaseDesc {
     int nx, ny, bc_x, bc_y, split, pc_max_iter, pc_fixed;
-    int box_w, box_h;           // staged box capacity (nodes)
+    int tiles_x;                // tiles along x (tile index -> tile coordinates)
     long long N;                // nx * ny
     double cv, inv_cv, mu, pc_tol;
-    const double* mac_in;       // [4][N]: rho, u_x, u_y, T at time n
-    const void* neq_in;         // [19][N] storage type S
+    double* mac[2];             // [4][N]: rho, u_x, u_y, T
+    void* neq[2];               // [19][N] storage type S
+    int cur;                    // buffer holding the state when flip = 0
+    DevStatus* status;
+};
+
+struct StepParams {
+    Lattice lat;
+    int box_w, box_h;           // staged box capacity (nodes)
+    int flip;                   // the input state is buffer cur ^ flip, the output the other one
+    int ncase;                  // 0: the single case `one`; > 0: `cases` (batched launch)
+    CaseDesc one;
+    const CaseDesc* cases;
+    const int* tile_start;      // [ncase + 1]: first tile of each case, total at the end
+};
+
+// The case of this block, resolved once per block (kept in shared memory).
+struct CaseRun {
+    int nx, ny, bc_x, bc_y, split, pc_max_iter, pc_fixed;
+    int tile_x, tile_y;
+    long long N;
+    double cv, inv_cv, mu, pc_tol;
+    const double* mac_in;
+    const void* neq_in;
     double* mac_out;
     void* neq_out;
     DevStatus* status;
 };
+
+__device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r)
+{
+    const CaseDesc* c = &p.one;
+    int tile = 0;
+    if (p.ncase > 0) {
+        int lo = 0, hi = p.ncase - 1;             // last case with tile_start <= blockIdx.x
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.tile_start[mid] <= b) lo = mid; else hi = mid - 1;
+        }
+        c = p.cases + lo;
+        tile = b - p.tile_start[lo];
+        r.tile_x = tile % c->tiles_x;
+        r.tile_y = tile / c->tiles_x;
+    } else {
+        r.tile_x = blockIdx.x;
+        r.tile_y = blockIdx.y;
+    }
+    r.nx = c->nx; r.ny = c->ny; r.bc_x = c->bc_x; r.bc_y = c->bc_y; r.split = c->split;
+    r.pc_max_iter = c->pc_max_iter; r.pc_fixed = c->pc_fixed;
+    r.N = c->N; r.cv = c->cv; r.inv_cv = c->inv_cv; r.mu = c->mu; r.pc_tol = c->pc_tol;
+    const int in = c->cur ^ p.flip;
+    r.mac_in = c->mac[in];
+    r.neq_in = c->neq[in];
+    r.mac_out = c->mac[in ^ 1];
+    r.neq_out = c->neq[in ^ 1];
+    r.status = c->status;
+}
 
 // Tile reference state: the centre node's frame (FP64) and derived values in R.
 template <class R>
@@ -138,7 +191,7 @@ __device__ __forceinline__ void add_g_eq_dev(int split, const BaseFrame<R>& bf, 
 // Deviation of node nd's coefficients, moved into the reference frame, from the reference
 // node's equilibrium coefficients (f into Df, g into Dg).
 template <class S, class R>
-__device__ __forceinline__ void source_dev(const StepParams& p, const RefState<R>& rf, long long nd,
+__device__ __forceinline__ void source_dev(const CaseRun& p, const RefState<R>& rf, long long nd,
                                            R* Df, R* Dg)
 {
     const long long N = p.N;
@@ -299,7 +352,7 @@ __host__ __device__ constexpr size_t step_smem_bytes(int rbytes, int q1, bool on
 }
 
 template <class S, class R, int Q1, int P, bool ONE_D, int TPB>
-__global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
+__global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
@@ -309,14 +362,18 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
     __shared__ RefState<R> srf;
     constexpr bool kSharedX = !ONE_D && std::is_same<R, float>::value;
 
+    __shared__ CaseRun scase;
     const int TX = blockDim.x, TY = blockDim.y;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    const int x = blockIdx.x * TX + threadIdx.x;
-    const int y = blockIdx.y * TY + threadIdx.y;
+    if (tid == 0) resolve_case(pp, scase);
+    __syncthreads();
+    const CaseRun& p = scase;
+    const int x = p.tile_x * TX + threadIdx.x;
+    const int y = p.tile_y * TY + threadIdx.y;
     const bool active = (x < p.nx) && (y < p.ny);
     const long long N = p.N;
     const long long node = active ? (long long)y * p.nx + x : 0;
-    const Lattice& L = p.lat;
+    const Lattice& L = pp.lat;
 
     if (tid < Q1) {
         LatRow<R> r;
@@ -339,8 +396,8 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
     }
     if (tid == 0) {
         RefState<R> rf;
-        const int cxn = min(blockIdx.x * TX + TX / 2, p.nx - 1);
-        const int cyn = min(blockIdx.y * TY + TY / 2, p.ny - 1);
+        const int cxn = min(p.tile_x * TX + TX / 2, p.nx - 1);
+        const int cyn = min(p.tile_y * TY + TY / 2, p.ny - 1);
         const long long c = (long long)cyn * p.nx + cxn;
         rf.rho = p.mac_in[c];
         rf.ux = p.mac_in[N + c];
@@ -396,17 +453,17 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams p)
             int x_hi = (TX - 1) + (int)floorf(fminf(hx + margin, 1e6f)) + 2;
             int y_lo = (int)floorf(fmaxf(ly - margin, -1e6f)) - 1;
             int y_hi = (TY - 1) + (int)floorf(fminf(hy + margin, 1e6f)) + 2;
-            box[0] = blockIdx.x * TX + x_lo;
-            box[1] = ONE_D ? 0 : blockIdx.y * TY + y_lo;
-            box[2] = min(x_hi - x_lo + 1, p.box_w);
-            box[3] = ONE_D ? 1 : min(y_hi - y_lo + 1, p.box_h);
+            box[0] = p.tile_x * TX + x_lo;
+            box[1] = ONE_D ? 0 : p.tile_y * TY + y_lo;
+            box[2] = min(x_hi - x_lo + 1, pp.box_w);
+            box[3] = ONE_D ? 1 : min(y_hi - y_lo + 1, pp.box_h);
         }
         __syncthreads();
     }
     const int ox = box[0], oy = box[1], bw = box[2], bh = box[3];
     const int bn = bw * bh;
     // per-thread V cache after the box capacity (FP32 2-D kernel)
-    R* sV = sm + (size_t)p.box_w * p.box_h * 2 * NCOEF;
+    R* sV = sm + (size_t)pp.box_w * pp.box_h * 2 * NCOEF;
 
     // ---- staging: source deviations in the reference frame --------------------------------
     // Node-interleaved layout: node i holds its 20 values (f: 0..9, g: 10..19) contiguously,

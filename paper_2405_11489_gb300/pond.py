@@ -36,7 +36,9 @@ BCS = {"periodic": POND_BC_PERIODIC, "outflow": POND_BC_OUTFLOW}
 EXPORTS = ("pond_config_default", "pond_workspace_bytes", "pond_create", "pond_set_state",
            "pond_set_populations", "pond_step", "pond_get_moments", "pond_get_populations",
            "pond_get_stats", "pond_sync", "pond_destroy", "pond_strerror", "pond_version",
-           "pond_state_bytes", "pond_export_state", "pond_import_state", "pond_step_static")
+           "pond_state_bytes", "pond_export_state", "pond_import_state", "pond_step_static",
+           "pond_batch_workspace_bytes", "pond_batch_create", "pond_batch_step",
+           "pond_batch_use_graph", "pond_batch_destroy")
 
 
 class pond_config(ctypes.Structure):
@@ -92,6 +94,11 @@ def load_library(path: str = LIB_PATH):
         lib.pond_export_state.argtypes = [vp, vp, vp, ctypes.c_int]
         lib.pond_import_state.argtypes = [vp, vp, vp, ctypes.c_int]
         lib.pond_step_static.argtypes = [P(pond_config), vp, vp, i32, vp, P(pond_stats)]
+        lib.pond_batch_workspace_bytes.argtypes = [i32, P(sz)]
+        lib.pond_batch_create.argtypes = [P(vp), i32, vp, sz, vp, P(vp)]
+        lib.pond_batch_step.argtypes = [vp, i32]
+        lib.pond_batch_use_graph.argtypes = [vp, i32]
+        lib.pond_batch_destroy.argtypes = [vp]
         lib.pond_strerror.argtypes = [ctypes.c_int]
         lib.pond_strerror.restype = ctypes.c_char_p
         lib.pond_version.restype = ctypes.c_char_p
@@ -188,6 +195,33 @@ def pond_step_static(cfg: pond_config, mac_ptr: int, neq_ptr: int, nsteps: int, 
                                          ctypes.c_void_p(stream_ptr),
                                          ctypes.byref(st) if want_stats else None)
     return rc, st
+
+
+def pond_batch_workspace_bytes(count: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load_library().pond_batch_workspace_bytes(count, ctypes.byref(n)), "pond_batch_workspace_bytes")
+    return n.value
+
+
+def pond_batch_create(handles, workspace_ptr: int, nbytes: int, stream_ptr: int) -> int:
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    h = ctypes.c_void_p(0)
+    _check(load_library().pond_batch_create(arr, len(handles), ctypes.c_void_p(workspace_ptr), nbytes,
+                                            ctypes.c_void_p(stream_ptr), ctypes.byref(h)),
+           "pond_batch_create")
+    return h.value
+
+
+def pond_batch_step(h, nsteps: int) -> int:
+    return load_library().pond_batch_step(h, nsteps)
+
+
+def pond_batch_use_graph(h, steps_per_graph: int) -> int:
+    return load_library().pond_batch_use_graph(h, steps_per_graph)
+
+
+def pond_batch_destroy(h) -> int:
+    return load_library().pond_batch_destroy(h)
 
 
 def pond_sync(h) -> int:
@@ -364,6 +398,43 @@ class Simulation:
         if getattr(self, "handle", None):
             with self.torch.cuda.device(self.device):
                 pond_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Simulations advanced together: one kernel launch per time step (pond_batch)."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        self.torch = torch
+        self.sims = list(sims)
+        self.device = self.sims[0].device
+        self.stream = stream if stream is not None else self.sims[0].stream
+        with torch.cuda.device(self.device):
+            nb = pond_batch_workspace_bytes(len(self.sims))
+            self.workspace = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+            ptr = (int(self.workspace.data_ptr()) + 255) // 256 * 256
+            self.handle = pond_batch_create([s.handle for s in self.sims], ptr, nb,
+                                            self.stream.cuda_stream)
+
+    def use_graph(self, steps_per_graph: int):
+        with self.torch.cuda.device(self.device):
+            _check(pond_batch_use_graph(self.handle, steps_per_graph), "pond_batch_use_graph")
+
+    def step(self, n: int = 1):
+        with self.torch.cuda.device(self.device):
+            _check(pond_batch_step(self.handle, n), "pond_batch_step")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            with self.torch.cuda.device(self.device):
+                pond_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -66,9 +66,11 @@ def shock_tube(nx, ny, left, right, gamma=1.4, kappa=0.2, mu=1e-4, steps=None, x
                 meta={"kappa": kappa, "left": left, "right": right, "x0": x0})
 
 
-def sod(nx=400, ny=4, kappa=0.2, mu=1e-4):
+def sod(nx=400, ny=4, kappa=0.2, mu=None):
     """Sod's problem: (1, 0, 1) | (0.125, 0, 0.1), gamma = 1.4.  With nx cells over the unit
-    length and kappa = 0.2, nx steps reach t = 0.2 in gas-dynamics units (dt = kappa/nx)."""
+    length and kappa = 0.2, nx steps reach t = 0.2 in gas-dynamics units (dt = kappa/nx).
+    Default viscosity: 1e-4 in the units of the states, i.e. mu_lat = 1e-4 kappa nx."""
+    mu = 1e-4 * kappa * nx if mu is None else mu
     return shock_tube(nx, ny, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), gamma=1.4, kappa=kappa, mu=mu,
                       steps=nx, name="sod")
 
@@ -123,7 +125,8 @@ def pressure_step(n=200, dp=1e-3, T0=1.0, gamma=1.4, mu=1e-3, steps=60):
 def riemann2d(n=1024, seed=0, gamma=1.4, max_disp=2.0, mu=1e-4, steps=500):
     """Four-quadrant 2-D Riemann problem: per quadrant rho ~ U[0.1, 1.5], p ~ U[0.03, 1.5],
     flow direction ~ U[0, 2 pi), |u| ~ U[0, 1.2 sqrt(gamma p / rho)]; outflow on all sides.
-    The lattice velocity scale makes the largest population displacement max_disp cells."""
+    The lattice velocity scale makes the largest population displacement max_disp cells.
+    mu is given in the units of the states on the unit square: mu_lat = mu kappa n."""
     rng = np.random.default_rng(seed)
     states = []
     for _ in range(4):
@@ -144,7 +147,7 @@ def riemann2d(n=1024, seed=0, gamma=1.4, max_disp=2.0, mu=1e-4, steps=500):
         uy[m] = kappa * vy
         T[m] = kappa * kappa * p / r
     ma = max(math.hypot(vx, vy) / math.sqrt(gamma * p / r) for r, vx, vy, p in states)
-    return Case("riemann2d", rho, ux, uy, T, gamma=gamma, mu=mu, bc_x="outflow", bc_y="outflow",
+    return Case("riemann2d", rho, ux, uy, T, gamma=gamma, mu=mu * kappa * n, bc_x="outflow", bc_y="outflow",
                 steps=steps, meta={"seed": seed, "kappa": kappa, "states": states, "max_ma": ma})
 
 
@@ -152,7 +155,8 @@ def tube_batch(count=256, seed=1, nmin=200, nmax=4000, gamma=1.4, mu=1e-4):
     """Uneven quasi-1-D shock tubes: N ~ logU[nmin, nmax] cells (ny = 1), p_L/p_R ~ logU[2, 100],
     rho_L/rho_R ~ logU[1, 10] (right state rho = 0.125, p = 0.1 as in Sod).  Each tube's
     velocity scale keeps its fastest wave inside the tube over N steps and bounds the
-    population displacement by 2 cells per step."""
+    population displacement by 2 cells per step.  mu is given in the units of the states on a
+    tube of unit length: mu_lat = mu kappa N."""
     rng = np.random.default_rng(seed)
     cases = []
     for k in range(count):
@@ -168,7 +172,7 @@ def tube_batch(count=256, seed=1, nmin=200, nmax=4000, gamma=1.4, mu=1e-4):
         smax = max(aL, s_shock)
         vmax = C_MAX_Q16 * max(math.sqrt(left[2] / left[0]), math.sqrt(right[2] / right[0])) + smax
         kappa = min(0.45 / smax, 2.0 / vmax)
-        c = shock_tube(N, 1, left, right, gamma=gamma, kappa=kappa, mu=mu, steps=N,
+        c = shock_tube(N, 1, left, right, gamma=gamma, kappa=kappa, mu=mu * kappa * N, steps=N,
                        name="tube%03d" % k)
         cases.append(c)
     return cases
