@@ -88,6 +88,8 @@ def _lib_handle():
             lib.or_step.argtypes = ([P(Config)] + [_D] * 10
                                     + [P(ctypes.c_int32), P(ctypes.c_int64)])
             lib.or_collide_node.argtypes = [P(Config), _D, _D] + [ctypes.c_double] * 3 + [_D] * 3
+            lib.or_step_nodes.argtypes = ([P(Config)] + [_D] * 5 + [ctypes.c_int]
+                                          + [P(ctypes.c_int32)] * 2 + [_D] * 3 + [P(ctypes.c_int32)])
             _lib = lib
     return _lib
 
@@ -186,6 +188,25 @@ def collide_node(cfg: Config, P, G, frame):
     if rc != 0:
         raise ValueError("non-physical moments")
     return fo, go, fr
+
+
+def step_nodes(cfg: Config, st: State, xs, ys):
+    """One time step at the listed nodes only, from the full state st (the internal-split
+    source pass, which needs every node's new frame, is not applied).  Returns
+    (f [Q][count], g [Q][count], (ux, uy, T), iters)."""
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    count = len(xs)
+    Q = cfg.q1 * cfg.q1
+    fo = np.zeros((Q, count))
+    go = np.zeros((Q, count))
+    fr = np.zeros((3, count))
+    it = np.zeros(count, dtype=np.int32)
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    _lib_handle().or_step_nodes(ctypes.byref(cfg), _p(st.f), _p(st.g), _p(st.ux), _p(st.uy),
+                                _p(st.T), count, xs.ctypes.data_as(I32), ys.ctypes.data_as(I32),
+                                _p(fo), _p(go), _p(fr), it.ctypes.data_as(I32))
+    return fo, go, (fr[0], fr[1], fr[2]), it
 
 
 class StepResult:

@@ -490,13 +490,59 @@ static void internal_source(const or_config *cfg, const or_lattice *L, double *g
 /* converge within pc_max_iter (state still advanced).  first_bad receives the first   */
 /* non-physical node (or -1).                                                          */
 /* ---------------------------------------------------------------------------------- */
+/* Predictor-corrector and collision at one node (x, y): streamed populations in successive
+ * frames until the frame converges (or K iterations in fixed mode), then BGK in the frame of
+ * the final moments.  Writes the node's post-collision populations fo_n, go_n and its moments.
+ * Returns the iteration count; *badnode / *nonconv flag the outcomes. */
+static int step_node(const or_src *S, or_memo *M, int x, int y, double *fo_n, double *go_n,
+                     or_moments *mout, int *badnode, int *nonconv)
+{
+    const or_config *cfg = S->cfg;
+    const or_lattice *L = S->L;
+    double cv = cv_of(cfg->gamma);
+    size_t n = (size_t)y * cfg->nx + x;
+    double P[OR_MAXQ], G[OR_MAXQ];
+    or_frame bar = {S->fux[n], S->fuy[n], S->fT[n]};        /* predictor: previous frame */
+    or_moments m;
+    int k = 0, stop = 0;
+    *badnode = 0;
+    *nonconv = 0;
+    while (!stop) {
+        stream_node(S, M, x, y, bar, P, G);
+        m = moments_of(L, P, G, 1, bar, cfg->split, cv);
+        ++k;
+        if (nonphysical(m)) { *badnode = 1; break; }
+        double du = sqrt((m.ux - bar.ux) * (m.ux - bar.ux) + (m.uy - bar.uy) * (m.uy - bar.uy));
+        double change = fmax(du / sqrt(bar.T), fabs(m.T - bar.T) / bar.T);
+        if (cfg->pc_fixed_iters > 0) {
+            stop = (k >= cfg->pc_fixed_iters);
+        } else if (change <= cfg->pc_tol) {
+            stop = 1;
+        } else if (k >= cfg->pc_max_iter) {
+            stop = 1;
+            *nonconv = 1;
+        }
+        if (!stop) {                                   /* corrector: frame of the moments */
+            bar.ux = m.ux;
+            bar.uy = m.uy;
+            bar.T = m.T;
+        }
+    }
+    *mout = m;
+    if (*badnode) {
+        for (int i = 0; i < L->Q; ++i) { fo_n[i] = NAN; go_n[i] = NAN; }
+        return k;
+    }
+    collide_node(L, cfg, P, G, bar, m, fo_n, go_n);
+    return k;
+}
+
 int or_step(const or_config *cfg, const double *f, const double *g, const double *fux,
             const double *fuy, const double *fT, double *fo, double *go, double *oux,
             double *ouy, double *oT, int32_t *iters, int64_t *first_bad)
 {
     or_lattice L;
     make_lattice(cfg->q1, &L);
-    double cv = cv_of(cfg->gamma);
     int nx = cfg->nx, ny = cfg->ny;
     size_t N = (size_t)nx * ny;
     or_src S = {cfg, &L, f, g, fux, fuy, fT};
@@ -507,43 +553,19 @@ int or_step(const or_config *cfg, const double *f, const double *g, const double
 #pragma omp parallel reduction(+ : nonconv)
     {
         or_memo *M = (or_memo *)malloc(sizeof(or_memo));
-        double P[OR_MAXQ], G[OR_MAXQ], fo_n[OR_MAXQ], go_n[OR_MAXQ];
+        double fo_n[OR_MAXQ], go_n[OR_MAXQ];
 #pragma omp for schedule(static)
         for (int64_t n = 0; n < (int64_t)N; ++n) {
             int x = (int)(n % nx), y = (int)(n / nx);
-            or_frame bar = {fux[n], fuy[n], fT[n]};        /* predictor: previous frame */
             or_moments m;
-            int k = 0, stop = 0, badnode = 0;
-            while (!stop) {
-                stream_node(&S, M, x, y, bar, P, G);
-                m = moments_of(&L, P, G, 1, bar, cfg->split, cv);
-                ++k;
-                if (nonphysical(m)) { badnode = 1; break; }
-                double du = sqrt((m.ux - bar.ux) * (m.ux - bar.ux) + (m.uy - bar.uy) * (m.uy - bar.uy));
-                double change = fmax(du / sqrt(bar.T), fabs(m.T - bar.T) / bar.T);
-                if (cfg->pc_fixed_iters > 0) {
-                    stop = (k >= cfg->pc_fixed_iters);
-                } else if (change <= cfg->pc_tol) {
-                    stop = 1;
-                } else if (k >= cfg->pc_max_iter) {
-                    stop = 1;
-                    nonconv += 1;
-                }
-                if (!stop) {                               /* corrector: frame of the moments */
-                    bar.ux = m.ux;
-                    bar.uy = m.uy;
-                    bar.T = m.T;
-                }
-            }
+            int badnode, nc;
+            int k = step_node(&S, M, x, y, fo_n, go_n, &m, &badnode, &nc);
+            nonconv += nc;
             if (iters) iters[n] = k;
             if (badnode) {
 #pragma omp critical
                 { if (bad < 0 || n < bad) bad = n; }
-                for (int i = 0; i < L.Q; ++i) { fo[(size_t)i * N + n] = NAN; go[(size_t)i * N + n] = NAN; }
-                oux[n] = m.ux; ouy[n] = m.uy; oT[n] = m.T; rho1[n] = m.rho;
-                continue;
             }
-            collide_node(&L, cfg, P, G, bar, m, fo_n, go_n);
             for (int i = 0; i < L.Q; ++i) {
                 fo[(size_t)i * N + n] = fo_n[i];
                 go[(size_t)i * N + n] = go_n[i];
@@ -562,6 +584,41 @@ int or_step(const or_config *cfg, const double *f, const double *g, const double
     if (bad >= 0) return -4;
     if (nonconv > 0) return -5;
     return 0;
+}
+
+/* Exported for the tests: one time step at the nodes listed in xs, ys only (total split, or
+ * the internal split before its source pass), from the full state of the previous step:
+ * fo, go [Q][count], frame [3][count] (ux, uy, T), iters [count]. */
+int or_step_nodes(const or_config *cfg, const double *f, const double *g, const double *fux,
+                  const double *fuy, const double *fT, int count, const int32_t *xs,
+                  const int32_t *ys, double *fo, double *go, double *frame, int32_t *iters)
+{
+    or_lattice L;
+    make_lattice(cfg->q1, &L);
+    or_src S = {cfg, &L, f, g, fux, fuy, fT};
+    int rc = 0;
+#pragma omp parallel
+    {
+        or_memo *M = (or_memo *)malloc(sizeof(or_memo));
+        double fo_n[OR_MAXQ], go_n[OR_MAXQ];
+#pragma omp for schedule(dynamic)
+        for (int j = 0; j < count; ++j) {
+            or_moments m;
+            int badnode, nc;
+            int k = step_node(&S, M, xs[j], ys[j], fo_n, go_n, &m, &badnode, &nc);
+            if (iters) iters[j] = k;
+            if (badnode) rc = -4;
+            for (int i = 0; i < L.Q; ++i) {
+                fo[(size_t)i * count + j] = fo_n[i];
+                go[(size_t)i * count + j] = go_n[i];
+            }
+            frame[j] = m.ux;
+            frame[count + j] = m.uy;
+            frame[2 * count + j] = m.T;
+        }
+        free(M);
+    }
+    return rc;
 }
 
 /* Exported for the tests: predictor-corrector-free collision of streamed populations P, G
