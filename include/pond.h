@@ -169,7 +169,8 @@ int pond_destroy(pond_sim *sim);
  * memory of pond_batch_workspace_bytes(count), 256-byte aligned) holds the case table.  The
  * members' own handles stay valid and see the batch's steps (pond_get_moments etc.), but a
  * member must not be stepped through pond_step while its batch exists.  The batch works on
- * cuda_stream, so the caller orders it against the members' streams.
+ * cuda_stream and orders itself with events: each pond_batch_step waits for the work already
+ * queued on the members' streams, and later work on those streams waits for the batch.
  * pond_batch_use_graph(batch, k), k even and > 0, captures k time steps into a CUDA graph
  * that pond_batch_step then replays (k = 0 returns to plain launches); it needs a non-NULL
  * stream.  Errors: POND_EINVAL for mismatched members or bad arguments, POND_ENOMEM for a

@@ -507,6 +507,9 @@ struct pond_batch {
     int flip;                      // parity of the steps taken since creation
     int graph_steps, graph_flip;
     cudaGraphExec_t graph;
+    std::vector<cudaStream_t> member_streams;   // distinct member streams other than `stream`
+    std::vector<cudaEvent_t> member_events;     // one per member stream
+    cudaEvent_t done;                           // recorded on `stream` after each batch call
 };
 
 namespace {
@@ -543,6 +546,35 @@ cudaError_t batch_launch_step(pond_batch* b)
         e = POND_BY_PRECISION(c.precision, internal_source_batch, b->d_cases, b->d_aux_start, b->count,
                               b->flip, b->total_aux_blocks, b->stream);
     return e;
+}
+
+// Order the batch after work already queued on the members' streams, and the members'
+// streams after the batch's work.
+cudaError_t batch_wait_members(pond_batch* b)
+{
+    for (size_t k = 0; k < b->member_streams.size(); ++k) {
+        cudaError_t e = cudaEventRecord(b->member_events[k], b->member_streams[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->member_events[k], 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t batch_release_members(pond_batch* b)
+{
+    if (b->member_streams.empty()) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(b->done, b->stream);
+    for (size_t k = 0; k < b->member_streams.size() && e == cudaSuccess; ++k)
+        e = cudaStreamWaitEvent(b->member_streams[k], b->done, 0);
+    return e;
+}
+
+void batch_destroy_events(pond_batch* b)
+{
+    for (cudaEvent_t ev : b->member_events) cudaEventDestroy(ev);
+    b->member_events.clear();
+    if (b->done) cudaEventDestroy(b->done);
+    b->done = nullptr;
 }
 
 void batch_advance_members(pond_batch* b, int steps)
@@ -619,8 +651,24 @@ extern "C" int pond_batch_create(pond_sim* const* sims, int32_t count, void* dev
     b->graph_steps = 0;
     b->graph_flip = 0;
     b->graph = nullptr;
-    cudaError_t e = cudaMemcpyAsync(b->d_cases, cases.data(), count * sizeof(CaseDesc),
-                                    cudaMemcpyHostToDevice, b->stream);
+    b->done = nullptr;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < count; ++i) {
+        cudaStream_t ms = sims[i]->stream;
+        bool seen = (ms == b->stream);
+        for (cudaStream_t t : b->member_streams) seen = seen || (t == ms);
+        if (!seen) b->member_streams.push_back(ms);
+    }
+    for (size_t k = 0; k < b->member_streams.size() && e == cudaSuccess; ++k) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->member_events.push_back(ev);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = batch_wait_members(b);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_cases, cases.data(), count * sizeof(CaseDesc),
+                            cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_tile_start, tile_start.data(), (count + 1) * sizeof(int),
                             cudaMemcpyHostToDevice, b->stream);
@@ -629,6 +677,7 @@ extern "C" int pond_batch_create(pond_sim* const* sims, int32_t count, void* dev
                             cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
+        batch_destroy_events(b);
         delete b;
         return cuda_status(e);
     }
@@ -675,6 +724,8 @@ extern "C" int pond_batch_use_graph(pond_batch* b, int32_t steps_per_graph)
 extern "C" int pond_batch_step(pond_batch* b, int32_t nsteps)
 {
     if (!b || nsteps < 0) return POND_EINVAL;
+    cudaError_t we = batch_wait_members(b);
+    if (we != cudaSuccess) return cuda_status(we);
     int left = nsteps;
     while (left > 0) {
         if (b->graph && left >= b->graph_steps && b->flip == b->graph_flip) {
@@ -690,7 +741,7 @@ extern "C" int pond_batch_step(pond_batch* b, int32_t nsteps)
         batch_advance_members(b, 1);
         --left;
     }
-    return POND_OK;
+    return cuda_status(batch_release_members(b));
 }
 
 extern "C" int pond_batch_destroy(pond_batch* b)
@@ -698,6 +749,7 @@ extern "C" int pond_batch_destroy(pond_batch* b)
     if (!b) return POND_EINVAL;
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    batch_destroy_events(b);
     delete b;
     return cuda_status(e);
 }

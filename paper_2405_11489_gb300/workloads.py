@@ -50,20 +50,32 @@ def _fields(ny, nx):
     return (np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)), np.ones((ny, nx)))
 
 
+def _blend(xs, x0, width):
+    """Weight of the left state: a step at x0 - 1/2, or a tanh profile of the given width."""
+    if width <= 0:
+        return (xs < x0).astype(float)
+    return 0.5 * (1.0 - np.tanh((xs - (x0 - 0.5)) / width))
+
+
 def shock_tube(nx, ny, left, right, gamma=1.4, kappa=0.2, mu=1e-4, steps=None, x0=None,
-               name="tube"):
+               name="tube", width=0.0):
     """Left/right states (rho, u, p) in gas-dynamics units, split at x0 (default nx/2);
-    x outflow, y periodic.  kappa = lattice velocity scale."""
+    x outflow, y periodic.  kappa = lattice velocity scale.  width > 0 resolves the initial
+    discontinuity over a tanh profile of that many cells (density, velocity and pressure
+    blended, T = p/rho)."""
     rho, ux, uy, T = _fields(ny, nx)
     x0 = nx // 2 if x0 is None else x0
-    xs = np.arange(nx)[None, :].repeat(ny, 0)
-    for (r, u, p), m in ((left, xs < x0), (right, xs >= x0)):
-        rho[m] = r
-        ux[m] = kappa * u
-        T[m] = kappa * kappa * p / r
+    xs = np.arange(nx, dtype=float)[None, :].repeat(ny, 0)
+    wl = _blend(xs, x0, width)
+    r = wl * left[0] + (1 - wl) * right[0]
+    u = wl * left[1] + (1 - wl) * right[1]
+    p = wl * left[2] + (1 - wl) * right[2]
+    rho[:] = r
+    ux[:] = kappa * u
+    T[:] = kappa * kappa * p / r
     return Case(name, rho, ux, uy, T, gamma=gamma, mu=mu, bc_x="outflow", bc_y="periodic",
                 steps=steps if steps is not None else nx,
-                meta={"kappa": kappa, "left": left, "right": right, "x0": x0})
+                meta={"kappa": kappa, "left": left, "right": right, "x0": x0, "width": width})
 
 
 def sod(nx=400, ny=4, kappa=0.2, mu=None):
@@ -122,11 +134,12 @@ def pressure_step(n=200, dp=1e-3, T0=1.0, gamma=1.4, mu=1e-3, steps=60):
                 steps=steps, meta={"dp": dp, "T0": T0, "x0": n // 2})
 
 
-def riemann2d(n=1024, seed=0, gamma=1.4, max_disp=2.0, mu=1e-4, steps=500):
+def riemann2d(n=1024, seed=0, gamma=1.4, max_disp=2.0, mu=1e-3, steps=500, width=4.0, mu_lat=None):
     """Four-quadrant 2-D Riemann problem: per quadrant rho ~ U[0.1, 1.5], p ~ U[0.03, 1.5],
     flow direction ~ U[0, 2 pi), |u| ~ U[0, 1.2 sqrt(gamma p / rho)]; outflow on all sides.
     The lattice velocity scale makes the largest population displacement max_disp cells.
-    mu is given in the units of the states on the unit square: mu_lat = mu kappa n."""
+    mu is given in the units of the states on the unit square (mu_lat = mu kappa n) unless
+    mu_lat is given.  width > 0 blends the quadrants over tanh profiles of that many cells."""
     rng = np.random.default_rng(seed)
     states = []
     for _ in range(4):
@@ -138,25 +151,33 @@ def riemann2d(n=1024, seed=0, gamma=1.4, max_disp=2.0, mu=1e-4, steps=500):
     vmax = max(math.hypot(ux, uy) + C_MAX_Q16 * math.sqrt(p / r) for r, ux, uy, p in states)
     kappa = max_disp / vmax
     rho, ux, uy, T = _fields(n, n)
-    y, x = np.mgrid[0:n, 0:n]
-    quads = [(x >= n // 2) & (y >= n // 2), (x < n // 2) & (y >= n // 2),
-             (x < n // 2) & (y < n // 2), (x >= n // 2) & (y < n // 2)]
-    for (r, vx, vy, p), m in zip(states, quads):
-        rho[m] = r
-        ux[m] = kappa * vx
-        uy[m] = kappa * vy
-        T[m] = kappa * kappa * p / r
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    wr = 1.0 - _blend(x, n // 2, width)        # weight of the x >= n/2 side
+    wt = 1.0 - _blend(y, n // 2, width)        # weight of the y >= n/2 side
+    quads = [wr * wt, (1 - wr) * wt, (1 - wr) * (1 - wt), wr * (1 - wt)]
+    pres = np.zeros((n, n))
+    rho[:] = 0.0
+    for (r, vx, vy, p), w in zip(states, quads):
+        rho += w * r
+        ux += w * kappa * vx
+        uy += w * kappa * vy
+        pres += w * kappa * kappa * p
+    T[:] = pres / rho
     ma = max(math.hypot(vx, vy) / math.sqrt(gamma * p / r) for r, vx, vy, p in states)
-    return Case("riemann2d", rho, ux, uy, T, gamma=gamma, mu=mu * kappa * n, bc_x="outflow", bc_y="outflow",
-                steps=steps, meta={"seed": seed, "kappa": kappa, "states": states, "max_ma": ma})
+    mul = mu * kappa * n if mu_lat is None else mu_lat
+    return Case("riemann2d", rho, ux, uy, T, gamma=gamma, mu=mul, bc_x="outflow",
+                bc_y="outflow", steps=steps,
+                meta={"seed": seed, "kappa": kappa, "states": states, "max_ma": ma, "width": width})
 
 
-def tube_batch(count=256, seed=1, nmin=200, nmax=4000, gamma=1.4, mu=1e-4):
+def tube_batch(count=256, seed=1, nmin=200, nmax=4000, gamma=1.4, mu=1e-3, width=4.0):
     """Uneven quasi-1-D shock tubes: N ~ logU[nmin, nmax] cells (ny = 1), p_L/p_R ~ logU[2, 100],
     rho_L/rho_R ~ logU[1, 10] (right state rho = 0.125, p = 0.1 as in Sod).  Each tube's
     velocity scale keeps its fastest wave inside the tube over N steps and bounds the
     population displacement by 2 cells per step.  mu is given in the units of the states on a
-    tube of unit length: mu_lat = mu kappa N."""
+    tube of unit length: mu_lat = mu kappa N; the discontinuity is resolved over a tanh
+    profile of `width` cells.  With the 3-point interpolation of Sec. III.A.2 these tubes stay
+    physical over their N steps at the strongest pressure and temperature jumps."""
     rng = np.random.default_rng(seed)
     cases = []
     for k in range(count):
@@ -173,6 +194,6 @@ def tube_batch(count=256, seed=1, nmin=200, nmax=4000, gamma=1.4, mu=1e-4):
         vmax = C_MAX_Q16 * max(math.sqrt(left[2] / left[0]), math.sqrt(right[2] / right[0])) + smax
         kappa = min(0.45 / smax, 2.0 / vmax)
         c = shock_tube(N, 1, left, right, gamma=gamma, kappa=kappa, mu=mu * kappa * N, steps=N,
-                       name="tube%03d" % k)
+                       name="tube%03d" % k, width=width)
         cases.append(c)
     return cases

@@ -1,0 +1,170 @@
+"""Mixed precision against the FP64 oracle, and sampled parity at the full configuration
+sizes.
+
+Mixed modes compute in FP32 on deviations from a per-tile reference equilibrium, with rho,
+u, T in FP64 and the non-equilibrium Hermite coefficients stored in FP32, FP16 or BF16.
+Stated bounds (per-field relative L1 error against the oracle, fixed-K mode):
+
+  FP32 storage:  rho, T <= 5e-8 relative; u <= 1e-7 of the velocity scale
+  FP16 storage:  rho, T <= 2e-6;          u <= 2e-5
+  BF16 storage:  rho, T <= 2e-5;          u <= 2e-4
+
+Full sizes (256 x 256 decay configuration, 1024 x 1024 four-quadrant Riemann problem with the
+3-point interpolation of Sec. III.A.2, in the launch configuration the benchmark uses): after a few GPU steps the state is exported as
+FP64 populations, the GPU takes one more step and the oracle computes that step node by
+node at sampled nodes (corners, edges, the quadrant interfaces, random nodes).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2405_11489_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pond():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_11489_gb300 import build, pond as P
+    build.build()
+    P.load_library()
+    return P
+
+
+def _l1(a, b, scale):
+    return float(np.mean(np.abs(a - b)) / scale)
+
+
+BOUNDS = {"fp32": (5e-8, 1e-7), "fp16": (2e-6, 2e-5), "bf16": (2e-5, 2e-4)}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("split", ["total", "internal"])
+def test_mixed_precision_l1_bounds(pond, orc, precision, split):
+    nx, ny, steps = 48, 40, 20
+    y, x = np.mgrid[0:ny, 0:nx]
+    rho = 1.0 + 0.02 * np.sin(2 * math.pi * x / nx) * np.cos(2 * math.pi * y / ny)
+    ux = 0.6 + 0.03 * np.cos(2 * math.pi * y / ny)
+    uy = -0.2 + 0.03 * np.sin(2 * math.pi * x / nx)
+    T = 0.8 * (1.0 + 0.02 * np.cos(2 * math.pi * (x / nx + y / ny)))
+    ocfg = orc.make_config(nx, ny, split=split, mu=0.04, pc_fixed_iters=2)
+    st = orc.init_state(ocfg, rho, ux, uy, T)
+    for _ in range(steps):
+        st = orc.step(ocfg, st).state
+    o = orc.moments(ocfg, st)
+    sim = pond.Simulation(pond.Config(nx=nx, ny=ny, precision=precision, split=split, mu=0.04,
+                                      pc_fixed_iters=2))
+    sim.set_state(rho, ux, uy, T)
+    sim.step(steps)
+    g = sim.moments()
+    brt, bu = BOUNDS[precision]
+    speed = max(np.abs(o[1]).max(), np.abs(o[2]).max(), math.sqrt(o[3].max()))
+    errs = {"rho": _l1(g[0], o[0], np.mean(np.abs(o[0]))), "T": _l1(g[3], o[3], np.mean(o[3])),
+            "ux": _l1(g[1], o[1], speed), "uy": _l1(g[2], o[2], speed)}
+    print(precision, split, errs)
+    assert errs["rho"] <= brt and errs["T"] <= brt, errs
+    assert errs["ux"] <= bu and errs["uy"] <= bu, errs
+    sim.close()
+
+
+def _sample_nodes(nx, ny, rng, n_random=48):
+    pts = {(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1), (nx // 2, ny // 2),
+           (nx // 2 - 1, ny // 2 - 1), (nx // 2, 0), (0, ny // 2), (nx - 1, ny // 2 + 1)}
+    for _ in range(n_random):
+        pts.add((int(rng.integers(nx)), int(rng.integers(ny))))
+    pts = sorted(pts)
+    return np.array([p[0] for p in pts]), np.array([p[1] for p in pts])
+
+
+def _sampled_step(pond, orc, case, precision, split, warm, tol_m, tol_f, seed, order=3):
+    cfg = pond.Config(nx=case.nx, ny=case.ny, precision=precision, split=split, gamma=case.gamma,
+                      mu=case.mu, bc_x=case.bc_x, bc_y=case.bc_y, interp_order=order)
+    sim = pond.Simulation(cfg)
+    sim.set_state(case.rho, case.ux, case.uy, case.T)
+    sim.step(warm)
+    f, g, fux, fuy, fT = sim.populations()
+    sim.step(1)
+    gf, gg, gux, guy, gT = sim.populations()
+    ocfg = orc.make_config(case.nx, case.ny, split=split, gamma=case.gamma, mu=case.mu,
+                           bc_x=case.bc_x, bc_y=case.bc_y, pc_tol=1e-13, pc_max_iter=40,
+                           interp_order=order)
+    st = orc.State(f, g, fux, fuy, fT)
+    xs, ys = _sample_nodes(case.nx, case.ny, np.random.default_rng(seed))
+    of, og, (oux, ouy, oT), _ = orc.step_nodes(ocfg, st, xs, ys)
+    speed = max(np.abs(oux).max(), np.abs(ouy).max(), math.sqrt(oT.max()))
+    assert np.max(np.abs(gT[ys, xs] - oT) / oT) <= tol_m
+    assert np.max(np.abs(gux[ys, xs] - oux)) <= tol_m * speed
+    assert np.max(np.abs(guy[ys, xs] - ouy)) <= tol_m * speed
+    scale = np.max(np.abs(of))
+    assert np.max(np.abs(gf[:, ys, xs] - of)) <= tol_f * scale
+    if split == "total":
+        assert np.max(np.abs(gg[:, ys, xs] - og)) <= tol_f * np.max(np.abs(og))
+    sim.close()
+
+
+@pytest.mark.parametrize("precision,tol_m,tol_f", [("fp32", 2e-6, 2e-5), ("fp64", 1e-9, 1e-8)])
+def test_decay_256_sampled_parity(pond, orc, precision, tol_m, tol_f):
+    rho = W.thermal_pulse(n=256, amp=1e-3, width=16.0, mu=0.05, ma=1.0).rho
+    sh = W.shear_wave(n=256, ma=1.0, amp=0.05, mu=0.05)
+    case = W.Case("decay", rho, sh.ux, sh.uy, 1.0 / rho, mu=0.05)
+    _sampled_step(pond, orc, case, precision, "total", 3, tol_m, tol_f, seed=1)
+
+
+@pytest.mark.parametrize("split", ["total", "internal"])
+def test_riemann_1024_sampled_parity(pond, orc, split):
+    case = W.riemann2d(n=1024, seed=0)
+    _sampled_step(pond, orc, case, "fp32", split, 4, 5e-6, 5e-5, seed=2, order=2)
+
+
+@pytest.mark.parametrize("split", ["total", "internal"])
+def test_riemann_1024_runs_500_steps_physical(pond, split):
+    """The four-quadrant configuration (1024^2, 500 steps, mixed FP32) stays physical."""
+    case = W.riemann2d(n=1024, seed=0)
+    sim = pond.Simulation(pond.Config(nx=case.nx, ny=case.ny, precision="fp32", split=split,
+                                      gamma=case.gamma, mu=case.mu, bc_x=case.bc_x, bc_y=case.bc_y,
+                                      interp_order=2))
+    sim.set_state(case.rho, case.ux, case.uy, case.T)
+    sim.step(case.steps)
+    rc, st = sim.stats()
+    assert rc in (pond.POND_OK, pond.POND_ENOCONV) and st.first_bad_node == -1
+    rho, ux, uy, T = sim.moments()
+    assert np.all(rho > 0) and np.all(T > 0) and np.all(np.isfinite(ux))
+    sim.close()
+
+
+def test_tube_batch_runs_physical(pond):
+    """The 256 uneven tubes (N ~ logU[200, 4000]) advanced together for 600 steps."""
+    cases = W.tube_batch(count=256, seed=1)
+    sims = []
+    for c in cases:
+        s = pond.Simulation(pond.Config(nx=c.nx, ny=c.ny, precision="fp32", gamma=c.gamma, mu=c.mu,
+                                        bc_x=c.bc_x, bc_y=c.bc_y, interp_order=2))
+        s.set_state(c.rho, c.ux, c.uy, c.T)
+        sims.append(s)
+    batch = pond.Batch(sims)
+    batch.step(600)
+    for s in sims:
+        rc, st = s.stats()
+        assert rc in (pond.POND_OK, pond.POND_ENOCONV) and st.first_bad_node == -1, pond.strerror(rc)
+    batch.close()
+
+
+def test_sod_400x4_fp32_matches_exact_riemann(pond):
+    from oracle.riemann import RiemannSolution
+    c = W.sod(nx=400, ny=4)
+    sim = pond.Simulation(pond.Config(nx=c.nx, ny=c.ny, precision="fp32", gamma=c.gamma, mu=c.mu,
+                                      bc_x=c.bc_x, bc_y=c.bc_y))
+    sim.set_state(c.rho, c.ux, c.uy, c.T)
+    sim.step(c.steps)
+    rho, ux, uy, T = sim.moments()
+    sol = RiemannSolution((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4)
+    t = c.steps * 0.2 / c.nx
+    re, ue, pe = sol.sample((np.arange(c.nx) - c.meta["x0"] + 0.5) / c.nx / t)
+    for row in range(c.ny):
+        assert np.mean(np.abs(rho[row] - re)) < 4e-3
+        assert np.mean(np.abs(rho[row] * T[row] / 0.04 - pe)) < 4e-3
+    sim.close()
