@@ -371,6 +371,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="pond", choices=["pond", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests of the Poisson serving run (the full stream is 10 000: "
+                         "python -m paper_2405_11489_gb300.serve)")
     ap.add_argument("--quick", action="store_true",
                     help="timed mixed-precision steps only (for profiler runs)")
     args = ap.parse_args()
@@ -434,6 +437,9 @@ def main():
     e2e = e2e_rate(torch, pond, device, steps=max(5, args.steps), warmup=3)
     tubes = tube_batch_rates(torch, pond, device)
     others = config_rates(torch, pond, device)
+    from paper_2405_11489_gb300.serve import serve_benchmark
+    serving = serve_benchmark(args.serve_requests, rate=50.0, seed=2, load=0.7, chunk=16,
+                              device=device)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
@@ -457,6 +463,7 @@ def main():
         "l1_err_mixed_vs_fp64": err,
         "tube_batch": tubes,
         "other_configs": others,
+        "serving": serving,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                      "kernel": "step_kernel<float,float,4,4,false,256> (batched over the 4 grids)",

@@ -197,3 +197,57 @@ def tube_batch(count=256, seed=1, nmin=200, nmax=4000, gamma=1.4, mu=1e-3, width
                        name="tube%03d" % k, width=width)
         cases.append(c)
     return cases
+
+
+@dataclass
+class Request:
+    """One simulation request of the serving workload."""
+    rid: int
+    arrival: float              # seconds after the start of the stream
+    case: Case
+    precision: str              # "fp32" or "fp64"
+    split: str                  # "total" or "internal"
+    interp_order: int
+    steps: int
+
+
+def serving_requests(count=10000, rate=50.0, seed=2, step_scale=1.0, max_side=1024):
+    """Poisson request stream: exponential inter-arrival times of mean 1/rate; the type is
+    uniform over shock tubes (N ~ logU[400, 4000], N steps), 2-D Riemann problems
+    (n ~ logU[128, 1024] squared, 100 steps) and periodic decay cases (n ~ logU[64, 512]
+    squared, 200 steps); Ma ~ U[0.5, 3] (background flow of decay cases); split and precision
+    Bernoulli(1/2).  step_scale multiplies the step counts (to set the offered load)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += rng.exponential(1.0 / rate)
+        kind = int(rng.integers(3))
+        ma = rng.uniform(0.5, 3.0)
+        split = "internal" if rng.random() < 0.5 else "total"
+        precision = "fp64" if rng.random() < 0.5 else "fp32"
+        if kind == 0:
+            N = int(round(math.exp(rng.uniform(math.log(400), math.log(4000)))))
+            pr = math.exp(rng.uniform(math.log(2.0), math.log(100.0)))
+            rr = math.exp(rng.uniform(0.0, math.log(10.0)))
+            right = (0.125, 0.0, 0.1)
+            left = (0.125 * rr, 0.0, 0.1 * pr)
+            aR = math.sqrt(1.4 * right[2] / right[0])
+            aL = math.sqrt(1.4 * left[2] / left[0])
+            smax = max(aL, aR * math.sqrt(1.2 / 1.4 * pr + 0.2 / 1.4))
+            vmax = C_MAX_Q16 * max(math.sqrt(left[2] / left[0]), math.sqrt(right[2] / right[0])) + smax
+            kappa = min(0.45 / smax, 2.0 / vmax)
+            case = shock_tube(N, 1, left, right, kappa=kappa, mu=1e-3 * kappa * N, width=4.0,
+                              name="tube")
+            order, steps = 2, N
+        elif kind == 1:
+            n = int(round(math.exp(rng.uniform(math.log(128), math.log(max_side)))))
+            case = riemann2d(n=n, seed=int(rng.integers(1 << 30)))
+            order, steps = 2, 100
+        else:
+            n = int(round(math.exp(rng.uniform(math.log(64), math.log(min(512, max_side))))))
+            case = shear_wave(n=n, ma=ma, amp=0.05, mu=0.05)
+            order, steps = 3, 200
+        out.append(Request(k, t, case, precision, split, order,
+                           max(1, int(round(steps * step_scale)))))
+    return out
