@@ -364,6 +364,21 @@ def run_reference(args, world, rank):
     return 0
 
 
+def profiled_traffic(key):
+    """DRAM bytes (read + write) per launch of the timed kernel from the committed ncu record,
+    or None when the record is missing or the kernel sources have changed since the capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(prof))[key]
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+    except (OSError, ValueError, KeyError):
+        return None
+    return rec["bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,13 +456,7 @@ def main():
     serving = serve_benchmark(args.serve_requests, rate=50.0, seed=2, load=0.7, chunk=16,
                               device=device)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("step_kernel_fp32_256x256_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = profiled_traffic("step_kernel_fp32_batched_4x256x256")
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
