@@ -183,6 +183,44 @@ int pond_batch_step(pond_batch *batch, int32_t nsteps);
 int pond_batch_use_graph(pond_batch *batch, int32_t steps_per_graph);
 int pond_batch_destroy(pond_batch *batch);
 
+/* Launch shapes and autotuning.  (No counterpart in the paper: the paper gives no
+ * implementation; this tunes the staging of its interpolation stencils, Sec. III.A.2.)
+ *
+ * The step kernel runs one CTA per tile of 256 nodes and stages, per tile, the source nodes
+ * of its interpolation stencils in shared memory; the staged box holds the tile plus
+ * 2 * halo + 2 nodes per axis, and stencils that leave it are gathered from global memory.
+ * The shape (tile_x, tile_y, halo) changes speed only, never results beyond rounding (the
+ * tile's centre node is the reference of the FP32 deviation arithmetic).
+ *  - pond_get_launch: the current shape of sim (candidates = 0, ms_per_step = 0).
+ *  - pond_set_launch: set sim's shape (0 = default, as in pond_config); POND_EINVAL if
+ *    tile_x * tile_y != 256, tile_x is odd, or the box does not fit shared memory.
+ *  - pond_autotune: time every candidate shape -- tiles 32x8, 16x16, 64x4, 128x2, 8x32 on
+ *    2-D grids (256x1 on quasi-1-D ones) times halos 4, 5, 6, 8 -- by running
+ *    1 + steps time steps of a copy of sim's current state in dev_scratch (caller-owned
+ *    device memory of pond_workspace_bytes(cfg) bytes, 256-byte aligned) on sim's stream,
+ *    and return the fastest in *out (candidates = shapes timed, ms_per_step its time per
+ *    step).  sim's own state and statistics are untouched.  Results are cached per class
+ *    (precision, lattice, interpolation order, split, 1-D or 2-D, boundaries, and nx, ny
+ *    rounded up to powers of two) for the life of the process: a later call for the same
+ *    class returns the cached shape with candidates = 0 and touches neither the GPU nor
+ *    dev_scratch (which may then be NULL).  flags: POND_TUNE_APPLY also sets the shape on
+ *    sim; POND_TUNE_RETIME times again even if the class is cached.  Synchronises sim's
+ *    stream.  Errors: POND_EINVAL (bad arguments, or no candidate could run),
+ *    POND_ENOMEM (small scratch), POND_ECUDA.
+ *  - pond_autotune_clear: empty the cache. */
+typedef struct {
+    int32_t tile_x, tile_y;    /* tile in nodes */
+    int32_t halo;              /* staged box = tile + 2 * halo + 2 per axis */
+    int32_t candidates;        /* shapes timed by this call (0: current or cached shape) */
+    double ms_per_step;        /* time per step of the chosen shape when it was timed */
+} pond_tuning;
+enum { POND_TUNE_APPLY = 1, POND_TUNE_RETIME = 2 };
+int pond_get_launch(pond_sim *sim, pond_tuning *out);
+int pond_set_launch(pond_sim *sim, int32_t tile_x, int32_t tile_y, int32_t halo);
+int pond_autotune(pond_sim *sim, void *dev_scratch, size_t bytes, int32_t steps, int32_t flags,
+                  pond_tuning *out);
+void pond_autotune_clear(void);
+
 /* Allocation-free stepping.  (No counterpart in the paper: this is plumbing for callers.)
  *
  * Some callers cannot allocate device memory: an application that owns all GPU memory

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -215,6 +216,65 @@ void fill_case(const pond_config& c, DevStatus* status, CaseDesc& d)
     d.status = status;
 }
 
+// Launch shape of the step kernel: the tile (tile_x * tile_y nodes per CTA; 0 = default,
+// 32 x 8 on 2-D grids, 256 x 1 on quasi-1-D ones) and the staged box, the tile plus
+// 2 halo + 2 cells per axis (halo 0 = default 5).
+struct Shape {
+    int tx, ty, box_w, box_h, halo;
+    size_t smem;
+    bool one_d;
+};
+
+int make_shape(const pond_config& c, int tile_x, int tile_y, int halo, Shape* sh)
+{
+    if (tile_x < 0 || tile_y < 0 || halo < 0 || halo > 64) return POND_EINVAL;
+    sh->one_d = (c.ny == 1);
+    if (sh->one_d) {
+        if ((tile_x && tile_x != kStepThreads) || (tile_y && tile_y != 1)) return POND_EINVAL;
+        sh->tx = kStepThreads;
+        sh->ty = 1;
+    } else {
+        if ((tile_x != 0) != (tile_y != 0)) return POND_EINVAL;
+        sh->tx = tile_x ? tile_x : 32;
+        sh->ty = tile_y ? tile_y : kStepThreads / 32;
+        if (sh->tx * sh->ty != kStepThreads || sh->tx % 2) return POND_EINVAL;
+    }
+    sh->halo = halo ? halo : 5;
+    const int extent = 2 * sh->halo + 2;
+    sh->box_w = sh->tx + extent;
+    sh->box_h = sh->one_d ? 1 : sh->ty + extent;
+    const int q1 = c.lattice == POND_D2Q16 ? 4 : 5;
+    sh->smem = step_smem_bytes(c.precision == POND_FP64 ? 8 : 4, q1, sh->one_d, sh->box_w, sh->box_h,
+                               kStepThreads);
+    int dev = 0, smem_optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (sh->smem + 1024 > (size_t)smem_optin) return POND_EINVAL;   // box too large: lower halo or tile
+    // The limit is an attribute of the kernel, shared by every simulation of the process: set
+    // it to the device's largest (less room for the static part), never to this shape's need,
+    // so that a smaller shape set later cannot shrink it under a larger one.
+    e = kSmem[c.precision][q1 == 5][sh->one_d](c.interp_order, (size_t)smem_optin - 1024);
+    return cuda_status(e);
+}
+
+int apply_shape(pond_sim* s, int tile_x, int tile_y, int halo)
+{
+    Shape sh;
+    int rc = make_shape(s->cfg, tile_x, tile_y, halo, &sh);
+    if (rc != POND_OK) return rc;
+    s->one_d = sh.one_d;
+    s->tx = sh.tx;
+    s->ty = sh.ty;
+    s->box_w = sh.box_w;
+    s->box_h = sh.box_h;
+    s->smem = sh.smem;
+    s->cfg.tile_x = s->one_d ? 0 : sh.tx;
+    s->cfg.tile_y = s->one_d ? 0 : sh.ty;
+    s->cfg.halo = sh.halo;
+    return POND_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -282,30 +342,13 @@ int pond_create(const pond_config* cfg, void* dev_workspace, size_t bytes, void*
     s->lay = lay;
     s->cur = 0;
     s->lat = make_lattice(cfg->lattice == POND_D2Q16 ? 4 : 5);
-    s->one_d = (cfg->ny == 1);
-    if (s->one_d) {
-        s->tx = kStepThreads;
-        s->ty = 1;
-    } else {
-        s->tx = cfg->tile_x ? cfg->tile_x : 32;
-        s->ty = cfg->tile_y ? cfg->tile_y : kStepThreads / 32;
-    }
-    const int extent = 2 * (cfg->halo ? cfg->halo : 5) + 2;
-    s->box_w = s->tx + extent;
-    s->box_h = s->one_d ? 1 : s->ty + extent;
-    const int rbytes = cfg->precision == POND_FP64 ? 8 : 4;
-    s->smem = step_smem_bytes(rbytes, s->lat.q1, s->one_d, s->box_w, s->box_h, kStepThreads);
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    int smem_optin = 0;
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess && s->smem + 1024 > (size_t)smem_optin) {
+    rc = apply_shape(s, cfg->tile_x, cfg->tile_y, cfg->halo);
+    if (rc != POND_OK) {
         delete s;
-        return POND_EINVAL;   // box too large for shared memory: lower halo or tile
+        return rc;
     }
-    if (e == cudaSuccess)
-        e = kSmem[cfg->precision][s->lat.q1 == 5][s->one_d](cfg->interp_order, s->smem);
-    if (e == cudaSuccess) {
+    cudaError_t e = cudaSuccess;
+    {
         rc = reset_status(s);
         if (rc != POND_OK) { delete s; return rc; }
         e = cudaMemsetAsync(s->ws, 0, lay.status, s->stream);
@@ -755,6 +798,161 @@ extern "C" int pond_batch_destroy(pond_batch* b)
 }
 
 // ---------------------------------------------------------------------------------------
+// Launch-shape autotuning
+// ---------------------------------------------------------------------------------------
+namespace {
+
+// Problem class of a tuning result: everything that selects the kernel, the boundary
+// handling and the grid size rounded up to powers of two.
+struct TuneKey {
+    int precision, lattice, order, split, one_d, bc_x, bc_y, lx, ly;
+    bool operator<(const TuneKey& o) const
+    {
+        const int a[9] = {precision, lattice, order, split, one_d, bc_x, bc_y, lx, ly};
+        const int b[9] = {o.precision, o.lattice, o.order, o.split, o.one_d, o.bc_x, o.bc_y, o.lx, o.ly};
+        for (int k = 0; k < 9; ++k)
+            if (a[k] != b[k]) return a[k] < b[k];
+        return false;
+    }
+};
+
+int ceil_log2(int v)
+{
+    int k = 0;
+    while ((1 << k) < v && k < 30) ++k;
+    return k;
+}
+
+TuneKey tune_key(const pond_config& c)
+{
+    return TuneKey{c.precision, c.lattice, c.interp_order, c.split, c.ny == 1, c.bc_x, c.bc_y,
+                   ceil_log2(c.nx), ceil_log2(c.ny)};
+}
+
+std::mutex g_tune_mutex;
+std::map<TuneKey, pond_tuning> g_tune_cache;
+
+// Time `steps` steps (after one warm-up step) of a copy of s's current state under one launch
+// shape, on s's stream, in the scratch workspace.  Returns POND_OK and the time per step, or
+// the status that ruled the shape out.
+int time_shape(pond_sim* s, void* scratch, size_t bytes, int tile_x, int tile_y, int halo, int steps,
+               cudaEvent_t e0, cudaEvent_t e1, double* ms)
+{
+    pond_config c = s->cfg;
+    c.tile_x = tile_x;
+    c.tile_y = tile_y;
+    c.halo = halo;
+    pond_sim* t = nullptr;
+    int rc = pond_create(&c, scratch, bytes, s->stream, &t);
+    if (rc != POND_OK) return rc;
+    size_t mb = 0, nb = 0;
+    pond_state_bytes(&s->cfg, &mb, &nb);
+    cudaError_t e = cudaMemcpyAsync(mac_ptr(t, t->cur), mac_ptr(s, s->cur), mb, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(neq_ptr(t, t->cur), neq_ptr(s, s->cur), nb, cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) {
+        pond_destroy(t);
+        return cuda_status(e);
+    }
+    rc = pond_step(t, 1);
+    if (rc == POND_OK) rc = cuda_status(cudaEventRecord(e0, s->stream));
+    if (rc == POND_OK) rc = pond_step(t, steps);
+    if (rc == POND_OK) rc = cuda_status(cudaEventRecord(e1, s->stream));
+    if (rc == POND_OK) rc = sync_status(t);
+    float f = 0.f;
+    if (rc == POND_OK) rc = cuda_status(cudaEventElapsedTime(&f, e0, e1));
+    const int rd = pond_destroy(t);
+    if (rc == POND_OK) rc = rd;
+    *ms = (double)f / steps;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int pond_get_launch(pond_sim* s, pond_tuning* out)
+{
+    if (!s || !out) return POND_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->tile_x = s->tx;
+    out->tile_y = s->ty;
+    out->halo = s->cfg.halo;
+    return POND_OK;
+}
+
+extern "C" int pond_set_launch(pond_sim* s, int32_t tile_x, int32_t tile_y, int32_t halo)
+{
+    if (!s) return POND_EINVAL;
+    return apply_shape(s, tile_x, tile_y, halo);
+}
+
+extern "C" int pond_autotune(pond_sim* s, void* dev_scratch, size_t bytes, int32_t steps, int32_t flags,
+                             pond_tuning* out)
+{
+    if (!s || !out || steps < 1 || steps > 1000 || (flags & ~(POND_TUNE_APPLY | POND_TUNE_RETIME)))
+        return POND_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    const TuneKey key = tune_key(s->cfg);
+    if (!(flags & POND_TUNE_RETIME)) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *out = it->second;
+            out->candidates = 0;
+            return (flags & POND_TUNE_APPLY) ? apply_shape(s, out->tile_x, out->tile_y, out->halo) : POND_OK;
+        }
+    }
+    if (!dev_scratch || (reinterpret_cast<uintptr_t>(dev_scratch) % kAlign)) return POND_EINVAL;
+    if (bytes < layout_of(s->cfg).total) return POND_ENOMEM;
+    // candidates: every 2-D tile of 256 nodes with an even width from 8 x 32 to 128 x 2, and
+    // box halos that cover the footprint of cool (4) to hot (8) gas
+    static const int tiles2d[5][2] = {{32, 8}, {16, 16}, {64, 4}, {128, 2}, {8, 32}};
+    static const int halos[4] = {4, 5, 6, 8};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int rc = cuda_status(e);
+    double best = 0.0;
+    int bx = 0, by = 0, bh = 0, tried = 0;
+    const int ntiles = s->one_d ? 1 : 5;
+    for (int ti = 0; ti < ntiles && rc == POND_OK; ++ti) {
+        const int tx = s->one_d ? 0 : tiles2d[ti][0], ty = s->one_d ? 0 : tiles2d[ti][1];
+        for (int hi = 0; hi < 4 && rc == POND_OK; ++hi) {
+            double ms = 0.0;
+            const int r = time_shape(s, dev_scratch, bytes, tx, ty, halos[hi], steps, e0, e1, &ms);
+            if (r == POND_ECUDA) rc = r;           // a runtime failure ends the search
+            if (r != POND_OK) continue;            // shape ruled out (shared memory, state)
+            ++tried;
+            if (tried == 1 || ms < best) {
+                best = ms;
+                bx = s->one_d ? kStepThreads : tx;
+                by = s->one_d ? 1 : ty;
+                bh = halos[hi];
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != POND_OK) return rc;
+    if (tried == 0) return POND_EINVAL;
+    out->tile_x = bx;
+    out->tile_y = by;
+    out->halo = bh;
+    out->candidates = tried;
+    out->ms_per_step = best;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = *out;
+    }
+    return (flags & POND_TUNE_APPLY) ? apply_shape(s, s->one_d ? 0 : bx, s->one_d ? 0 : by, bh) : POND_OK;
+}
+
+extern "C" void pond_autotune_clear(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache.clear();
+}
+
+// ---------------------------------------------------------------------------------------
 // Allocation-free stepping (pond_step_static): the second copy of the state and the status
 // block live in this file-scope device array instead of a caller workspace.
 // ---------------------------------------------------------------------------------------
@@ -808,20 +1006,13 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
 
     // launch shape of the step kernel, as pond_create chooses it
-    const bool one_d = (cfg->ny == 1);
-    const int tx = one_d ? kStepThreads : (cfg->tile_x ? cfg->tile_x : 32);
-    const int ty = one_d ? 1 : (cfg->tile_y ? cfg->tile_y : kStepThreads / 32);
-    const int extent = 2 * (cfg->halo ? cfg->halo : 5) + 2;
-    const int box_w = tx + extent, box_h = one_d ? 1 : ty + extent;
-    const size_t smem = step_smem_bytes(cfg->precision == POND_FP64 ? 8 : 4, cfg->lattice == POND_D2Q16 ? 4 : 5,
-                                        one_d, box_w, box_h, kStepThreads);
-    int smem_optin = 0;
-    e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (smem + 1024 > (size_t)smem_optin) return POND_EINVAL;
+    Shape sh;
+    rc = make_shape(*cfg, cfg->tile_x, cfg->tile_y, cfg->halo, &sh);
+    if (rc != POND_OK) return rc;
+    const bool one_d = sh.one_d;
+    const int tx = sh.tx, ty = sh.ty, box_w = sh.box_w, box_h = sh.box_h;
+    const size_t smem = sh.smem;
     const Lattice lat = make_lattice(cfg->lattice == POND_D2Q16 ? 4 : 5);
-    e = kSmem[cfg->precision][lat.q1 == 5][one_d](cfg->interp_order, smem);
-    if (e != cudaSuccess) return cuda_status(e);
 
     // the array keeps the previous call's contents: clear the status block
     e = cudaMemsetAsync(st, 0, sizeof(DevStatus), stream);

@@ -342,15 +342,207 @@ __device__ __forceinline__ R pick(const R* w, int j, int n)
     return v;
 }
 
-// Bytes of dynamic shared memory of the step kernel: the staged box (20 values per node) and,
-// for the FP32 2-D kernel, a per-thread cache of the per-b factors V (10 values per b).
+// Bytes of dynamic shared memory of the step kernel for a tile of `nodes` nodes: the staged
+// box (20 values per node) and, for the FP32 2-D kernel, a per-thread cache of the per-b
+// factors V (10 values per b).
 __host__ __device__ constexpr size_t step_smem_bytes(int rbytes, int q1, bool one_d, int box_w,
-                                                     int box_h, int threads)
+                                                     int box_h, int nodes)
 {
     return (size_t)box_w * box_h * 2 * NCOEF * rbytes +
-           ((rbytes == 4 && !one_d) ? (size_t)q1 * NCOEF * threads * 4 : 0);
+           ((rbytes == 4 && !one_d) ? (size_t)q1 * NCOEF * nodes * 4 : 0);
 }
 
+template <class R>
+__device__ __forceinline__ LatRow<R> lat_row(const Lattice& L, int a)
+{
+    LatRow<R> r;
+    r.c = lat_c<R>(L, a);
+    r.w = lat_w<R>(L, a);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        r.he[k] = lat_he<R>(L, a, k);
+        r.hn[k] = lat_hn<R>(L, a, k);
+    }
+    return r;
+}
+
+// The tile's reference state: the frame of its centre node (clamped into the grid).
+template <class R>
+__device__ __forceinline__ RefState<R> tile_reference(const CaseRun& p, int TX, int TY)
+{
+    RefState<R> rf;
+    const long long N = p.N;
+    const int cxn = min(p.tile_x * TX + TX / 2, p.nx - 1);
+    const int cyn = min(p.tile_y * TY + TY / 2, p.ny - 1);
+    const long long c = (long long)cyn * p.nx + cxn;
+    rf.rho = p.mac_in[c];
+    rf.ux = p.mac_in[N + c];
+    rf.uy = p.mac_in[2 * N + c];
+    rf.T = p.mac_in[3 * N + c];
+    const double P = rf.rho * rf.T;
+    const double E = (p.split == 0) ? rf.rho * (p.cv * rf.T + 0.5 * (rf.ux * rf.ux + rf.uy * rf.uy))
+                                    : p.cv * P;
+    rf.rhoR = R(rf.rho);
+    rf.uxR = R(rf.ux);
+    rf.uyR = R(rf.uy);
+    rf.TR = R(rf.T);
+    rf.ER = R(E);
+    rf.PR = R(P);
+    rf.eR = R(E / rf.rho);
+    rf.isT = R(1.0 / sqrt(rf.T));
+    rf.invT = R(1.0 / rf.T);
+    rf.cvR = R(p.cv);
+    return rf;
+}
+
+// Interpolation footprint of the tile (all threads of the block call it; nodes may appear in
+// several threads): the box of source nodes that covers the stencils of every node's departure
+// points under its previous frame, plus a margin for the frame to move during the iterations.
+// Writes box = {x0, y0, width, height}, the size clipped to the staged capacity.
+template <bool ONE_D, int NW>
+__device__ __forceinline__ void footprint_box(const CaseRun& p, const StepParams& pp, int TX, int TY,
+                                              bool active, double ux0, double uy0, double T0,
+                                              float (*red)[NW], int* box, int tid)
+{
+    float cm = (float)pp.lat.cmax;
+    float sT0 = sqrtf(fmaxf((float)T0, 0.f));
+    float lx = active ? -(float)ux0 - cm * sT0 : 1e30f;
+    float hx = active ? -(float)ux0 + cm * sT0 : -1e30f;
+    float ly = active ? -(float)uy0 - cm * sT0 : 1e30f;
+    float hy = active ? -(float)uy0 + cm * sT0 : -1e30f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+        red[0][warp] = lx; red[1][warp] = hx; red[2][warp] = ly; red[3][warp] = hy;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < NW; ++w) {
+            lx = fminf(lx, red[0][w]); hx = fmaxf(hx, red[1][w]);
+            ly = fminf(ly, red[2][w]); hy = fmaxf(hy, red[3][w]);
+        }
+        const float margin = 0.5f;   // room for the frame to move during the iterations
+        // taps of a departure offset `off` lie in [floor(off) - 1, floor(off) + 2]
+        int x_lo = (int)floorf(fmaxf(lx - margin, -1e6f)) - 1;
+        int x_hi = (TX - 1) + (int)floorf(fminf(hx + margin, 1e6f)) + 2;
+        int y_lo = (int)floorf(fmaxf(ly - margin, -1e6f)) - 1;
+        int y_hi = (TY - 1) + (int)floorf(fminf(hy + margin, 1e6f)) + 2;
+        box[0] = p.tile_x * TX + x_lo;
+        box[1] = ONE_D ? 0 : p.tile_y * TY + y_lo;
+        box[2] = min(x_hi - x_lo + 1, pp.box_w);
+        box[3] = ONE_D ? 1 : min(y_hi - y_lo + 1, pp.box_h);
+    }
+    __syncthreads();
+}
+
+// Frame of the final moments lambda* and the maps of the collision (Sec. III.A, collision in the
+// frame of the streamed populations' moments).  Inputs are the deviations of the last
+// iteration: u - u_bar, T - T_bar, u - u_r, T - T_r, rho - rho_r.
+template <class R>
+struct FinalFrame {
+    Tau<R> dx, dy;          // lambda_bar -> lambda* (deviation part)
+    Tau<R> rx, ry;          // lambda_r -> lambda* (reference part)
+    R rdx, rdy, rsig;       // (u_r - u*)/sqrt(T*), T_r/T* - 1
+    R isTn, iTn, TnR, rhoN, keep;
+};
+
+template <class R>
+__device__ __forceinline__ FinalFrame<R> final_frame(const RefState<R>& rf, double mu, R drho, R dubx,
+                                                     R duby, R durx, R dury, R dTr, R dTb)
+{
+    FinalFrame<R> ff;
+    ff.TnR = rf.TR + dTr;
+    ff.isTn = R(1) / sqrt_r<R>(ff.TnR);
+    ff.iTn = ff.isTn * ff.isTn;
+    {
+        const R sig = -dTb * ff.iTn;                          // T_bar/T* - 1
+        const R s = sqrt_r<R>(R(1) + sig);
+        ff.dx = make_tau_sig<R>(s, -dubx * ff.isTn, sig);
+        ff.dy = make_tau_sig<R>(s, -duby * ff.isTn, sig);
+    }
+    ff.rsig = -dTr * ff.iTn;                                  // T_r/T* - 1
+    const R s = sqrt_r<R>(R(1) + ff.rsig);
+    ff.rdx = -durx * ff.isTn;                                 // (u_r - u*)/sqrt(T*)
+    ff.rdy = -dury * ff.isTn;
+    ff.rx = make_tau_sig<R>(s, ff.rdx, ff.rsig);
+    ff.ry = make_tau_sig<R>(s, ff.rdy, ff.rsig);
+    ff.rhoN = rf.rhoR + drho;
+    const R tau = R(mu) / (ff.rhoN * ff.TnR);                 // tau = mu / (rho T)
+    ff.keep = R(1) - R(1) / (tau + R(0.5));                   // 1 - omega
+    return ff;
+}
+
+// BGK relaxation of f in lambda*: the streamed deviation coefficients Af (in lambda_bar) are
+// moved into lambda*, the reference part rho_r moved lambda_r -> lambda* is added (its order
+// 0 and 1 terms are the equilibrium's), and the non-equilibrium part is relaxed and written.
+// A*_10 = A*_01 = 0 hold by definition of lambda*.
+template <class S, class R>
+__device__ __forceinline__ void collide_f(const FinalFrame<R>& ff, const RefState<R>& rf, R* Af, S* nout,
+                                          long long N, long long node)
+{
+    retarget(ff.dx, ff.dy, Af, Af);
+    const R hx[4] = {R(1), ff.rx.t10, ff.rx.t20, ff.rx.t30};
+    const R hy[4] = {R(1), ff.ry.t10, ff.ry.t20, ff.ry.t30};
+#pragma unroll
+    for (int pp = 0; pp <= 3; ++pp)
+#pragma unroll
+        for (int q = 0; q <= 3 - pp; ++q)
+            if (pp + q >= 2) Af[slot(pp, q)] += rf.rhoR * hx[pp] * hy[q];
+    sto_put<S, R>(nout + 0 * N + node, R(0));
+    sto_put<S, R>(nout + 1 * N + node, R(0));
+#pragma unroll
+    for (int m = 3; m < NCOEF; ++m) sto_put<S, R>(nout + (long long)(m - 1) * N + node, ff.keep * Af[m]);
+}
+
+// BGK relaxation of g in lambda*: the reference equilibrium moved into lambda* minus the
+// equilibrium of lambda* itself (the same expansion as for a staged node, with the reference as
+// the node and lambda* as the base) is added; B*_00 = B_00^eq holds by definition of T*.
+template <class S, class R>
+__device__ __forceinline__ void collide_g(int split, const FinalFrame<R>& ff, const RefState<R>& rf,
+                                          R drho, R durx, R dury, R dTr, R* Ag, S* nout, long long N,
+                                          long long node)
+{
+    retarget(ff.dx, ff.dy, Ag, Ag);
+    const R dP = -(drho * ff.TnR + rf.rhoR * dTr);            // p_r - p*
+    const BaseFrame<R> bf = {rf.PR - dP, ff.isTn, ff.iTn};    // p* = rho T*
+    add_g_eq_dev<R>(split, bf, ff.rx, ff.ry, ff.rdx, ff.rdy, ff.rsig, rf.ER, R(0), rf.PR, rf.uxR, rf.uyR,
+                    dP, -durx, -dury, rf.TR, -dTr, Ag);
+    sto_put<S, R>(nout + 9 * N + node, R(0));
+#pragma unroll
+    for (int m = 1; m < NCOEF; ++m) sto_put<S, R>(nout + (long long)(9 + m) * N + node, ff.keep * Ag[m]);
+}
+
+// Per-warp sums of the step statistics, one atomic per warp (every lane of the warp calls it).
+__device__ __forceinline__ void report_stats(DevStatus* st, int tid, unsigned int kk, unsigned int nc,
+                                             unsigned int fb, bool bad, long long node)
+{
+    unsigned int sum_k = __reduce_add_sync(0xffffffffu, kk);
+    unsigned int max_k = __reduce_max_sync(0xffffffffu, kk);
+    unsigned int sum_nc = __reduce_add_sync(0xffffffffu, nc);
+    unsigned int sum_fb = __reduce_add_sync(0xffffffffu, fb);
+    if ((tid & 31) == 0) {
+        atomicAdd(&st->iters_total, (unsigned long long)sum_k);
+        atomicMax(&st->iters_max, max_k);
+        if (sum_nc) {
+            atomicAdd(&st->nonconv, (unsigned long long)sum_nc);
+            atomicOr(&st->flags, 2);
+        }
+        if (sum_fb) atomicAdd(&st->fallbacks, (unsigned long long)sum_fb);
+    }
+    if (bad) {
+        atomicOr(&st->flags, 1);
+        atomicMin(&st->first_bad, (unsigned long long)node);
+    }
+}
+
+// Single-thread-per-node kernel: FP64 arithmetic (2-D and quasi-1-D) and the FP32 quasi-1-D
+// grids.  One CTA per tile of TPB nodes.
 template <class S, class R, int Q1, int P, bool ONE_D, int TPB>
 __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
 {
@@ -360,9 +552,8 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     __shared__ int box[4];
     __shared__ LatRow<R> lat[Q1];
     __shared__ RefState<R> srf;
-    constexpr bool kSharedX = !ONE_D && std::is_same<R, float>::value;
-
     __shared__ CaseRun scase;
+    constexpr bool kSharedX = !ONE_D && std::is_same<R, float>::value;
     const int TX = blockDim.x, TY = blockDim.y;
     const int tid = threadIdx.y * TX + threadIdx.x;
     if (tid == 0) resolve_case(pp, scase);
@@ -373,20 +564,8 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     const bool active = (x < p.nx) && (y < p.ny);
     const long long N = p.N;
     const long long node = active ? (long long)y * p.nx + x : 0;
-    const Lattice& L = pp.lat;
 
-    if (tid < Q1) {
-        LatRow<R> r;
-        r.c = lat_c<R>(L, tid);
-        r.w = lat_w<R>(L, tid);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            r.he[k] = lat_he<R>(L, tid, k);
-            r.hn[k] = lat_hn<R>(L, tid, k);
-        }
-        lat[tid] = r;
-    }
-
+    if (tid < Q1) lat[tid] = lat_row<R>(pp.lat, tid);
     // ---- own frame (predictor) and the tile's reference state ------------------------------
     double ux0 = 0.0, uy0 = 0.0, T0 = 1.0;
     if (active) {
@@ -394,72 +573,11 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
         uy0 = p.mac_in[2 * N + node];
         T0 = p.mac_in[3 * N + node];
     }
-    if (tid == 0) {
-        RefState<R> rf;
-        const int cxn = min(p.tile_x * TX + TX / 2, p.nx - 1);
-        const int cyn = min(p.tile_y * TY + TY / 2, p.ny - 1);
-        const long long c = (long long)cyn * p.nx + cxn;
-        rf.rho = p.mac_in[c];
-        rf.ux = p.mac_in[N + c];
-        rf.uy = p.mac_in[2 * N + c];
-        rf.T = p.mac_in[3 * N + c];
-        const double P = rf.rho * rf.T;
-        const double E = (p.split == 0) ? rf.rho * (p.cv * rf.T + 0.5 * (rf.ux * rf.ux + rf.uy * rf.uy))
-                                        : p.cv * P;
-        rf.rhoR = R(rf.rho);
-        rf.uxR = R(rf.ux);
-        rf.uyR = R(rf.uy);
-        rf.TR = R(rf.T);
-        rf.ER = R(E);
-        rf.PR = R(P);
-        rf.eR = R(E / rf.rho);
-        rf.isT = R(1.0 / sqrt(rf.T));
-        rf.invT = R(1.0 / rf.T);
-        rf.cvR = R(p.cv);
-        srf = rf;
-    }
+    if (tid == 0) srf = tile_reference<R>(p, TX, TY);
     __syncthreads();
     const RefState<R>& rf = srf;
     const R sTr = R(1) / rf.isT;
-
-    // ---- per-tile interpolation footprint --------------------------------------------------
-    {
-        float cm = (float)L.cmax;
-        float sT0 = sqrtf(fmaxf((float)T0, 0.f));
-        float lx = active ? -(float)ux0 - cm * sT0 : 1e30f;
-        float hx = active ? -(float)ux0 + cm * sT0 : -1e30f;
-        float ly = active ? -(float)uy0 - cm * sT0 : 1e30f;
-        float hy = active ? -(float)uy0 + cm * sT0 : -1e30f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-            hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
-            ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-            hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
-        }
-        const int warp = tid >> 5, lane = tid & 31;
-        if (lane == 0) {
-            red[0][warp] = lx; red[1][warp] = hx; red[2][warp] = ly; red[3][warp] = hy;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < TPB / 32; ++w) {
-                lx = fminf(lx, red[0][w]); hx = fmaxf(hx, red[1][w]);
-                ly = fminf(ly, red[2][w]); hy = fmaxf(hy, red[3][w]);
-            }
-            const float margin = 0.5f;   // room for the frame to move during the iterations
-            // taps of a departure offset `off` lie in [floor(off) - 1, floor(off) + 2]
-            int x_lo = (int)floorf(fmaxf(lx - margin, -1e6f)) - 1;
-            int x_hi = (TX - 1) + (int)floorf(fminf(hx + margin, 1e6f)) + 2;
-            int y_lo = (int)floorf(fmaxf(ly - margin, -1e6f)) - 1;
-            int y_hi = (TY - 1) + (int)floorf(fminf(hy + margin, 1e6f)) + 2;
-            box[0] = p.tile_x * TX + x_lo;
-            box[1] = ONE_D ? 0 : p.tile_y * TY + y_lo;
-            box[2] = min(x_hi - x_lo + 1, pp.box_w);
-            box[3] = ONE_D ? 1 : min(y_hi - y_lo + 1, pp.box_h);
-        }
-        __syncthreads();
-    }
+    footprint_box<ONE_D, TPB / 32>(p, pp, TX, TY, active, ux0, uy0, T0, red, box, tid);
     const int ox = box[0], oy = box[1], bw = box[2], bh = box[3];
     const int bn = bw * bh;
     // per-thread V cache after the box capacity (FP32 2-D kernel)
@@ -779,76 +897,15 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
         p.mac_out[2 * N + node] = uny;
         p.mac_out[3 * N + node] = Tn;
         if (!bad) {
-            const R TnR = rf.TR + dTr;
-            const R isTn = R(1) / sqrt_r<R>(TnR);
-            const R iTn = isTn * isTn;
-            // deviation part: lambda_bar -> lambda*  (T_bar/T* - 1, (u_bar - u*)/sqrt(T*))
-            {
-                const R sig = -dTb * iTn;
-                const R s = sqrt_r<R>(R(1) + sig);
-                const Tau<R> tx = make_tau_sig<R>(s, -dubx * isTn, sig);
-                const Tau<R> ty = make_tau_sig<R>(s, -duby * isTn, sig);
-                retarget(tx, ty, Af, Af);
-                retarget(tx, ty, Ag, Ag);
-            }
-            // reference part: K moved lambda_r -> lambda*, minus the equilibrium in lambda*
-            const R sig = -dTr * iTn;                                 // T_r/T* - 1
-            const R s = sqrt_r<R>(R(1) + sig);
-            const R dx = -durx * isTn, dy = -dury * isTn;             // (u_r - u*)/sqrt(T*)
-            const Tau<R> tx = make_tau_sig<R>(s, dx, sig);
-            const Tau<R> ty = make_tau_sig<R>(s, dy, sig);
-            const R hx[4] = {R(1), tx.t10, tx.t20, tx.t30};
-            const R hy[4] = {R(1), ty.t10, ty.t20, ty.t30};
-#pragma unroll
-            for (int pp = 0; pp <= 3; ++pp)
-#pragma unroll
-                for (int q = 0; q <= 3 - pp; ++q)
-                    if (pp + q >= 2) Af[slot(pp, q)] += rf.rhoR * hx[pp] * hy[q];
-            // g: the reference equilibrium moved into lambda*, minus the equilibrium of lambda*
-            // itself: the same expansion as for a staged node, with the reference as the node
-            // and lambda* (density rho) as the base; slot (0,0) is zero by definition of T*.
-            const R rhoN = rf.rhoR + drho;
-            const R dP = -(drho * TnR + rf.rhoR * dTr);               // p_r - p*
-            const BaseFrame<R> bf = {rf.PR - dP, isTn, iTn};          // p* = rho T*
-            add_g_eq_dev<R>(p.split, bf, tx, ty, dx, dy, sig, rf.ER, R(0), rf.PR, rf.uxR, rf.uyR,
-                            dP, -durx, -dury, rf.TR, -dTr, Ag);
-            const R tau = R(p.mu) / (rhoN * TnR);                     // tau = mu / (rho T)
-            const R keep = R(1) - R(1) / (tau + R(0.5));              // 1 - omega
-            // f: A*_10 = A*_01 = 0 and B*_00 = B_00^eq hold by definition of lambda*.
-            sto_put<S, R>(nout + 0 * N + node, R(0));
-            sto_put<S, R>(nout + 1 * N + node, R(0));
-#pragma unroll
-            for (int m = 3; m < NCOEF; ++m) sto_put<S, R>(nout + (long long)(m - 1) * N + node, keep * Af[m]);
-            sto_put<S, R>(nout + 9 * N + node, R(0));
-#pragma unroll
-            for (int m = 1; m < NCOEF; ++m) sto_put<S, R>(nout + (long long)(9 + m) * N + node, keep * Ag[m]);
+            const FinalFrame<R> ff = final_frame<R>(rf, p.mu, drho, dubx, duby, durx, dury, dTr, dTb);
+            collide_f<S, R>(ff, rf, Af, nout, N, node);
+            collide_g<S, R>(p.split, ff, rf, drho, durx, dury, dTr, Ag, nout, N, node);
         } else {
             for (int m = 0; m < NNEQ; ++m) sto_put<S, R>(nout + (long long)m * N + node, R(NAN));
         }
     }
-
-    // ---- statistics (one atomic per warp) -----------------------------------------------------
-    {
-        unsigned int kk = active ? (unsigned int)k : 0u;
-        unsigned int nc = (active && nonconv) ? 1u : 0u;
-        unsigned int sum_k = __reduce_add_sync(0xffffffffu, kk);
-        unsigned int max_k = __reduce_max_sync(0xffffffffu, kk);
-        unsigned int sum_nc = __reduce_add_sync(0xffffffffu, nc);
-        unsigned int sum_fb = __reduce_add_sync(0xffffffffu, fallbacks);
-        if ((tid & 31) == 0) {
-            atomicAdd(&p.status->iters_total, (unsigned long long)sum_k);
-            atomicMax(&p.status->iters_max, max_k);
-            if (sum_nc) {
-                atomicAdd(&p.status->nonconv, (unsigned long long)sum_nc);
-                atomicOr(&p.status->flags, 2);
-            }
-            if (sum_fb) atomicAdd(&p.status->fallbacks, (unsigned long long)sum_fb);
-        }
-        if (active && bad) {
-            atomicOr(&p.status->flags, 1);
-            atomicMin(&p.status->first_bad, (unsigned long long)node);
-        }
-    }
+    report_stats(p.status, tid, active ? (unsigned int)k : 0u, (active && nonconv) ? 1u : 0u, fallbacks,
+                 active && bad, node);
 }
 
 }  // namespace pond

@@ -38,7 +38,9 @@ EXPORTS = ("pond_config_default", "pond_workspace_bytes", "pond_create", "pond_s
            "pond_get_stats", "pond_sync", "pond_destroy", "pond_strerror", "pond_version",
            "pond_state_bytes", "pond_export_state", "pond_import_state", "pond_step_static",
            "pond_batch_workspace_bytes", "pond_batch_create", "pond_batch_step",
-           "pond_batch_use_graph", "pond_batch_destroy")
+           "pond_batch_use_graph", "pond_batch_destroy", "pond_get_launch", "pond_set_launch",
+           "pond_autotune", "pond_autotune_clear")
+POND_TUNE_APPLY, POND_TUNE_RETIME = 1, 2
 
 
 class pond_config(ctypes.Structure):
@@ -55,6 +57,14 @@ class pond_stats(ctypes.Structure):
                 ("pc_iters_total", ctypes.c_int64), ("pc_iters_max", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("nonconv_updates", ctypes.c_int64),
                 ("first_bad_node", ctypes.c_int64), ("halo_fallbacks", ctypes.c_int64)]
+
+
+class pond_tuning(ctypes.Structure):
+    _fields_ = [("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("halo", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("ms_per_step", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PondError(RuntimeError):
@@ -99,12 +109,17 @@ def load_library(path: str = LIB_PATH):
         lib.pond_batch_step.argtypes = [vp, i32]
         lib.pond_batch_use_graph.argtypes = [vp, i32]
         lib.pond_batch_destroy.argtypes = [vp]
+        lib.pond_get_launch.argtypes = [vp, P(pond_tuning)]
+        lib.pond_set_launch.argtypes = [vp, i32, i32, i32]
+        lib.pond_autotune.argtypes = [vp, vp, sz, i32, i32, P(pond_tuning)]
+        lib.pond_autotune_clear.argtypes = []
         lib.pond_strerror.argtypes = [ctypes.c_int]
         lib.pond_strerror.restype = ctypes.c_char_p
         lib.pond_version.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("pond_strerror", "pond_version"):
+            if name not in ("pond_strerror", "pond_version", "pond_autotune_clear"):
                 getattr(lib, name).restype = ctypes.c_int
+        lib.pond_autotune_clear.restype = None
         _lib = lib
         return lib
 
@@ -222,6 +237,26 @@ def pond_batch_use_graph(h, steps_per_graph: int) -> int:
 
 def pond_batch_destroy(h) -> int:
     return load_library().pond_batch_destroy(h)
+
+
+def pond_get_launch(h) -> pond_tuning:
+    t = pond_tuning()
+    _check(load_library().pond_get_launch(h, ctypes.byref(t)), "pond_get_launch")
+    return t
+
+
+def pond_set_launch(h, tile_x: int, tile_y: int, halo: int) -> int:
+    return load_library().pond_set_launch(h, tile_x, tile_y, halo)
+
+
+def pond_autotune(h, scratch_ptr: int, nbytes: int, steps: int, flags: int):
+    t = pond_tuning()
+    rc = load_library().pond_autotune(h, ctypes.c_void_p(scratch_ptr), nbytes, steps, flags, ctypes.byref(t))
+    return rc, t
+
+
+def pond_autotune_clear() -> None:
+    load_library().pond_autotune_clear()
 
 
 def pond_sync(h) -> int:
@@ -389,6 +424,30 @@ class Simulation:
         with self.torch.cuda.device(self.device):
             rc, st = pond_get_stats(self.handle)
         return rc, st
+
+    # -- launch shape ---------------------------------------------------------------------
+    def launch(self) -> dict:
+        """Current tile and halo of the step kernel."""
+        t = pond_get_launch(self.handle)
+        return {"tile_x": t.tile_x, "tile_y": t.tile_y, "halo": t.halo}
+
+    def set_launch(self, tile_x: int, tile_y: int, halo: int):
+        with self.torch.cuda.device(self.device):
+            _check(pond_set_launch(self.handle, tile_x, tile_y, halo), "pond_set_launch")
+
+    def autotune(self, steps: int = 3, apply: bool = True, retime: bool = False) -> dict:
+        """Time the candidate launch shapes on a copy of the current state (pond_autotune)
+        and, with apply, use the fastest; the result is cached per problem class."""
+        torch = self.torch
+        flags = (POND_TUNE_APPLY if apply else 0) | (POND_TUNE_RETIME if retime else 0)
+        with torch.cuda.device(self.device):
+            scratch = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+            ptr = (_dptr(scratch) + 255) // 256 * 256
+            rc, t = pond_autotune(self.handle, ptr, self.ws_bytes, steps, flags)
+            self.stream.synchronize()
+            del scratch
+        _check(rc, "pond_autotune")
+        return t.as_dict()
 
     def sync(self):
         with self.torch.cuda.device(self.device):

@@ -19,7 +19,7 @@ def lib():
 
 def _declared():
     text = open(HEADER).read()
-    decl = r"^\s*(?:int|const\s+char\s*\*)\s*(pond_[a-z_]+)\s*\("
+    decl = r"^\s*(?:int|void|const\s+char\s*\*)\s*(pond_[a-z_]+)\s*\("
     return sorted(set(re.findall(decl, text, flags=re.MULTILINE)))
 
 
