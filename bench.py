@@ -66,6 +66,25 @@ def dist_init():
     return world, rank, local
 
 
+def max_over_ranks(step_ms, world, device=None):
+    """The slowest rank's time per step (every rank gets it); a barrier follows.  device:
+    where the reduction tensor lives (the rank's GPU under NCCL, the CPU under gloo)."""
+    if world <= 1:
+        return step_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_mlups(world, nodes_per_step, step_ms):
+    """Replicas (weak scaling): every rank advances its own copy of the workload, so the
+    job's throughput is the node updates of all ranks over the slowest rank's time."""
+    return world * nodes_per_step / (step_ms * 1e-3) / 1e6
+
+
 class ClockSampler:
     """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
 
@@ -126,14 +145,22 @@ def l2_flusher(torch, device):
     return flush
 
 
-def make_sims(pond, precision, device, stream):
+def make_sims(pond, precision, device, stream, tune=False):
+    """The four decay grids as one batch; with tune, the launch shape is picked by the
+    library's autotuner on the first grid and used for all four (same class)."""
     sims = []
     for ma in MACHS:
         cfg = pond.Config(nx=NX, ny=NY, precision=precision, gamma=GAMMA, mu=MU)
         s = pond.Simulation(cfg, device=device, stream=stream)
         s.set_state(*case_fields(ma))
         sims.append(s)
-    return sims, pond.Batch(sims, stream=stream)
+    tuning = None
+    if tune:
+        tuning = sims[0].autotune(steps=3, apply=True)
+        for s in sims[1:]:
+            s.set_launch(tuning["tile_x"], tuning["tile_y"], tuning["halo"])
+    batch = pond.Batch(sims, stream=stream)
+    return (sims, batch, tuning) if tune else (sims, batch)
 
 
 def time_steps(torch, batch, stream, steps, warmup, flush):
@@ -143,6 +170,7 @@ def time_steps(torch, batch, stream, steps, warmup, flush):
         batch.step(1)
     torch.cuda.synchronize()
     starts, ends = [], []
+    torch.cuda.nvtx.range_push("timed_steps")       # lets a profiler select the timed launches
     for _ in range(steps):
         flush()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -152,6 +180,7 @@ def time_steps(torch, batch, stream, steps, warmup, flush):
         e1.record(stream)
         starts.append(e0)
         ends.append(e1)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return [e0.elapsed_time(e1) for e0, e1 in zip(starts, ends)]
 
@@ -171,6 +200,11 @@ def tube_batch_rates(torch, pond, device, steps=20):
         sims.append(s)
     nodes = sum(c.nx * c.ny for c in cases)
     out = {"cases": len(cases), "nodes": nodes}
+    # launch shape: autotuned on the longest tube, used by every member (one class)
+    big = max(range(len(cases)), key=lambda i: cases[i].nx)
+    out["autotune"] = sims[big].autotune(steps=3, apply=True)
+    for s in sims:
+        s.set_launch(0, 0, out["autotune"]["halo"])
 
     def timed(fn):
         fn(2)
@@ -210,6 +244,7 @@ def config_rates(torch, pond, device, steps=6):
                           bc_y=case.bc_y, **kw)
         s = pond.Simulation(cfg, device=device, stream=stream)
         s.set_state(case.rho, case.ux, case.uy, case.T)
+        tuning = s.autotune(steps=2, apply=True)
         s.step(2)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -222,7 +257,8 @@ def config_rates(torch, pond, device, steps=6):
         s.close()
         return {"mlups": case.nx * case.ny * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6,
                 "pc_iters_mean": st.pc_iters_total / max(st.node_updates, 1),
-                "status": pond.strerror(rc)}
+                "status": pond.strerror(rc),
+                "launch_shape": "%dx%d halo %d" % (tuning["tile_x"], tuning["tile_y"], tuning["halo"])}
     out = {}
     rie = W.riemann2d(n=1024, seed=0)
     out["riemann_1024_total_fp32"] = rate(rie, steps, interp_order=2)
@@ -410,24 +446,19 @@ def main():
         dist.init_process_group("nccl", device_id=device)
 
     flush = l2_flusher(torch, device)
-    sims, batch = make_sims(pond, "fp32", device, stream)
+    sims, batch, tuning = make_sims(pond, "fp32", device, stream, tune=True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         per_launch = time_steps(torch, batch, stream, args.steps, args.warmup, flush)
-    step_ms = sum(per_launch) / args.steps
-    if world > 1:
-        t = torch.tensor([step_ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-        dist.barrier()
+    step_ms = max_over_ranks(sum(per_launch) / args.steps, world, device)
     K = mean_iters(sims)
     batch.close()
     for s in sims:
         s.close()
     nodes_per_step = len(MACHS) * NX * NY
-    value = world * nodes_per_step / (step_ms * 1e-3) / 1e6
+    value = whole_job_mlups(world, nodes_per_step, step_ms)
     launch_ms = sum(per_launch) / len(per_launch)
     flops_per_launch = nodes_per_step * (FLOP_PER_POP_ITER * 16 * K + FLOP_PER_UPDATE)
     achieved = flops_per_launch / (launch_ms * 1e-3) / 1e12
@@ -442,7 +473,7 @@ def main():
                           "achieved_tflops": achieved}))
         return 0
     # plain FP64 GPU step on the same workload (fewer steps: it is ~two orders slower)
-    sims64, batch64 = make_sims(pond, "fp64", device, stream)
+    sims64, batch64, tune64 = make_sims(pond, "fp64", device, stream, tune=True)
     per64 = time_steps(torch, batch64, stream, max(2, args.steps // 10), 1, flush)
     batch64.close()
     for s in sims64:
@@ -465,10 +496,15 @@ def main():
                    "precision": "mixed: FP32 arithmetic and non-equilibrium state, FP64 rho/u/T, "
                                 "compensated moment sums",
                    "l2": "flushed (256 MB write) before every timed step",
+                   "launch_shape": "tile %dx%d, halo %d (autotuned)" % (tuning["tile_x"], tuning["tile_y"],
+                                                                      tuning["halo"]),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "pc_iters_mean": K,
+        "autotune": tuning,
         "fp64": {"value": nodes_per_step / (fp64_ms * 1e-3) / 1e6, "unit": "MLUPS",
-                 "ms_per_step": fp64_ms, "speedup_mixed_over_fp64": fp64_ms / step_ms},
+                 "ms_per_step": fp64_ms, "speedup_mixed_over_fp64": fp64_ms / step_ms,
+                 "launch_shape": "tile %dx%d, halo %d (autotuned)" % (tune64["tile_x"], tune64["tile_y"],
+                                                                    tune64["halo"])},
         "l1_err_mixed_vs_fp64": err,
         "tube_batch": tubes,
         "other_configs": others,

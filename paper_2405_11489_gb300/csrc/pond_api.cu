@@ -858,7 +858,12 @@ int time_shape(pond_sim* s, void* scratch, size_t bytes, int tile_x, int tile_y,
     if (rc == POND_OK) rc = cuda_status(cudaEventRecord(e0, s->stream));
     if (rc == POND_OK) rc = pond_step(t, steps);
     if (rc == POND_OK) rc = cuda_status(cudaEventRecord(e1, s->stream));
-    if (rc == POND_OK) rc = sync_status(t);
+    if (rc == POND_OK) {
+        // kernel-side outcomes of the copy (a node that hit the iteration cap, a non-physical
+        // node) do not change the work timed; only runtime failures rule the shape out
+        rc = sync_status(t);
+        if (rc == POND_ENOCONV || rc == POND_ENONPHYSICAL) rc = POND_OK;
+    }
     float f = 0.f;
     if (rc == POND_OK) rc = cuda_status(cudaEventElapsedTime(&f, e0, e1));
     const int rd = pond_destroy(t);

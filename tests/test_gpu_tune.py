@@ -66,6 +66,17 @@ def test_quasi_1d_grids_keep_the_row_tile(pond):
     s.close()
 
 
+def test_autotune_times_states_whose_nodes_do_not_converge(pond):
+    pond.pond_autotune_clear()
+    case = W.riemann2d(n=64, seed=0)
+    s = _sim(pond, case, "fp32", interp_order=2, pc_max_iter=1)
+    s.step(1)
+    assert s.stats()[0] == pond.POND_ENOCONV
+    t = s.autotune(steps=1)
+    assert t["candidates"] >= 5
+    s.close()
+
+
 # shapes whose staged box fits shared memory (FP64 records are twice as large)
 SHAPES = [("fp64", 1e-12, (16, 16, 4)), ("fp64", 1e-12, (64, 4, 5)), ("fp64", 1e-12, (8, 32, 5)),
           ("fp32", 2e-6, (16, 16, 4)), ("fp32", 2e-6, (64, 4, 8)), ("fp32", 2e-6, (128, 2, 6)),
