@@ -1,0 +1,184 @@
+"""A third implementation of the PonD step in 50-digit arithmetic (mpmath), for tiny periodic
+grids: test infrastructure that pins the FP64 oracle's rounding.  It is written separately
+from the oracle (no shared code) and follows the paper with the same readings:
+
+- lattice: D1Q4 / D1Q5 Gauss-Hermite rules (Table I) in closed form, tensor products;
+- frame transformation (Eq. gradGeneralTransform, N = 3): Hermite coefficients of the
+  source populations about the target frame, A_pq = sum_j f_j He_p(xi_jx) He_q(xi_jy) with
+  xi_j = (C_j - u_bar)/sqrt(T_bar), p + q <= 3, and the target populations
+  w_i sum_{p+q<=3} A_pq He_p(c_ix) He_q(c_iy) / (p! q!);
+- streaming (Eq. propagationInterpolated): cubic Lagrange interpolation at the departure
+  point x - C_i(lambda_bar) of every stencil node's populations moved into lambda_bar;
+- predictor-corrector: guess = previous frame, exactly K iterations;
+- collision: project into the frame of the final moments, BGK with omega = 1/(tau + 1/2),
+  tau = mu/(rho T), f_eq = rho w_i, g_eq of the total or internal split (Sec. II);
+- internal split: G_i = -rho w_i (C_i - u).(d_t u + C_i . grad u) after the collision, with
+  d_t u = u^{n+1} - u^n and central differences of u^{n+1}.
+"""
+import mpmath as mp
+
+mp.mp.dps = 50
+
+
+def rule(q1):
+    """Table I: nodes and weights of the 1-D Gauss-Hermite rule (ascending nodes)."""
+    if q1 == 4:
+        s6 = mp.sqrt(6)
+        ci, co = mp.sqrt(3 - s6), mp.sqrt(3 + s6)
+        wi, wo = (3 + s6) / 12, (3 - s6) / 12
+        return [-co, -ci, ci, co], [wo, wi, wi, wo]
+    s10 = mp.sqrt(10)
+    ci, co = mp.sqrt(5 - s10), mp.sqrt(5 + s10)
+    wi, wo = (7 + 2 * s10) / 60, (7 - 2 * s10) / 60
+    return [-co, -ci, mp.mpf(0), ci, co], [wo, wi, mp.mpf(8) / 15, wi, wo]
+
+
+def he(n, x):
+    return (mp.mpf(1), x, x * x - 1, x * x * x - 3 * x)[n]
+
+
+FACT = (1, 1, 2, 6)
+ORDERS = [(p, q) for p in range(4) for q in range(4 - p)]
+
+
+class Lattice:
+    def __init__(self, q1):
+        c, w = rule(q1)
+        self.q1 = q1
+        self.Q = q1 * q1
+        self.cx = [c[i % q1] for i in range(self.Q)]      # population i = b q1 + a
+        self.cy = [c[i // q1] for i in range(self.Q)]
+        self.w = [w[i % q1] * w[i // q1] for i in range(self.Q)]
+
+
+def coefficients(lat, pops, src, dst):
+    """Hermite coefficients (p + q <= 3) about frame dst of populations given in frame src."""
+    sTs, sTd = mp.sqrt(src[2]), mp.sqrt(dst[2])
+    A = {pq: mp.mpf(0) for pq in ORDERS}
+    for j in range(lat.Q):
+        xi_x = (sTs * lat.cx[j] + src[0] - dst[0]) / sTd
+        xi_y = (sTs * lat.cy[j] + src[1] - dst[1]) / sTd
+        hx = [he(n, xi_x) for n in range(4)]
+        hy = [he(n, xi_y) for n in range(4)]
+        for (p, q) in ORDERS:
+            A[(p, q)] += pops[j] * hx[p] * hy[q]
+    return A
+
+
+def population(lat, A, i):
+    s = mp.mpf(0)
+    for (p, q) in ORDERS:
+        s += A[(p, q)] * he(p, lat.cx[i]) * he(q, lat.cy[i]) / (FACT[p] * FACT[q])
+    return lat.w[i] * s
+
+
+def cubic(xd):
+    b = mp.floor(xd)
+    t = xd - b
+    w = [-t * (t - 1) * (t - 2) / 6, (t + 1) * (t - 1) * (t - 2) / 2,
+         -(t + 1) * t * (t - 2) / 2, (t + 1) * t * (t - 1) / 6]
+    return int(b) - 1, w
+
+
+def g_eq(lat, i, split, rho, fr, cv):
+    sT = mp.sqrt(fr[2])
+    Cx, Cy = sT * lat.cx[i] + fr[0], sT * lat.cy[i] + fr[1]
+    if split == "total":
+        kin = (Cx * Cx + Cy * Cy) / 2
+    else:
+        kin = ((Cx - fr[0]) ** 2 + (Cy - fr[1]) ** 2) / 2
+    return ((cv - 1) * fr[2] + kin) * rho * lat.w[i]
+
+
+def moments(lat, P, G, fr, split, cv):
+    sT = mp.sqrt(fr[2])
+    rho = sum(P)
+    jx = sum((sT * lat.cx[i] + fr[0]) * P[i] for i in range(lat.Q))
+    jy = sum((sT * lat.cy[i] + fr[1]) * P[i] for i in range(lat.Q))
+    ux, uy = jx / rho, jy / rho
+    if split == "total":
+        T = (sum(G) / rho - (ux * ux + uy * uy) / 2) / cv
+    else:
+        T = sum(G) / (rho * cv)
+    return rho, ux, uy, T
+
+
+def init(lat, nx, ny, rho, ux, uy, T, split, gamma):
+    """Equilibrium state from double fields [ny][nx]; pops [n][i], frames [n]."""
+    cv = 1 / (mp.mpf(gamma) - 1)
+    st = {"f": [], "g": [], "fr": []}
+    for y in range(ny):
+        for x in range(nx):
+            r = mp.mpf(float(rho[y][x]))
+            fr = (mp.mpf(float(ux[y][x])), mp.mpf(float(uy[y][x])), mp.mpf(float(T[y][x])))
+            st["f"].append([r * lat.w[i] for i in range(lat.Q)])
+            st["g"].append([g_eq(lat, i, split, r, fr, cv) for i in range(lat.Q)])
+            st["fr"].append(fr)
+    return st
+
+
+def step(lat, st, nx, ny, split, gamma, mu, K):
+    """One time step of the whole (periodic) grid with exactly K PC iterations per node."""
+    cv = 1 / (mp.mpf(gamma) - 1)
+    mu = mp.mpf(mu)
+    out = {"f": [], "g": [], "fr": []}
+    for y in range(ny):
+        for x in range(nx):
+            bar = st["fr"][y * nx + x]
+            for k in range(K):
+                cache = {}
+                sT = mp.sqrt(bar[2])
+                P, G = [], []
+                for i in range(lat.Q):
+                    bx, wx = cubic(x - (sT * lat.cx[i] + bar[0]))
+                    by, wy = cubic(y - (sT * lat.cy[i] + bar[1]))
+                    fi = gi = mp.mpf(0)
+                    for ky in range(4):
+                        for kx in range(4):
+                            s = ((by + ky) % ny) * nx + (bx + kx) % nx
+                            if s not in cache:
+                                cache[s] = (coefficients(lat, st["f"][s], st["fr"][s], bar),
+                                            coefficients(lat, st["g"][s], st["fr"][s], bar))
+                            W = wx[kx] * wy[ky]
+                            fi += W * population(lat, cache[s][0], i)
+                            gi += W * population(lat, cache[s][1], i)
+                    P.append(fi)
+                    G.append(gi)
+                m = moments(lat, P, G, bar, split, cv)
+                if k < K - 1:
+                    bar = (m[1], m[2], m[3])
+            rho, star = m[0], (m[1], m[2], m[3])
+            Af = coefficients(lat, P, bar, star)
+            Ag = coefficients(lat, G, bar, star)
+            omega = 1 / (mu / (rho * star[2]) + mp.mpf(1) / 2)
+            fo, go = [], []
+            for i in range(lat.Q):
+                fp, gp = population(lat, Af, i), population(lat, Ag, i)
+                fo.append(fp + omega * (rho * lat.w[i] - fp))
+                go.append(gp + omega * (g_eq(lat, i, split, rho, star, cv) - gp))
+            out["f"].append(fo)
+            out["g"].append(go)
+            out["fr"].append(star)
+    if split == "internal":
+        internal_source(lat, st, out, nx, ny)
+    return out
+
+
+def internal_source(lat, before, after, nx, ny):
+    ux = [fr[0] for fr in after["fr"]]
+    uy = [fr[1] for fr in after["fr"]]
+    for y in range(ny):
+        for x in range(nx):
+            n = y * nx + x
+            xp, xm = y * nx + (x + 1) % nx, y * nx + (x - 1) % nx
+            yp, ym = ((y + 1) % ny) * nx + x, ((y - 1) % ny) * nx + x
+            dxux, dyux = (ux[xp] - ux[xm]) / 2, (ux[yp] - ux[ym]) / 2
+            dxuy, dyuy = (uy[xp] - uy[xm]) / 2, (uy[yp] - uy[ym]) / 2
+            dtux, dtuy = ux[n] - before["fr"][n][0], uy[n] - before["fr"][n][1]
+            rho = sum(after["f"][n])
+            sT = mp.sqrt(after["fr"][n][2])
+            for i in range(lat.Q):
+                Cx, Cy = sT * lat.cx[i] + ux[n], sT * lat.cy[i] + uy[n]
+                ax = dtux + Cx * dxux + Cy * dyux
+                ay = dtuy + Cx * dxuy + Cy * dyuy
+                after["g"][n][i] += -rho * lat.w[i] * ((Cx - ux[n]) * ax + (Cy - uy[n]) * ay)
