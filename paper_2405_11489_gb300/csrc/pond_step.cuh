@@ -27,8 +27,9 @@
 // evaluated in the working precision R, so in mixed precision FP32 only ever carries
 // deviations and no FP64 multiply, divide or square root is needed in the loops.
 //
-// Interpolation.  FP32 (shared-memory bound): for each a, the x pass is done once per row of
-// the union of the y stencils of all b and then added to the b's whose y stencil contains
+// Interpolation.  FP32: for each a, the x pass is done once per row of the union of the y
+// stencils of all b and folded at once (make_phi / z_contract) into the four values that the
+// populations (a, b) need along y, which are then added to the b's whose y stencil contains
 // the row.  FP64 (FP64-pipe bound): each population is interpolated directly.
 //
 // A stencil that leaves the staged box (a frame far outside the per-tile estimate) is read
@@ -287,6 +288,50 @@ __device__ __forceinline__ void make_gamma(const LatRow<R>& la, R wab, const Tau
         }
 }
 
+// Folded x factors of population column a for the FP32 2-D path.  A population (a, b) of the
+// target frame is w_a w_b sum_q hn_b(q) sum_l ty_ql sum_{p <= 3-q} hn_a(p) sum_{k <= p} tx_pk R_kl
+// (the move lambda_r -> lambda_bar and the Grad reconstruction, R = interpolated coefficients
+// in lambda_r).  Everything but hn_b(q) and the y interpolation is independent of b, so each
+// x-interpolated row X (10 values) is contracted at once into four values
+//   Z_q = sum_{l <= q, k <= 3-q} phi_q(k, l) X_kl,  phi_q(k, l) = ty_ql w_a sum_{p=k}^{3-q} hn_a(p) tx_pk,
+// and only the Z_q are interpolated along y.  phi holds the 20 factors in the order z_contract
+// reads them: q = 0..3, then l = 0..q, then k = 0..3-q.
+template <class R>
+__device__ __forceinline__ void make_phi(const LatRow<R>& la, const Tau<R>& tx, const Tau<R>& ty, R* phi)
+{
+    int n = 0;
+#pragma unroll
+    for (int q = 0; q <= 3; ++q) {
+        R S[4];
+#pragma unroll
+        for (int k = 0; k <= 3 - q; ++k) {
+            R v = R(0);
+#pragma unroll
+            for (int p = k; p <= 3 - q; ++p) v += la.hn[p] * tau_at(tx, p, k);
+            S[k] = la.w * v;
+        }
+#pragma unroll
+        for (int l = 0; l <= q; ++l)
+#pragma unroll
+            for (int k = 0; k <= 3 - q; ++k) phi[n++] = tau_at(ty, q, l) * S[k];
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void z_contract(const R* phi, const R* X, R* Z)
+{
+    int n = 0;
+#pragma unroll
+    for (int q = 0; q <= 3; ++q) {
+        R z = R(0);
+#pragma unroll
+        for (int l = 0; l <= q; ++l)
+#pragma unroll
+            for (int k = 0; k <= 3 - q; ++k) z += phi[n++] * X[slot(k, l)];
+        Z[q] = z;
+    }
+}
+
 // Node-interleaved shared-memory records: 20 values per node, f in 0..9 and g in 10..19.
 template <class R>
 __device__ __forceinline__ void store20(R* dst, const R* v)
@@ -342,14 +387,11 @@ __device__ __forceinline__ R pick(const R* w, int j, int n)
     return v;
 }
 
-// Bytes of dynamic shared memory of the step kernel for a tile of `nodes` nodes: the staged
-// box (20 values per node) and, for the FP32 2-D kernel, a per-thread cache of the per-b
-// factors V (10 values per b).
+// Bytes of dynamic shared memory of the step kernel: the staged box, 20 values per node.
 __host__ __device__ constexpr size_t step_smem_bytes(int rbytes, int q1, bool one_d, int box_w,
                                                      int box_h, int nodes)
 {
-    return (size_t)box_w * box_h * 2 * NCOEF * rbytes +
-           ((rbytes == 4 && !one_d) ? (size_t)q1 * NCOEF * nodes * 4 : 0);
+    return (void)q1, (void)one_d, (void)nodes, (size_t)box_w * box_h * 2 * NCOEF * rbytes;
 }
 
 template <class R>
@@ -580,8 +622,6 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     footprint_box<ONE_D, TPB / 32>(p, pp, TX, TY, active, ux0, uy0, T0, red, box, tid);
     const int ox = box[0], oy = box[1], bw = box[2], bh = box[3];
     const int bn = bw * bh;
-    // per-thread V cache after the box capacity (FP32 2-D kernel)
-    R* sV = sm + (size_t)pp.box_w * pp.box_h * 2 * NCOEF;
 
     // ---- staging: source deviations in the reference frame --------------------------------
     // Node-interleaved layout: node i holds its 20 values (f: 0..9, g: 10..19) contiguously,
@@ -614,8 +654,9 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
             const R isT = R(1) / sT;
             const R iTb = isT * isT;
             const R sig_t = rbT * iTb;                             // T_r / T_bar - 1
-            const Tau<R> txr = make_tau_sig<R>(sTr * isT, rbx * isT, sig_t);
-            const Tau<R> tyr = make_tau_sig<R>(sTr * isT, rby * isT, sig_t);
+            const R s_rb = sTr * isT, dx_rb = rbx * isT, dy_rb = rby * isT;   // lambda_r -> lambda_bar
+            const Tau<R> txr = make_tau_sig<R>(s_rb, dx_rb, sig_t);
+            const Tau<R> tyr = make_tau_sig<R>(s_rb, dy_rb, sig_t);
             const R ubxr = rf.uxR - rbx, ubyr = rf.uyR - rby;      // u_bar
 #pragma unroll
             for (int m = 0; m < NCOEF; ++m) { Af[m] = R(0); Ag[m] = R(0); }
@@ -689,8 +730,7 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                         }
                 }
             } else if constexpr (kSharedX) {
-                // y stencils of all b and the per-b factors V (shared by every a and both
-                // distributions); V goes to this thread's shared-memory cache.
+                // y stencils of all b (shared by every a and both distributions)
                 R wy[Q1][P];
                 int jy[Q1];
                 int rmin = 1 << 30, rmax = -(1 << 30);
@@ -699,28 +739,32 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                     jy[b] = lagrange<R, P>(-(sT * lat[b].c + ubyr), wy[b]);
                     rmin = min(rmin, jy[b]);
                     rmax = max(rmax, jy[b] + P - 1);
-                    R V[NCOEF];
-                    make_V<R>(lat[b], tyr, V);
-#pragma unroll
-                    for (int m = 0; m < NCOEF; ++m) sV[(b * NCOEF + m) * TPB + tid] = V[m];
                 }
                 const bool rows_in = (y + rmin - oy >= 0) && (y + rmax - oy < bh);
-#pragma unroll
-                for (int d = 0; d < 2; ++d) {
 #pragma unroll 1
-                    for (int a = 0; a < Q1; ++a) {
-                        const LatRow<R>& la = lat[a];
-                        R wx[P];
-                        const int jx = lagrange<R, P>(-(sT * la.c + ubxr), wx);
-                        const int tx0 = x + jx - ox;
-                        // x pass once per row of the union of the y stencils, then the row is
-                        // added to the populations (a, b) whose y stencil contains it
-                        R acc[Q1][NCOEF];
+                for (int a = 0; a < Q1; ++a) {
+                    const LatRow<R>& la = lat[a];
+                    R wx[P];
+                    const int jx = lagrange<R, P>(-(sT * la.c + ubxr), wx);
+                    const int tx0 = x + jx - ox;
+                    const bool cols_in = tx0 >= 0 && tx0 + P <= bw;
+                    R phi[2 * NCOEF];
+                    {
+                        // the iteration's moves, rebuilt here so that only four scalars stay live
+                        const Tau<R> tx = make_tau_sig<R>(s_rb, dx_rb, sig_t);
+                        const Tau<R> ty = make_tau_sig<R>(s_rb, dy_rb, sig_t);
+                        make_phi<R>(la, tx, ty, phi);
+                    }
+#pragma unroll
+                    for (int d = 0; d < 2; ++d) {
+                        // x pass once per row of the union of the y stencils, folded into Z_q,
+                        // then added to the b's whose y stencil contains the row
+                        R acc[Q1][4];
 #pragma unroll
                         for (int b = 0; b < Q1; ++b)
 #pragma unroll
-                            for (int m = 0; m < NCOEF; ++m) acc[b][m] = R(0);
-                        if (rows_in && tx0 >= 0 && tx0 + P <= bw) {
+                            for (int q = 0; q < 4; ++q) acc[b][q] = R(0);
+                        if (rows_in && cols_in) {
                             const R* rowp = sm + ((size_t)(y + rmin - oy) * bw + tx0) * 2 * NCOEF;
 #pragma unroll 1
                             for (int r = rmin; r <= rmax; ++r, rowp += (size_t)bw * 2 * NCOEF) {
@@ -739,13 +783,15 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
 #pragma unroll
                                     for (int m = 0; m < NCOEF; ++m) X[m] += wx[ii] * v[m];
                                 }
+                                R Z[4];
+                                z_contract<R>(phi, X, Z);
 #pragma unroll
                                 for (int b = 0; b < Q1; ++b) {
                                     const int j = r - jy[b];
                                     if ((unsigned)j < (unsigned)P) {     // warp-uniform in smooth flow
                                         const R w = pick<R>(wy[b], j, P);
 #pragma unroll
-                                        for (int m = 0; m < NCOEF; ++m) acc[b][m] += w * X[m];
+                                        for (int q = 0; q < 4; ++q) acc[b][q] += w * Z[q];
                                     }
                                 }
                             }
@@ -762,34 +808,32 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                                     for (int ii = 0; ii < P; ++ii) {
                                         const R wxi = pick<R>(wx, ii, P);
                                         const int sx = bc_map(x + jx + ii, p.nx, p.bc_x);
-                                        R D[2 * NCOEF];
+                                        R D[2 * NCOEF], Z[4];
                                         source_dev<S, R>(p, rf, (long long)sy * p.nx + sx, D, D + NCOEF);
+                                        z_contract<R>(phi, D + d * NCOEF, Z);
 #pragma unroll
-                                        for (int m = 0; m < NCOEF; ++m) acc[b][m] += wyj * wxi * D[d * NCOEF + m];
+                                        for (int q = 0; q < 4; ++q) acc[b][q] += wyj * wxi * Z[q];
                                     }
                                 }
                         }
-                        // populations (a, b): f'_ab = gamma_ab . acc_b; their Hermite moments
+                        // populations (a, b): f'_ab = w_b sum_q hn_b(q) acc_b(q); their moments
                         R Sq[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
                         for (int b = 0; b < Q1; ++b) {
                             const LatRow<R>& lb = lat[b];
-                            R V[NCOEF], gam[NCOEF];
-#pragma unroll
-                            for (int m = 0; m < NCOEF; ++m) V[m] = sV[(b * NCOEF + m) * TPB + tid];
-                            make_gamma<R>(la, la.w * lb.w, txr, V, gam);
                             R val = R(0);
 #pragma unroll
-                            for (int m = 0; m < NCOEF; ++m) val += gam[m] * acc[b][m];
+                            for (int q = 0; q < 4; ++q) val += lb.hn[q] * acc[b][q];
+                            val *= lb.w;
 #pragma unroll
                             for (int q = 0; q < 4; ++q) Sq[q] += val * lb.he[q];
                         }
 #pragma unroll
-                        for (int pp = 0; pp <= 3; ++pp)
+                        for (int pq = 0; pq <= 3; ++pq)
 #pragma unroll
-                            for (int q = 0; q <= 3 - pp; ++q) {
-                                if (d == 0) Af[slot(pp, q)] += la.he[pp] * Sq[q];
-                                else Ag[slot(pp, q)] += la.he[pp] * Sq[q];
+                            for (int q = 0; q <= 3 - pq; ++q) {
+                                if (d == 0) Af[slot(pq, q)] += la.he[pq] * Sq[q];
+                                else Ag[slot(pq, q)] += la.he[pq] * Sq[q];
                             }
                     }
                 }
