@@ -27,10 +27,10 @@
 // evaluated in the working precision R, so in mixed precision FP32 only ever carries
 // deviations and no FP64 multiply, divide or square root is needed in the loops.
 //
-// Interpolation.  FP32: for each a, the x pass is done once per row of the union of the y
-// stencils of all b and folded at once (make_phi / z_contract) into the four values that the
+// Interpolation.  For each a, the x pass is done once per row of the union of the y stencils
+// of all b and folded at once (make_phi / z_contract) into the four values that the
 // populations (a, b) need along y, which are then added to the b's whose y stencil contains
-// the row.  FP64 (FP64-pipe bound): each population is interpolated directly.
+// the row.  Quasi-1-D grids fold the single row once per a.
 //
 // A stencil that leaves the staged box (a frame far outside the per-tile estimate) is read
 // from global memory instead, node by node, and counted.
@@ -250,43 +250,6 @@ template <class R>
 struct LatRow {
     R c, w, he[4], hn[4];
 };
-
-// V_b(p, l) = sum_{q = l}^{3 - p} hn_b(q) ty_ql (shared by all a of one b).
-template <class R>
-__device__ __forceinline__ void make_V(const LatRow<R>& lb, const Tau<R>& ty, R* V)
-{
-#pragma unroll
-    for (int pp = 0; pp <= 3; ++pp)
-#pragma unroll
-        for (int l = 0; l <= 3 - pp; ++l) {
-            R v = R(0);
-#pragma unroll
-            for (int q = l; q <= 3 - pp; ++q) v += lb.hn[q] * tau_at(ty, q, l);
-            V[slot(pp, l)] = v;
-        }
-}
-
-// gamma_kl of population (a, b): f_ab = sum_kl gamma_kl R_kl for coefficients R in lambda_r,
-//   gamma_kl = w_a w_b sum_{p >= k, q >= l, p + q <= 3} hn_a(p) tx_pk hn_b(q) ty_ql.
-template <class R>
-__device__ __forceinline__ void make_gamma(const LatRow<R>& la, R wab, const Tau<R>& tx, const R* V,
-                                           R* gam)
-{
-    R U[4][4];
-#pragma unroll
-    for (int pp = 0; pp <= 3; ++pp)
-#pragma unroll
-        for (int k = 0; k <= pp; ++k) U[pp][k] = la.hn[pp] * tau_at(tx, pp, k);
-#pragma unroll
-    for (int k = 0; k <= 3; ++k)
-#pragma unroll
-        for (int l = 0; l <= 3 - k; ++l) {
-            R g = R(0);
-#pragma unroll
-            for (int pp = k; pp <= 3 - l; ++pp) g += U[pp][k] * V[slot(pp, l)];
-            gam[slot(k, l)] = wab * g;
-        }
-}
 
 // Folded x factors of population column a for the FP32 2-D path.  A population (a, b) of the
 // target frame is w_a w_b sum_q hn_b(q) sum_l ty_ql sum_{p <= 3-q} hn_a(p) sum_{k <= p} tx_pk R_kl
@@ -595,7 +558,6 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     __shared__ LatRow<R> lat[Q1];
     __shared__ RefState<R> srf;
     __shared__ CaseRun scase;
-    constexpr bool kSharedX = !ONE_D && std::is_same<R, float>::value;
     const int TX = blockDim.x, TY = blockDim.y;
     const int tid = threadIdx.y * TX + threadIdx.x;
     if (tid == 0) resolve_case(pp, scase);
@@ -661,75 +623,7 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
 #pragma unroll
             for (int m = 0; m < NCOEF; ++m) { Af[m] = R(0); Ag[m] = R(0); }
 
-            if constexpr (!ONE_D && std::is_same<R, double>::value) {
-                // FP64: bound by the FP64 pipe, so each population is interpolated directly
-                // (16 taps x 20 values), which needs the fewest multiply-adds.
-#pragma unroll 1
-                for (int b = 0; b < Q1; ++b) {
-                    const LatRow<R>& lb = lat[b];
-                    R wy[P];
-                    const int jy = lagrange<R, P>(-(sT * lb.c + ubyr), wy);
-                    const int ty0 = y + jy - oy;
-                    R V[NCOEF];
-                    make_V<R>(lb, tyr, V);
-                    R Sf[4] = {R(0), R(0), R(0), R(0)}, Sg[4] = {R(0), R(0), R(0), R(0)};
-#pragma unroll 1
-                    for (int a = 0; a < Q1; ++a) {
-                        const LatRow<R>& la = lat[a];
-                        R wx[P];
-                        const int jx = lagrange<R, P>(-(sT * la.c + ubxr), wx);
-                        const int tx0 = x + jx - ox;
-                        R gam[NCOEF];
-                        make_gamma<R>(la, la.w * lb.w, txr, V, gam);
-                        R Ri[2 * NCOEF];
-#pragma unroll
-                        for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] = R(0);
-                        if (tx0 >= 0 && tx0 + P <= bw && ty0 >= 0 && ty0 + P <= bh) {
-#pragma unroll
-                            for (int j = 0; j < P; ++j)
-#pragma unroll
-                                for (int ii = 0; ii < P; ++ii) {
-                                    const R W = wy[j] * wx[ii];
-                                    const R* src = sm + ((size_t)(ty0 + j) * bw + tx0 + ii) * 2 * NCOEF;
-#pragma unroll
-                                    for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] += W * src[m];
-                                }
-                        } else {
-                            ++fallbacks;
-#pragma unroll 1
-                            for (int j = 0; j < P; ++j)
-#pragma unroll 1
-                                for (int ii = 0; ii < P; ++ii) {
-                                    const R W = pick<R>(wy, j, P) * pick<R>(wx, ii, P);
-                                    const int sx = bc_map(x + jx + ii, p.nx, p.bc_x);
-                                    const int sy = bc_map(y + jy + j, p.ny, p.bc_y);
-                                    R D[2 * NCOEF];
-                                    source_dev<S, R>(p, rf, (long long)sy * p.nx + sx, D, D + NCOEF);
-#pragma unroll
-                                    for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] += W * D[m];
-                                }
-                        }
-                        R f = R(0), g = R(0);
-#pragma unroll
-                        for (int m = 0; m < NCOEF; ++m) {
-                            f += gam[m] * Ri[m];
-                            g += gam[m] * Ri[NCOEF + m];
-                        }
-#pragma unroll
-                        for (int pp = 0; pp < 4; ++pp) {
-                            Sf[pp] += f * la.he[pp];
-                            Sg[pp] += g * la.he[pp];
-                        }
-                    }
-#pragma unroll
-                    for (int pp = 0; pp <= 3; ++pp)
-#pragma unroll
-                        for (int q = 0; q <= 3 - pp; ++q) {
-                            Af[slot(pp, q)] += Sf[pp] * lb.he[q];
-                            Ag[slot(pp, q)] += Sg[pp] * lb.he[q];
-                        }
-                }
-            } else if constexpr (kSharedX) {
+            if constexpr (!ONE_D) {
                 // y stencils of all b (shared by every a and both distributions)
                 R wy[Q1][P];
                 int jy[Q1];
@@ -872,19 +766,24 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                             for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] += W * D[m];
                         }
                     }
+                    // the y taps all read row 0 with weights summing to one, so every b sees
+                    // the same folded values Z (see make_phi)
+                    R phi[2 * NCOEF], Zf[4], Zg[4];
+                    make_phi<R>(la, txr, tyr, phi);
+                    z_contract<R>(phi, Ri, Zf);
+                    z_contract<R>(phi, Ri + NCOEF, Zg);
                     R Sf[4] = {R(0), R(0), R(0), R(0)}, Sg[4] = {R(0), R(0), R(0), R(0)};
-#pragma unroll 1
+#pragma unroll
                     for (int b = 0; b < Q1; ++b) {
                         const LatRow<R>& lb = lat[b];
-                        R V[NCOEF], gam[NCOEF];
-                        make_V<R>(lb, tyr, V);
-                        make_gamma<R>(la, la.w * lb.w, txr, V, gam);
                         R f = R(0), g = R(0);
 #pragma unroll
-                        for (int m = 0; m < NCOEF; ++m) {
-                            f += gam[m] * Ri[m];
-                            g += gam[m] * Ri[NCOEF + m];
+                        for (int q = 0; q < 4; ++q) {
+                            f += lb.hn[q] * Zf[q];
+                            g += lb.hn[q] * Zg[q];
                         }
+                        f *= lb.w;
+                        g *= lb.w;
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             Sf[q] += f * lb.he[q];
