@@ -339,6 +339,29 @@ __device__ __forceinline__ void load10(const R* rec, R* v)
     }
 }
 
+// The values of ND distributions of one record starting at distribution d0 (ND = 2: all 20).
+template <class R, int ND>
+__device__ __forceinline__ void load_dist(const R* rec, int d0, R* v)
+{
+    if constexpr (ND == 2) {
+        if constexpr (std::is_same<R, float>::value) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const float4 t = reinterpret_cast<const float4*>(rec)[k];
+                v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 10; ++k) {
+                const double2 t = reinterpret_cast<const double2*>(rec)[k];
+                v[2 * k] = t.x; v[2 * k + 1] = t.y;
+            }
+        }
+    } else {
+        if (d0 == 0) load10<R, 0>(rec, v); else load10<R, 1>(rec, v);
+    }
+}
+
 // w[j] for a runtime j < n <= 4 without indexing the register array dynamically.
 template <class R>
 __device__ __forceinline__ R pick(const R* w, int j, int n)
@@ -649,43 +672,48 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                         const Tau<R> ty = make_tau_sig<R>(s_rb, dy_rb, sig_t);
                         make_phi<R>(la, tx, ty, phi);
                     }
+                    // FP32: both distributions in one pass over the rows (each record is five
+                    // 16-byte loads and the row overhead is shared); FP64: one pass each
+                    constexpr int ND = std::is_same<R, float>::value ? 2 : 1;
 #pragma unroll
-                    for (int d = 0; d < 2; ++d) {
+                    for (int d0 = 0; d0 < 2; d0 += ND) {
                         // x pass once per row of the union of the y stencils, folded into Z_q,
                         // then added to the b's whose y stencil contains the row
-                        R acc[Q1][4];
+                        R acc[ND][Q1][4];
 #pragma unroll
-                        for (int b = 0; b < Q1; ++b)
+                        for (int e = 0; e < ND; ++e)
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) acc[b][q] = R(0);
+                            for (int b = 0; b < Q1; ++b)
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) acc[e][b][q] = R(0);
                         if (rows_in && cols_in) {
                             const R* rowp = sm + ((size_t)(y + rmin - oy) * bw + tx0) * 2 * NCOEF;
 #pragma unroll 1
                             for (int r = rmin; r <= rmax; ++r, rowp += (size_t)bw * 2 * NCOEF) {
-                                R X[NCOEF];
-                                {
-                                    R v[NCOEF];
-                                    if (d == 0) load10<R, 0>(rowp, v); else load10<R, 1>(rowp, v);
+                                R X[ND][NCOEF];
 #pragma unroll
-                                    for (int m = 0; m < NCOEF; ++m) X[m] = wx[0] * v[m];
+                                for (int ii = 0; ii < P; ++ii) {
+                                    R v[ND * NCOEF];
+                                    load_dist<R, ND>(rowp + ii * 2 * NCOEF, d0, v);
+#pragma unroll
+                                    for (int e = 0; e < ND; ++e)
+#pragma unroll
+                                        for (int m = 0; m < NCOEF; ++m)
+                                            X[e][m] = (ii == 0) ? wx[0] * v[e * NCOEF + m]
+                                                                : X[e][m] + wx[ii] * v[e * NCOEF + m];
                                 }
+                                R Z[ND][4];
 #pragma unroll
-                                for (int ii = 1; ii < P; ++ii) {
-                                    R v[NCOEF];
-                                    const R* q = rowp + ii * 2 * NCOEF;
-                                    if (d == 0) load10<R, 0>(q, v); else load10<R, 1>(q, v);
-#pragma unroll
-                                    for (int m = 0; m < NCOEF; ++m) X[m] += wx[ii] * v[m];
-                                }
-                                R Z[4];
-                                z_contract<R>(phi, X, Z);
+                                for (int e = 0; e < ND; ++e) z_contract<R>(phi, X[e], Z[e]);
 #pragma unroll
                                 for (int b = 0; b < Q1; ++b) {
                                     const int j = r - jy[b];
                                     if ((unsigned)j < (unsigned)P) {     // warp-uniform in smooth flow
                                         const R w = pick<R>(wy[b], j, P);
 #pragma unroll
-                                        for (int q = 0; q < 4; ++q) acc[b][q] += w * Z[q];
+                                        for (int e = 0; e < ND; ++e)
+#pragma unroll
+                                            for (int q = 0; q < 4; ++q) acc[e][b][q] += w * Z[e][q];
                                     }
                                 }
                             }
@@ -702,33 +730,40 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                                     for (int ii = 0; ii < P; ++ii) {
                                         const R wxi = pick<R>(wx, ii, P);
                                         const int sx = bc_map(x + jx + ii, p.nx, p.bc_x);
-                                        R D[2 * NCOEF], Z[4];
+                                        R D[2 * NCOEF];
                                         source_dev<S, R>(p, rf, (long long)sy * p.nx + sx, D, D + NCOEF);
-                                        z_contract<R>(phi, D + d * NCOEF, Z);
 #pragma unroll
-                                        for (int q = 0; q < 4; ++q) acc[b][q] += wyj * wxi * Z[q];
+                                        for (int e = 0; e < ND; ++e) {
+                                            R Z[4];
+                                            z_contract<R>(phi, D + (d0 + e) * NCOEF, Z);
+#pragma unroll
+                                            for (int q = 0; q < 4; ++q) acc[e][b][q] += wyj * wxi * Z[q];
+                                        }
                                     }
                                 }
                         }
                         // populations (a, b): f'_ab = w_b sum_q hn_b(q) acc_b(q); their moments
-                        R Sq[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
-                        for (int b = 0; b < Q1; ++b) {
-                            const LatRow<R>& lb = lat[b];
-                            R val = R(0);
+                        for (int e = 0; e < ND; ++e) {
+                            R Sq[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) val += lb.hn[q] * acc[b][q];
-                            val *= lb.w;
+                            for (int b = 0; b < Q1; ++b) {
+                                const LatRow<R>& lb = lat[b];
+                                R val = R(0);
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) Sq[q] += val * lb.he[q];
-                        }
+                                for (int q = 0; q < 4; ++q) val += lb.hn[q] * acc[e][b][q];
+                                val *= lb.w;
 #pragma unroll
-                        for (int pq = 0; pq <= 3; ++pq)
-#pragma unroll
-                            for (int q = 0; q <= 3 - pq; ++q) {
-                                if (d == 0) Af[slot(pq, q)] += la.he[pq] * Sq[q];
-                                else Ag[slot(pq, q)] += la.he[pq] * Sq[q];
+                                for (int q = 0; q < 4; ++q) Sq[q] += val * lb.he[q];
                             }
+#pragma unroll
+                            for (int pq = 0; pq <= 3; ++pq)
+#pragma unroll
+                                for (int q = 0; q <= 3 - pq; ++q) {
+                                    if (d0 + e == 0) Af[slot(pq, q)] += la.he[pq] * Sq[q];
+                                    else Ag[slot(pq, q)] += la.he[pq] * Sq[q];
+                                }
+                        }
                     }
                 }
             } else {
