@@ -308,6 +308,61 @@ def l1_error(pond, device, stream, nsteps=200):
     return {"steps": nsteps, "rel_l1": out}
 
 
+def decay_physics(torch, pond, device, steps=2000):
+    """The 256^2 decay configuration over `steps` steps in mixed FP32 and in FP64: decay of the
+    shear wave's Fourier mode against exp(-nu k^2 t), nu = mu / rho (Sec. III.B), of the
+    thermal pulse's peak against 2-D diffusion sigma0^2 / (sigma0^2 + 2 alpha t) with
+    alpha = nu (Pr = 1), the drift of total mass, momentum and energy, and the per-field
+    relative L1 difference of the FP32 result from the FP64 one."""
+    k = 2 * math.pi / NX
+    shear_expected = math.exp(-MU * k * k * steps)
+    sigma0 = 16.0
+    pulse_expected = sigma0 ** 2 / (sigma0 ** 2 + 2 * MU * steps)
+    cv = 1.0 / (GAMMA - 1.0)
+
+    def totals(f):
+        rho, ux, uy, T = f
+        E = rho * (cv * T + 0.5 * (ux * ux + uy * uy))
+        return np.array([rho.sum(), (rho * ux).sum(), (rho * uy).sum(), E.sum()])
+
+    def measure(fields0, fields):
+        uy0, uy1 = fields0[2], fields[2]
+        a0 = abs(np.fft.fft(uy0.mean(axis=0))[1])
+        a1 = abs(np.fft.fft(uy1.mean(axis=0))[1])
+        p0 = (fields0[3] - np.median(fields0[3])).max()
+        p1 = (fields[3] - np.median(fields[3])).max()
+        t0, t1 = totals(fields0), totals(fields)
+        drift = np.abs(t1 - t0) / np.maximum(np.abs(t0), [1.0, 1.0, 1.0, 1.0])
+        return a1 / a0, p1 / p0, drift
+
+    out = {"steps": steps, "shear_expected": shear_expected, "pulse_expected": pulse_expected}
+    finals = {}
+    for prec in ("fp32", "fp64"):
+        stream = torch.cuda.current_stream(device)
+        sims, batch = make_sims(pond, prec, device, stream)
+        f0 = [s.moments() for s in sims]
+        batch.step(steps)
+        stream.synchronize()
+        f1 = [s.moments() for s in sims]
+        res = [measure(a, b) for a, b in zip(f0, f1)]
+        out[prec] = {"shear_ratio_over_expected": [r[0] / shear_expected for r in res],
+                     "pulse_ratio_over_expected": [r[1] / pulse_expected for r in res],
+                     "max_drift_mass_momx_momy_energy": np.max([r[2] for r in res], axis=0).tolist(),
+                     "statuses": sorted({pond.strerror(s.stats()[0]) for s in sims})}
+        finals[prec] = f1
+        batch.close()
+        for s in sims:
+            s.close()
+    l1 = {}
+    for name, idx in (("rho", 0), ("ux", 1), ("uy", 2), ("T", 3)):
+        num = sum(np.abs(a[idx] - b[idx]).sum() for a, b in zip(finals["fp32"], finals["fp64"]))
+        den = sum(np.abs(b[idx]).sum() for b in finals["fp64"])
+        l1[name] = num / den
+    out["l1_fp32_vs_fp64"] = l1
+    out["machs"] = list(MACHS)
+    return out
+
+
 def e2e_rate(torch, pond, device, steps, warmup):
     """MLUPS through the public C-ABI with host buffers: every step uploads the step's input
     fields from pinned host memory (pond_set_state), advances one time step (pond_step) and
@@ -480,6 +535,7 @@ def main():
         s.close()
     fp64_ms = sum(per64) / max(2, args.steps // 10)
     err = l1_error(pond, device, stream)
+    decay = decay_physics(torch, pond, device)
     e2e = e2e_rate(torch, pond, device, steps=max(5, args.steps), warmup=3)
     tubes = tube_batch_rates(torch, pond, device)
     others = config_rates(torch, pond, device)
@@ -506,6 +562,7 @@ def main():
                  "launch_shape": "tile %dx%d, halo %d (autotuned)" % (tune64["tile_x"], tune64["tile_y"],
                                                                     tune64["halo"])},
         "l1_err_mixed_vs_fp64": err,
+        "decay_2000": decay,
         "tube_batch": tubes,
         "other_configs": others,
         "serving": serving,
