@@ -56,17 +56,20 @@ class Config(ctypes.Structure):
         ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
         ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("pc_tol", ctypes.c_double),
         ("pc_max_iter", ctypes.c_int32), ("pc_fixed_iters", ctypes.c_int32),
+        ("grad_order", ctypes.c_int32),
     ]
 
 
 def make_config(nx, ny, lattice=16, split="total", interp_order=3, bc_x="periodic",
                 bc_y="periodic", gamma=1.4, mu=1e-4, pc_tol=1e-12, pc_max_iter=20,
-                pc_fixed_iters=0) -> Config:
+                pc_fixed_iters=0, grad_order=0) -> Config:
+    """split: "total", "internal" or "nt" (non-translational); grad_order: N = 3 or 4
+    (0: the lattice's, 3 on D2Q16 and 4 on D2Q25)."""
     bc = {"periodic": 0, "outflow": 1}
     return Config(nx=nx, ny=ny, q1={16: 4, 25: 5}[lattice],
-                  split={"total": 0, "internal": 1}[split], interp_order=interp_order,
+                  split={"total": 0, "internal": 1, "nt": 2}[split], interp_order=interp_order,
                   bc_x=bc[bc_x], bc_y=bc[bc_y], gamma=gamma, mu=mu, pc_tol=pc_tol,
-                  pc_max_iter=pc_max_iter, pc_fixed_iters=pc_fixed_iters)
+                  pc_max_iter=pc_max_iter, pc_fixed_iters=pc_fixed_iters, grad_order=grad_order)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -81,6 +84,7 @@ def _lib_handle():
             lib.or_lattice_1d.argtypes = [ctypes.c_int, _D, _D]
             lib.or_grad_transform.argtypes = [ctypes.c_int, _D] + [ctypes.c_double] * 6 + [_D]
             lib.or_grad_coefficients.argtypes = [ctypes.c_int, _D] + [ctypes.c_double] * 6 + [_D]
+            lib.or_grad_transform_n.argtypes = [ctypes.c_int, ctypes.c_int, _D] + [ctypes.c_double] * 6 + [_D]
             lib.or_init.argtypes = [P(Config)] + [_D] * 8
             lib.or_moments_field.argtypes = [P(Config)] + [_D] * 10
             lib.or_stream_node.argtypes = ([P(Config)] + [_D] * 5 + [ctypes.c_int] * 2
@@ -121,6 +125,16 @@ def grad_transform(pops, src_frame, dst_frame, lattice=16):
     out = np.zeros_like(src)
     _lib_handle().or_grad_transform(q1, _p(src), *map(float, src_frame), *map(float, dst_frame),
                                     _p(out))
+    return out
+
+
+def grad_transform_n(pops, src_frame, dst_frame, lattice=25, order=4):
+    """The frame transformation with Grad order N = order (3 or 4)."""
+    q1 = {16: 4, 25: 5}[lattice]
+    src = np.ascontiguousarray(pops, dtype=np.float64)
+    out = np.zeros_like(src)
+    _lib_handle().or_grad_transform_n(q1, order, _p(src), *map(float, src_frame),
+                                      *map(float, dst_frame), _p(out))
     return out
 
 

@@ -23,7 +23,10 @@
  * Readings taken where the paper is silent (each is listed with its reason in the
  * design notes of the repository):
  *   - discrete BGK: f* = f + omega (f_eq - f), omega = 1/(tau + 1/2), tau = mu/p;
- *   - Grad expansion order N = 3 (all coefficients of total order <= 3);
+ *   - Grad expansion order N = the Hermite order the lattice carries: N = 3 (all
+ *     coefficients of total order <= 3) on D2Q16, N = 4 on D2Q25 (the non-translational
+ *     split needs the fourth-order moments of f, Sec. III.A; and with N = 3 the D2Q25
+ *     total split loses stability at Ma ~ 1.5-2); either can be forced by grad_order;
  *   - W(x - x_s) is evaluated at the departure point x - C_i(lambda_bar) dt;
  *   - cubic (4-point) Lagrange interpolation by default, 3-point as an option;
  *   - predictor-corrector: guess = previous frame of the node, metric
@@ -31,7 +34,8 @@
  *     exactly K iterations in fixed mode;
  *   - collision in the frame of the final moments, after projecting into it;
  *   - internal-energy split source: f -> f_eq inside the source, backward time
- *     difference of u against the frame before the step, central space differences.
+ *     difference of u against the frame before the step, central space differences;
+ *   - non-translational split: E = sum g + sum |C|^2/2 f, g_eq = (U'/rho) f_eq.
  */
 #include <math.h>
 #include <stdint.h>
@@ -44,14 +48,21 @@
 typedef struct {
     int32_t nx, ny;
     int32_t q1;            /* 4 -> D2Q16, 5 -> D2Q25 (Table I) */
-    int32_t split;         /* 0 total-energy split, 1 internal-energy split (Eq. Es) */
+    int32_t split;         /* 0 total, 1 internal, 2 non-translational energy split (Eq. Es) */
     int32_t interp_order;  /* 3 -> 4-point cubic Lagrange, 2 -> 3-point quadratic */
     int32_t bc_x, bc_y;    /* 0 periodic, 1 outflow (index clamp, zero gradient) */
     double gamma, mu;      /* adiabatic exponent (Eq. spec_heat), dynamic viscosity (Eq. kin_visc) */
     double pc_tol;
     int32_t pc_max_iter;
     int32_t pc_fixed_iters; /* > 0: exactly this many predictor-corrector iterations */
+    int32_t grad_order;     /* Grad expansion order N: 3 or 4; 0 = the lattice's (3 on D2Q16, 4 on D2Q25) */
 } or_config;
+
+static int grad_order_of(const or_config *cfg)
+{
+    if (cfg->grad_order == 3 || cfg->grad_order == 4) return cfg->grad_order;
+    return cfg->q1 == 5 ? 4 : 3;
+}
 
 /* ---------------------------------------------------------------------------------- */
 /* Table I: one-dimensional Gauss-Hermite quadratures with r T_L = 1.                  */
@@ -103,7 +114,7 @@ static void make_lattice(int q1, or_lattice *L)
 /* Hermite tensors H^(n)(xi), n <= 3, in D = 2 (probabilists' normalisation, r T_L = 1) */
 /* ---------------------------------------------------------------------------------- */
 typedef struct {
-    double h0, h1[2], h2[2][2], h3[2][2][2];
+    double h0, h1[2], h2[2][2], h3[2][2][2], h4[2][2][2][2];
 } or_tensors;
 
 static double kron(int a, int b) { return a == b ? 1.0 : 0.0; }
@@ -120,10 +131,19 @@ static void hermite_tensors(double xi_x, double xi_y, or_tensors *H)
             for (int g = 0; g < 2; ++g)
                 H->h3[a][b][g] = xi[a] * xi[b] * xi[g]
                                - xi[a] * kron(b, g) - xi[b] * kron(a, g) - xi[g] * kron(a, b);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int g = 0; g < 2; ++g)
+                for (int d = 0; d < 2; ++d)
+                    H->h4[a][b][g][d] = xi[a] * xi[b] * xi[g] * xi[d]
+                        - xi[a] * xi[b] * kron(g, d) - xi[a] * xi[g] * kron(b, d)
+                        - xi[a] * xi[d] * kron(b, g) - xi[b] * xi[g] * kron(a, d)
+                        - xi[b] * xi[d] * kron(a, g) - xi[g] * xi[d] * kron(a, b)
+                        + kron(a, b) * kron(g, d) + kron(a, g) * kron(b, d) + kron(a, d) * kron(b, g);
 }
 
 /* ---------------------------------------------------------------------------------- */
-/* Frame transformation M_{lambda}^{lambda_bar}, Eq. (gradGeneralTransform), N = 3.    */
+/* Frame transformation M_{lambda}^{lambda_bar}, Eq. (gradGeneralTransform), N = 3, 4. */
 /* a_n = sum_j f_j H^(n)((C_j(lambda) - u_bar)/sqrt(T_bar)); the populations of the    */
 /* target frame are f_i = w_i sum_n a_n : H^(n)(c_i) / n!.                             */
 /* ---------------------------------------------------------------------------------- */
@@ -149,22 +169,31 @@ static void grad_coefficients(const or_lattice *L, const double *pops, int strid
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
                 for (int g = 0; g < 2; ++g) A->h3[a][b][g] += fj * H.h3[a][b][g];
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int g = 0; g < 2; ++g)
+                    for (int d = 0; d < 2; ++d) A->h4[a][b][g][d] += fj * H.h4[a][b][g][d];
     }
 }
 
-/* Full Frobenius contraction of every rank (no symmetry shortcut), divided by n!. */
-static double grad_population(const or_lattice *L, const or_tensors *A, int i)
+/* Full Frobenius contraction of every rank up to N (no symmetry shortcut), divided by n!. */
+static double grad_population(const or_lattice *L, const or_tensors *A, int i, int order)
 {
     or_tensors H;
     hermite_tensors(L->cx[i], L->cy[i], &H);
-    double s0 = A->h0 * H.h0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    double s0 = A->h0 * H.h0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
     for (int a = 0; a < 2; ++a) s1 += A->h1[a] * H.h1[a];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) s2 += A->h2[a][b] * H.h2[a][b];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             for (int g = 0; g < 2; ++g) s3 += A->h3[a][b][g] * H.h3[a][b][g];
-    return L->w[i] * (s0 + s1 + s2 / 2.0 + s3 / 6.0);
+    if (order >= 4)
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int g = 0; g < 2; ++g)
+                    for (int d = 0; d < 2; ++d) s4 += A->h4[a][b][g][d] * H.h4[a][b][g][d];
+    return L->w[i] * (s0 + s1 + s2 / 2.0 + s3 / 6.0 + s4 / 24.0);
 }
 
 /* Exported for the tests: transform Q populations from frame src to frame dst. */
@@ -176,7 +205,19 @@ void or_grad_transform(int q1, const double *pops_src, double sux, double suy, d
     or_frame s = {sux, suy, sT}, d = {dux, duy, dT};
     or_tensors A;
     grad_coefficients(&L, pops_src, 1, s, d, &A);
-    for (int i = 0; i < L.Q; ++i) pops_dst[i] = grad_population(&L, &A, i);
+    for (int i = 0; i < L.Q; ++i) pops_dst[i] = grad_population(&L, &A, i, 3);
+}
+
+/* Exported for the tests: the same transformation with Grad order N (3 or 4). */
+void or_grad_transform_n(int q1, int order, const double *pops_src, double sux, double suy, double sT,
+                         double dux, double duy, double dT, double *pops_dst)
+{
+    or_lattice L;
+    make_lattice(q1, &L);
+    or_frame s = {sux, suy, sT}, d = {dux, duy, dT};
+    or_tensors A;
+    grad_coefficients(&L, pops_src, 1, s, d, &A);
+    for (int i = 0; i < L.Q; ++i) pops_dst[i] = grad_population(&L, &A, i, order);
 }
 
 /* Exported for the tests: the Grad coefficient tensors in frame dst, flattened as
@@ -207,8 +248,9 @@ static double cv_of(double gamma) { return 1.0 / (gamma - 1.0); }   /* Eq. spec_
 /* f_eq_i = rho w_i in the frame lambda = (u, T) (Sec. III.A). */
 static double feq_pop(const or_lattice *L, int i, double rho) { return rho * L->w[i]; }
 
-/* g_eq_i = (U'/rho + |v|^2/2) f_eq (total split) or (U'/rho + |v - u|^2/2) f_eq (internal
- * split) at v = C_i(lambda); U' = U - rho D T / 2 = rho (c_v - 1) T for D = 2. */
+/* g_eq_i = (U'/rho + |v|^2/2) f_eq (total split), (U'/rho + |v - u|^2/2) f_eq (internal
+ * split) or (U'/rho) f_eq (non-translational split) at v = C_i(lambda);
+ * U' = U - rho D T / 2 = rho (c_v - 1) T for D = 2. */
 static double geq_pop(const or_lattice *L, int i, int split, double rho, or_frame fr, double cv)
 {
     double sT = sqrt(fr.T);
@@ -217,8 +259,10 @@ static double geq_pop(const or_lattice *L, int i, int split, double rho, or_fram
     double kin;
     if (split == 0)
         kin = 0.5 * (Cx * Cx + Cy * Cy);
-    else
+    else if (split == 1)
         kin = 0.5 * ((Cx - fr.ux) * (Cx - fr.ux) + (Cy - fr.uy) * (Cy - fr.uy));
+    else
+        kin = 0.0;
     return (Uprime_over_rho + kin) * feq_pop(L, i, rho);
 }
 
@@ -244,8 +288,9 @@ int or_init(const or_config *cfg, const double *rho, const double *ux, const dou
 }
 
 /* ---------------------------------------------------------------------------------- */
-/* Moments (Sec. II): rho = sum f, rho u = sum C f; total split E = sum g; internal    */
-/* split U = sum g, E = U + rho u^2/2.  T from E = rho c_v T + rho u^2 / 2.            */
+/* Moments (Sec. II): rho = sum f, rho u = sum C f; total split E = sum g; internal     */
+/* split U = sum g, E = U + rho u^2/2; non-translational split E = sum g + sum C^2/2 f. */
+/* T from E = rho c_v T + rho u^2 / 2.                                                 */
 /* ---------------------------------------------------------------------------------- */
 typedef struct { double rho, ux, uy, T, E; } or_moments;
 
@@ -253,7 +298,7 @@ static or_moments moments_of(const or_lattice *L, const double *f, const double 
                              or_frame fr, int split, double cv)
 {
     double sT = sqrt(fr.T);
-    double rho = 0.0, jx = 0.0, jy = 0.0, G = 0.0;
+    double rho = 0.0, jx = 0.0, jy = 0.0, G = 0.0, K2 = 0.0;
     for (int i = 0; i < L->Q; ++i) {
         double fi = f[(size_t)i * stride], gi = g[(size_t)i * stride];
         double Cx = sT * L->cx[i] + fr.ux, Cy = sT * L->cy[i] + fr.uy;
@@ -261,6 +306,7 @@ static or_moments moments_of(const or_lattice *L, const double *f, const double 
         jx += Cx * fi;
         jy += Cy * fi;
         G += gi;
+        K2 += 0.5 * (Cx * Cx + Cy * Cy) * fi;
     }
     or_moments m;
     m.rho = rho;
@@ -270,9 +316,12 @@ static or_moments moments_of(const or_lattice *L, const double *f, const double 
     if (split == 0) {
         m.E = G;
         m.T = (G / rho - 0.5 * u2) / cv;
-    } else {
+    } else if (split == 1) {
         m.E = G + 0.5 * rho * u2;
         m.T = G / (rho * cv);
+    } else {
+        m.E = G + K2;
+        m.T = (m.E / rho - 0.5 * u2) / cv;
     }
     return m;
 }
@@ -397,8 +446,8 @@ static void stream_node(const or_src *S, or_memo *M, int x, int y, or_frame bar,
                 const or_tensors *Af, *Ag;
                 source_coefficients(S, M, sx, sy, bar, &Af, &Ag);
                 double W = wx[kx] * wy[ky];
-                fi += W * grad_population(L, Af, i);
-                gi += W * grad_population(L, Ag, i);
+                fi += W * grad_population(L, Af, i, grad_order_of(cfg));
+                gi += W * grad_population(L, Ag, i, grad_order_of(cfg));
             }
         }
         P[i] = fi;
@@ -437,8 +486,8 @@ static void collide_node(const or_lattice *L, const or_config *cfg, const double
     double tau = cfg->mu / (rho * m.T);             /* Eq. kin_visc: tau = mu / p, p = rho T */
     double omega = 1.0 / (tau + 0.5);
     for (int i = 0; i < L->Q; ++i) {
-        double fp = grad_population(L, &Af, i);
-        double gp = grad_population(L, &Ag, i);
+        double fp = grad_population(L, &Af, i, grad_order_of(cfg));
+        double gp = grad_population(L, &Ag, i, grad_order_of(cfg));
         double fe = feq_pop(L, i, rho);
         double ge = geq_pop(L, i, cfg->split, rho, star, cv);
         fo[i] = fp + omega * (fe - fp);

@@ -3,15 +3,16 @@ grids: test infrastructure that pins the FP64 oracle's rounding.  It is written 
 from the oracle (no shared code) and follows the paper with the same readings:
 
 - lattice: D1Q4 / D1Q5 Gauss-Hermite rules (Table I) in closed form, tensor products;
-- frame transformation (Eq. gradGeneralTransform, N = 3): Hermite coefficients of the
-  source populations about the target frame, A_pq = sum_j f_j He_p(xi_jx) He_q(xi_jy) with
-  xi_j = (C_j - u_bar)/sqrt(T_bar), p + q <= 3, and the target populations
-  w_i sum_{p+q<=3} A_pq He_p(c_ix) He_q(c_iy) / (p! q!);
+- frame transformation (Eq. gradGeneralTransform, N = 3 on D2Q16, 4 on D2Q25): Hermite
+  coefficients of the source populations about the target frame,
+  A_pq = sum_j f_j He_p(xi_jx) He_q(xi_jy) with xi_j = (C_j - u_bar)/sqrt(T_bar),
+  p + q <= N, and the target populations w_i sum_{p+q<=N} A_pq He_p(c_ix) He_q(c_iy) / (p! q!);
 - streaming (Eq. propagationInterpolated): cubic Lagrange interpolation at the departure
   point x - C_i(lambda_bar) of every stencil node's populations moved into lambda_bar;
 - predictor-corrector: guess = previous frame, exactly K iterations;
 - collision: project into the frame of the final moments, BGK with omega = 1/(tau + 1/2),
-  tau = mu/(rho T), f_eq = rho w_i, g_eq of the total or internal split (Sec. II);
+  tau = mu/(rho T), f_eq = rho w_i, g_eq of the total, internal or non-translational split
+  (Sec. II; the last with E = sum g + sum |C|^2/2 f);
 - internal split: G_i = -rho w_i (C_i - u).(d_t u + C_i . grad u) after the collision, with
   d_t u = u^{n+1} - u^n and central differences of u^{n+1}.
 """
@@ -34,17 +35,18 @@ def rule(q1):
 
 
 def he(n, x):
-    return (mp.mpf(1), x, x * x - 1, x * x * x - 3 * x)[n]
+    return (mp.mpf(1), x, x * x - 1, x * x * x - 3 * x, x ** 4 - 6 * x * x + 3)[n]
 
 
-FACT = (1, 1, 2, 6)
-ORDERS = [(p, q) for p in range(4) for q in range(4 - p)]
+FACT = (1, 1, 2, 6, 24)
 
 
 class Lattice:
-    def __init__(self, q1):
+    def __init__(self, q1, N=None):
         c, w = rule(q1)
         self.q1 = q1
+        self.N = N if N else (4 if q1 == 5 else 3)
+        self.orders = [(p, q) for p in range(self.N + 1) for q in range(self.N + 1 - p)]
         self.Q = q1 * q1
         self.cx = [c[i % q1] for i in range(self.Q)]      # population i = b q1 + a
         self.cy = [c[i // q1] for i in range(self.Q)]
@@ -52,22 +54,22 @@ class Lattice:
 
 
 def coefficients(lat, pops, src, dst):
-    """Hermite coefficients (p + q <= 3) about frame dst of populations given in frame src."""
+    """Hermite coefficients (p + q <= N) about frame dst of populations given in frame src."""
     sTs, sTd = mp.sqrt(src[2]), mp.sqrt(dst[2])
-    A = {pq: mp.mpf(0) for pq in ORDERS}
+    A = {pq: mp.mpf(0) for pq in lat.orders}
     for j in range(lat.Q):
         xi_x = (sTs * lat.cx[j] + src[0] - dst[0]) / sTd
         xi_y = (sTs * lat.cy[j] + src[1] - dst[1]) / sTd
-        hx = [he(n, xi_x) for n in range(4)]
-        hy = [he(n, xi_y) for n in range(4)]
-        for (p, q) in ORDERS:
+        hx = [he(n, xi_x) for n in range(lat.N + 1)]
+        hy = [he(n, xi_y) for n in range(lat.N + 1)]
+        for (p, q) in lat.orders:
             A[(p, q)] += pops[j] * hx[p] * hy[q]
     return A
 
 
 def population(lat, A, i):
     s = mp.mpf(0)
-    for (p, q) in ORDERS:
+    for (p, q) in lat.orders:
         s += A[(p, q)] * he(p, lat.cx[i]) * he(q, lat.cy[i]) / (FACT[p] * FACT[q])
     return lat.w[i] * s
 
@@ -85,8 +87,10 @@ def g_eq(lat, i, split, rho, fr, cv):
     Cx, Cy = sT * lat.cx[i] + fr[0], sT * lat.cy[i] + fr[1]
     if split == "total":
         kin = (Cx * Cx + Cy * Cy) / 2
-    else:
+    elif split == "internal":
         kin = ((Cx - fr[0]) ** 2 + (Cy - fr[1]) ** 2) / 2
+    else:
+        kin = 0
     return ((cv - 1) * fr[2] + kin) * rho * lat.w[i]
 
 
@@ -98,8 +102,12 @@ def moments(lat, P, G, fr, split, cv):
     ux, uy = jx / rho, jy / rho
     if split == "total":
         T = (sum(G) / rho - (ux * ux + uy * uy) / 2) / cv
-    else:
+    elif split == "internal":
         T = sum(G) / (rho * cv)
+    else:
+        K2 = sum(((sT * lat.cx[i] + fr[0]) ** 2 + (sT * lat.cy[i] + fr[1]) ** 2) / 2 * P[i]
+                 for i in range(lat.Q))
+        T = ((sum(G) + K2) / rho - (ux * ux + uy * uy) / 2) / cv
     return rho, ux, uy, T
 
 

@@ -55,7 +55,7 @@ def make_pair(pond, orc, nx, ny, lattice=16, split="total", order=3, bc=("period
               K=2, tol=1e-12, precision="fp64", halo=0, gamma=1.4, mu=0.02, maxit=20):
     ocfg = orc.make_config(nx, ny, lattice=lattice, split=split, interp_order=order, bc_x=bc[0],
                            bc_y=bc[1], gamma=gamma, mu=mu, pc_tol=tol, pc_max_iter=maxit,
-                           pc_fixed_iters=K)
+                           pc_fixed_iters=K, grad_order=3)
     gcfg = pond.Config(nx=nx, ny=ny, lattice=lattice, split=split, precision=precision,
                        interp_order=order, bc_x=bc[0], bc_y=bc[1], gamma=gamma, mu=mu, pc_tol=tol,
                        pc_max_iter=maxit, pc_fixed_iters=K, halo=halo)

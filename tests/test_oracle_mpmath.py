@@ -1,7 +1,7 @@
 """Pin of the FP64 oracle's rounding: a 3x3 and a 4x3 periodic grid stepped twice by the
 oracle and by a separate 50-digit implementation (tests/mp_reference.py) with the same
-readings agree to FP64 round-off in every population and frame value, for both energy
-splits and both lattices."""
+readings agree to FP64 round-off in every population and frame value, for the three energy
+splits and both lattices (Grad order N = 3 on D2Q16, 4 on D2Q25)."""
 import math
 
 import numpy as np
@@ -20,7 +20,8 @@ def _fields(nx, ny):
 
 
 @pytest.mark.parametrize("nx,ny,lattice,split", [(3, 3, 16, "total"), (3, 3, 16, "internal"),
-                                                 (4, 3, 25, "total")])
+                                                 (4, 3, 25, "total"), (3, 3, 25, "nt"),
+                                                 (3, 3, 16, "nt")])
 def test_oracle_matches_50_digit_step(orc, nx, ny, lattice, split):
     gamma, mu, K, steps = 1.4, 0.05, 2, 2
     fields = _fields(nx, ny)

@@ -1,0 +1,161 @@
+"""Pins of the oracle's non-translational energy split (Eq. Es, third line: E = sum g +
+sum v^2/2 f, g_eq = (U'/rho) f_eq) and of the order-4 Grad transformation that the split
+needs (Sec. III.A: its energy involves the fourth-order moments of f, so D2Q25 and N = 4):
+
+- the N = 4 transformation on D2Q25 keeps every moment of total order <= 4 (N = 3 only <= 3)
+  and is a projection;
+- equilibria of the split return the (rho, u, T) they were built from, up to Ma 3;
+- collision conserves rho, rho u and E = sum g + sum |C|^2/2 f per node;
+- a uniform supersonic flow stays uniform;
+- shear and entropy waves decay at k^2 nu and k^2 alpha with nu = alpha = tau T (Pr = 1),
+  like the other splits (the hydrodynamic limit is the same, Sec. II).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2405_11489_gb300 import workloads as W
+
+
+def _moments(P, cx, cy, frame, order):
+    sT = math.sqrt(frame[2])
+    Cx, Cy = sT * cx + frame[0], sT * cy + frame[1]
+    return [max(abs((P * Cx ** m * Cy ** (o - m)).sum()) for m in range(o + 1)) for o in range(order + 1)], (Cx, Cy)
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_order_n_transform_keeps_moments_up_to_n(orc, N):
+    cx, cy, w = orc.lattice_2d(25)
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        f = w * (1.0 + 0.2 * rng.standard_normal(25))
+        src = (rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.5, 1.5))
+        dst = (src[0] + rng.uniform(-0.3, 0.3), src[1] + rng.uniform(-0.3, 0.3), src[2] * rng.uniform(0.8, 1.25))
+        t = orc.grad_transform_n(f, src, dst, 25, N)
+        s = math.sqrt(src[2]); d = math.sqrt(dst[2])
+        Cs = (s * cx + src[0], s * cy + src[1])
+        Cd = (d * cx + dst[0], d * cy + dst[1])
+        for o in range(6):
+            err = max(abs((f * Cs[0] ** m * Cs[1] ** (o - m)).sum() - (t * Cd[0] ** m * Cd[1] ** (o - m)).sum())
+                      for m in range(o + 1))
+            if o <= N:
+                assert err < 1e-13
+            elif o == N + 1:
+                assert err > 1e-6          # the next order is not kept
+        # projection: transforming the result again (into its own frame) changes nothing
+        t2 = orc.grad_transform_n(t, dst, dst, 25, N)
+        assert np.allclose(t2, t, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("lattice,N", [(16, 3), (25, 4)])
+def test_nt_equilibrium_returns_its_state(orc, lattice, N):
+    rng = np.random.default_rng(5)
+    gamma = 1.4
+    cfg = orc.make_config(6, 1, lattice=lattice, split="nt", gamma=gamma, grad_order=N)
+    T = rng.uniform(0.3, 2.0, (1, 6))
+    ma = rng.uniform(0.0, 3.0, (1, 6))
+    ang = rng.uniform(0, 2 * math.pi, (1, 6))
+    u = ma * np.sqrt(gamma * T)
+    rho = rng.uniform(0.2, 3.0, (1, 6))
+    st = orc.init_state(cfg, rho, u * np.cos(ang), u * np.sin(ang), T)
+    r, vx, vy, TT, E = orc.moments(cfg, st)
+    cv = 1.0 / (gamma - 1.0)
+    assert np.allclose(r, rho, rtol=1e-13) and np.allclose(TT, T, rtol=1e-12)
+    assert np.allclose(vx, u * np.cos(ang), rtol=0, atol=1e-12)
+    assert np.allclose(E, rho * (cv * T + 0.5 * u * u), rtol=1e-12)
+    # g carries only the non-translational part U' = rho (c_v - 1) T
+    assert np.allclose(st.g.sum(axis=0), rho * (cv - 1.0) * T, rtol=1e-13)
+
+
+@pytest.mark.parametrize("lattice,N", [(16, 3), (25, 4)])
+def test_nt_collision_conserves_per_node(orc, lattice, N):
+    rng = np.random.default_rng(22)
+    cfg = orc.make_config(1, 1, lattice=lattice, split="nt", mu=0.02, grad_order=N)
+    cx, cy, w = orc.lattice_2d(lattice)
+    Q = lattice
+    for _ in range(8):
+        frame = (rng.uniform(-2, 2), rng.uniform(-2, 2), rng.uniform(0.3, 2.0))
+        st = orc.init_state(cfg, rng.uniform(0.5, 2.0), frame[0] + 0.1, frame[1] - 0.1, frame[2] * 1.1)
+        P = st.f[:, 0, 0] * (1 + 0.05 * rng.standard_normal(Q))
+        G = st.g[:, 0, 0] * (1 + 0.05 * rng.standard_normal(Q))
+        fo, go, star = orc.collide_node(cfg, P, G, frame)
+        sT, tT = math.sqrt(frame[2]), math.sqrt(star[2])
+        Cx, Cy = sT * cx + frame[0], sT * cy + frame[1]
+        Sx, Sy = tT * cx + star[0], tT * cy + star[1]
+        E0 = G.sum() + (0.5 * (Cx * Cx + Cy * Cy) * P).sum()
+        E1 = go.sum() + (0.5 * (Sx * Sx + Sy * Sy) * fo).sum()
+        assert abs(fo.sum() - P.sum()) < 1e-13 * P.sum()
+        assert abs((fo * Sx).sum() - (P * Cx).sum()) < 3e-12 * P.sum()
+        assert abs((fo * Sy).sum() - (P * Cy).sum()) < 3e-12 * P.sum()
+        assert abs(E1 - E0) < 1e-12 * abs(E0)
+
+
+@pytest.mark.parametrize("lattice,N", [(16, 3), (25, 4)])
+def test_nt_uniform_supersonic_flow_stays_uniform(orc, lattice, N):
+    gamma, T = 1.4, 0.6
+    u = 3.0 * math.sqrt(gamma * T)
+    cfg = orc.make_config(7, 5, lattice=lattice, split="nt", gamma=gamma, mu=0.01, grad_order=N)
+    st = orc.init_state(cfg, 1.3, u * math.cos(0.3), u * math.sin(0.3), T)
+    st0 = st.copy()
+    for _ in range(3):
+        r = orc.step(cfg, st)
+        assert r.status == 0 and np.all(r.iters == 1)
+        st = r.state
+    assert np.allclose(st.f, st0.f, rtol=1e-13, atol=0)
+    assert np.allclose(st.g, st0.g, rtol=1e-13, atol=0)
+
+
+def _mode(field, n):
+    x = np.arange(n)
+    return 2.0 * abs(np.mean(field * np.exp(-2j * math.pi * x / n)))
+
+
+def test_nt_shear_wave_decay_rate(orc):
+    case = W.shear_wave(n=48, ny=1, ma=1.0, amp=1e-3, mu=0.05, steps=200)
+    cfg = orc.make_config(case.nx, 1, lattice=25, split="nt", grad_order=4, gamma=case.gamma, mu=case.mu)
+    st = orc.init_state(cfg, case.rho, case.ux, case.uy, case.T)
+    ts, amps = [], []
+    for s in range(case.steps):
+        st = orc.step(cfg, st).state
+        if s % 50 == 49:
+            ts.append(s + 1)
+            amps.append(_mode(orc.moments(cfg, st)[2][0], case.nx))
+    nu = -np.polyfit(ts, np.log(amps), 1)[0] / case.meta["k"] ** 2
+    assert abs(nu / case.mu - 1.0) < 0.03
+
+
+def test_nt_thermal_wave_decay_rate(orc):
+    case = W.thermal_wave(n=96, amp=1e-3, mu=0.05, steps=500)
+    cfg = orc.make_config(case.nx, case.ny, lattice=25, split="nt", grad_order=4, gamma=case.gamma,
+                          mu=case.mu)
+    st = orc.init_state(cfg, case.rho, case.ux, case.uy, case.T)
+    ts, amps = [], []
+    for s in range(case.steps):
+        st = orc.step(cfg, st).state
+        if s >= 149 and s % 50 == 49:
+            ts.append(s + 1)
+            amps.append(_mode(orc.moments(cfg, st)[3][0] - 1.0, case.nx))
+    alpha = -np.polyfit(ts, np.log(amps), 1)[0] / case.meta["k"] ** 2
+    assert abs(alpha / case.mu - 1.0) < 0.02
+
+
+def test_d2q25_needs_order_4_at_high_mach(orc):
+    """With N = 3 the D2Q25 total split amplifies a Ma = 2 entropy wave until the
+    predictor-corrector stops converging; with N = 4 (the order D2Q25 carries, the default)
+    the same run stays at the initial amplitude and converges in two iterations."""
+    case = W.thermal_wave(n=96, amp=1e-3, mu=0.05, steps=200, ma=2.0)
+    out = {}
+    for N in (3, 4):
+        cfg = orc.make_config(case.nx, case.ny, lattice=25, split="total", grad_order=N,
+                              gamma=case.gamma, mu=case.mu)
+        st = orc.init_state(cfg, case.rho, case.ux, case.uy, case.T)
+        status = 0
+        for _ in range(case.steps):
+            r = orc.step(cfg, st)
+            st = r.state
+            status = status or r.status
+        T = orc.moments(cfg, st)[3]
+        out[N] = (status, np.nanmax(np.abs(T - 1.0)), r.iters.max())
+    assert out[3][0] == -5 or out[3][1] > 1e-2           # N = 3: non-convergence / growth
+    assert out[4][0] == 0 and out[4][1] < 1.01e-3 and out[4][2] <= 2

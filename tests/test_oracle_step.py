@@ -45,8 +45,10 @@ def test_uniform_supersonic_flow_stays_uniform(orc, lattice, split):
         assert r.status == 0
         assert np.all(r.iters == 1)
         st = r.state
-    assert np.allclose(st.f, st0.f, rtol=1e-13, atol=0)
-    assert np.allclose(st.g, st0.g, rtol=1e-13, atol=0)
+    # D2Q25 carries order-4 Hermite terms (N = 4), which at |xi| ~ 5 round a few times more
+    rtol = 1e-13 if lattice == 16 else 3e-13
+    assert np.allclose(st.f, st0.f, rtol=rtol, atol=0)
+    assert np.allclose(st.g, st0.g, rtol=rtol, atol=0)
     assert np.allclose(st.ux, st0.ux, rtol=1e-13) and np.allclose(st.T, st0.T, rtol=1e-13)
 
 
