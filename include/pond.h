@@ -53,14 +53,16 @@ typedef enum {
 } pond_status_t;
 
 enum { POND_D2Q16 = 16, POND_D2Q25 = 25 };                       /* Table I lattices */
-enum { POND_SPLIT_TOTAL = 0, POND_SPLIT_INTERNAL = 1 };           /* Eq. Es, lines 1 and 2 */
+enum { POND_SPLIT_TOTAL = 0, POND_SPLIT_INTERNAL = 1, POND_SPLIT_NT = 2 };   /* Eq. Es, lines 1-3 */
 enum { POND_FP64 = 0, POND_MIXED_FP32 = 1, POND_MIXED_FP16 = 2, POND_MIXED_BF16 = 3 };
 enum { POND_BC_PERIODIC = 0, POND_BC_OUTFLOW = 1 };
 
 typedef struct {
     int32_t nx, ny;            /* grid; ny = 1 runs the quasi-1-D form (all y taps on row 0) */
     int32_t lattice;           /* POND_D2Q16 (default) or POND_D2Q25 */
-    int32_t split;             /* POND_SPLIT_TOTAL (default) or POND_SPLIT_INTERNAL */
+    int32_t split;             /* POND_SPLIT_TOTAL (default), POND_SPLIT_INTERNAL or POND_SPLIT_NT
+                                  (non-translational: E = sum g + sum v^2/2 f, g_eq = (U'/rho) f_eq;
+                                  the paper's minimum lattice for it is D2Q25) */
     int32_t precision;         /* POND_FP64: FP64 storage and arithmetic.  POND_MIXED_*:
                                   FP32 arithmetic on deviations from a per-tile reference
                                   equilibrium, FP64 rho/u/T and frame update, non-equilibrium
@@ -77,6 +79,9 @@ typedef struct {
     int32_t halo;              /* 0 = automatic (5); the staged box is the tile plus
                                   2 * halo + 2 nodes per axis; stencils outside it are read
                                   from global memory (slower, same result) */
+    int32_t grad_order;        /* Grad expansion order N of the frame transformation
+                                  (Eq. gradGeneralTransform): 0 = the lattice's, which is the
+                                  only value accepted: 3 on D2Q16, 4 on D2Q25 */
 } pond_config;
 
 typedef struct {
@@ -138,10 +143,12 @@ int pond_get_populations(pond_sim *sim, double *f, double *g, double *ux, double
                          double *T, int on_device);
 
 /* Raw state (checkpoint / resume).  The state is mac = [4][ny][nx] FP64 (rho, u_x, u_y, T) and
- * neq = [19][ny][nx] in the storage type of cfg->precision (8, 4, 2 or 2 bytes): the
- * non-equilibrium Hermite coefficients of total order <= 3 of f (A_10, A_01, A_20, A_11, A_02,
- * A_30, A_21, A_12, A_03) and of g (B_pq - B_pq^eq for (p,q) = 00, 10, 01, 20, 11, 02, 30, 21,
- * 12, 03) in each node's own frame, A_pq = sum_i f_i He_p(c_ia) He_q(c_ib) (Sec. III.A.1).
+ * neq = [P][ny][nx] in the storage type of cfg->precision (8, 4, 2 or 2 bytes): the
+ * non-equilibrium Hermite coefficients of total order <= N (N = 3 on D2Q16, 4 on D2Q25) of f
+ * (all but A_00) and of g (B_pq - B_pq^eq), in each node's own frame,
+ * A_pq = sum_i f_i He_p(c_ia) He_q(c_ib) (Sec. III.A.1), slots ordered by total order and then
+ * by q: (p,q) = 00 | 10 01 | 20 11 02 | 30 21 12 03 | 40 31 22 13 04; P = 19 for N = 3
+ * (9 + 10), 29 for N = 4 (14 + 15).
  * pond_state_bytes gives the two array sizes.  Export copies the current state into the
  * caller's buffers (host or device) and synchronises; import copies it in (statistics and
  * sticky status reset).  A checkpoint resumes bit-identically on the same build. */
@@ -235,8 +242,9 @@ void pond_autotune_clear(void);
  * block live in one file-scope device array of the library, POND_STATIC_SCRATCH_BYTES
  * (16 MiB) on every GPU that loads the library, held until the process exits.
  *  - Size limit: the state must fit that array, state bytes = align256(4*8*N) +
- *    align256(19*s*N) + 256 with N = nx*ny and s = 8/4/2/2 bytes (FP64/FP32/FP16/BF16),
- *    i.e. N <= 91 178 (FP64), 155 341 (FP32), 239 669 (FP16/BF16); larger grids return
+ *    align256(P*s*N) + 256 with N = nx*ny, P = 19 (D2Q16) or 29 (D2Q25) and s = 8/4/2/2
+ *    bytes (FP64/FP32/FP16/BF16), i.e. N <= 91 178 / 63 548 (FP64), 155 341 / 113 357
+ *    (FP32), 239 669 / 186 408 (FP16/BF16) on D2Q16 / D2Q25; larger grids return
  *    POND_ENOMEM without touching the GPU.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) and sets the step kernel's shared-memory limit; make that first

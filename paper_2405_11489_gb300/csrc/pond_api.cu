@@ -51,11 +51,11 @@ Lattice make_lattice(int q1)
         for (int a = 0; a < 5; ++a) { L.c[a] = c[a]; L.w[a] = w[a]; }
         L.cmax = co;
     }
-    const double fact[4] = {1.0, 1.0, 2.0, 6.0};
+    const double fact[5] = {1.0, 1.0, 2.0, 6.0, 24.0};
     for (int a = 0; a < q1; ++a) {
         const double x = L.c[a];
-        const double he[4] = {1.0, x, x * x - 1.0, x * x * x - 3.0 * x};
-        for (int p = 0; p < 4; ++p) {
+        const double he[5] = {1.0, x, x * x - 1.0, x * x * x - 3.0 * x, x * x * x * x - 6.0 * x * x + 3.0};
+        for (int p = 0; p < 5; ++p) {
             L.he[a][p] = he[p];
             L.hn[a][p] = he[p] / fact[p];
             L.hef[a][p] = (float)L.he[a][p];
@@ -71,13 +71,17 @@ struct Layout {
     size_t mac[2], neq[2], status, total;
 };
 
+// Grad order of a configuration: the lattice's (3 on D2Q16, 4 on D2Q25).
+int grad_order(const pond_config& c) { return c.lattice == POND_D2Q25 ? 4 : 3; }
+
 Layout layout_of(const pond_config& c)
 {
     const size_t N = (size_t)c.nx * (size_t)c.ny;
+    const size_t planes = (size_t)nneq(grad_order(c));
     Layout l;
     size_t off = 0;
     for (int k = 0; k < 2; ++k) { l.mac[k] = off; off = align_up(off + NMAC * N * sizeof(double)); }
-    for (int k = 0; k < 2; ++k) { l.neq[k] = off; off = align_up(off + NNEQ * N * storage_bytes(c.precision)); }
+    for (int k = 0; k < 2; ++k) { l.neq[k] = off; off = align_up(off + planes * N * storage_bytes(c.precision)); }
     l.status = off;
     off = align_up(off + sizeof(DevStatus));
     l.total = off;
@@ -90,7 +94,10 @@ int check_config(const pond_config* c)
     if (c->nx < 1 || c->ny < 1) return POND_EINVAL;
     if ((long long)c->nx * (long long)c->ny > (1ll << 31)) return POND_EINVAL;
     if (c->lattice != POND_D2Q16 && c->lattice != POND_D2Q25) return POND_EINVAL;
-    if (c->split != POND_SPLIT_TOTAL && c->split != POND_SPLIT_INTERNAL) return POND_EINVAL;
+    if (c->split != POND_SPLIT_TOTAL && c->split != POND_SPLIT_INTERNAL && c->split != POND_SPLIT_NT)
+        return POND_EINVAL;
+    // the Grad order is the lattice's: 3 on D2Q16, 4 on D2Q25
+    if (c->grad_order != 0 && c->grad_order != (c->lattice == POND_D2Q25 ? 4 : 3)) return POND_EINVAL;
     if (c->precision < POND_FP64 || c->precision > POND_MIXED_BF16) return POND_EINVAL;
     if (c->interp_order != 2 && c->interp_order != 3) return POND_EINVAL;
     if ((c->bc_x != 0 && c->bc_x != 1) || (c->bc_y != 0 && c->bc_y != 1)) return POND_EINVAL;
@@ -140,6 +147,7 @@ AuxParams aux_params(pond_sim* s, int k)
     a.bc_x = s->cfg.bc_x;
     a.bc_y = s->cfg.bc_y;
     a.split = s->cfg.split;
+    a.nord = grad_order(s->cfg);
     a.N = (long long)s->cfg.nx * s->cfg.ny;
     a.cv = 1.0 / (s->cfg.gamma - 1.0);
     a.mac = mac_ptr(s, k);
@@ -205,6 +213,7 @@ void fill_case(const pond_config& c, DevStatus* status, CaseDesc& d)
     d.bc_x = c.bc_x;
     d.bc_y = c.bc_y;
     d.split = c.split;
+    d.nord = grad_order(c);
     d.pc_max_iter = c.pc_max_iter;
     d.pc_fixed = c.pc_fixed_iters;
     d.N = (long long)c.nx * c.ny;
@@ -472,7 +481,7 @@ int pond_state_bytes(const pond_config* cfg, size_t* mac_bytes, size_t* neq_byte
     if (!mac_bytes || !neq_bytes) return POND_EINVAL;
     const size_t N = (size_t)cfg->nx * (size_t)cfg->ny;
     *mac_bytes = NMAC * N * sizeof(double);
-    *neq_bytes = NNEQ * N * storage_bytes(cfg->precision);
+    *neq_bytes = (size_t)nneq(grad_order(*cfg)) * N * storage_bytes(cfg->precision);
     return POND_OK;
 }
 
@@ -1044,6 +1053,7 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     a.bc_x = cfg->bc_x;
     a.bc_y = cfg->bc_y;
     a.split = cfg->split;
+    a.nord = grad_order(*cfg);
     a.N = N;
     a.cv = p.one.cv;
     a.status = st;

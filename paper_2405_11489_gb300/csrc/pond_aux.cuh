@@ -10,10 +10,11 @@ namespace pond {
 struct AuxParams {
     Lattice lat;
     int nx, ny, bc_x, bc_y, split;
+    int nord;           // Grad order N of the state (3 or 4)
     long long N;
     double cv;
     double* mac;        // [4][N] rho, u_x, u_y, T
-    void* neq;          // [19][N] storage type
+    void* neq;          // [nneq(N)][N] storage type
     const double* mac_prev;  // internal source: frames before the step
     DevStatus* status;
 };
@@ -36,10 +37,10 @@ __global__ void init_kernel(AuxParams p, const double* rho, const double* ux, co
     p.mac[2 * p.N + n] = vy;
     p.mac[3 * p.N + n] = t;
     S* q = reinterpret_cast<S*>(p.neq);
-    for (int m = 0; m < NNEQ; ++m) sto_put<S, double>(q + (long long)m * p.N + n, 0.0);
+    for (int m = 0; m < nneq(p.nord); ++m) sto_put<S, double>(q + (long long)m * p.N + n, 0.0);
 }
 
-// Populations f, g [Q][N] in frames (ux, uy, T) -> Hermite coefficients of order <= 3.
+// Populations f, g [Q][N] in frames (ux, uy, T) -> Hermite coefficients of order <= N.
 template <class S>
 __global__ void set_pops_kernel(AuxParams p, const double* f, const double* g, const double* ux,
                                 const double* uy, const double* T)
@@ -47,14 +48,14 @@ __global__ void set_pops_kernel(AuxParams p, const double* f, const double* g, c
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
     const Lattice& L = p.lat;
-    const int q1 = L.q1;
-    double A[NCOEF] = {0}, B[NCOEF] = {0};
+    const int q1 = L.q1, no = p.nord, nc = ncoef(no);
+    double A[NCMAX] = {0}, B[NCMAX] = {0};
     for (int b = 0; b < q1; ++b)
         for (int a = 0; a < q1; ++a) {
             long long i = (long long)(b * q1 + a) * p.N + n;
             double fi = f[i], gi = g[i];
-            for (int pp = 0; pp <= 3; ++pp)
-                for (int qq = 0; qq <= 3 - pp; ++qq) {
+            for (int pp = 0; pp <= no; ++pp)
+                for (int qq = 0; qq <= no - pp; ++qq) {
                     double h = L.he[a][pp] * L.he[b][qq];
                     A[slot(pp, qq)] += fi * h;
                     B[slot(pp, qq)] += gi * h;
@@ -77,8 +78,8 @@ __global__ void set_pops_kernel(AuxParams p, const double* f, const double* g, c
     B[slot(2, 0)] -= e.b20;
     B[slot(0, 2)] -= e.b20;
     S* q = reinterpret_cast<S*>(p.neq);
-    for (int m = 1; m < NCOEF; ++m) sto_put<S, double>(q + (long long)(m - 1) * p.N + n, A[m]);
-    for (int m = 0; m < NCOEF; ++m) sto_put<S, double>(q + (long long)(9 + m) * p.N + n, B[m]);
+    for (int m = 1; m < nc; ++m) sto_put<S, double>(q + (long long)(m - 1) * p.N + n, A[m]);
+    for (int m = 0; m < nc; ++m) sto_put<S, double>(q + (long long)(nc - 1 + m) * p.N + n, B[m]);
 }
 
 // Full own-frame coefficients of node n (FP64).
@@ -87,13 +88,14 @@ __device__ __forceinline__ void node_coefficients(const AuxParams& p, long long 
                                                   double& rho, double& ux, double& uy, double& T)
 {
     const S* q = reinterpret_cast<const S*>(p.neq);
+    const int nc = ncoef(p.nord);
     rho = p.mac[n];
     ux = p.mac[p.N + n];
     uy = p.mac[2 * p.N + n];
     T = p.mac[3 * p.N + n];
     A[0] = rho;
-    for (int m = 1; m < NCOEF; ++m) A[m] = sto_load<S>(q + (long long)(m - 1) * p.N + n);
-    for (int m = 0; m < NCOEF; ++m) B[m] = sto_load<S>(q + (long long)(9 + m) * p.N + n);
+    for (int m = 1; m < nc; ++m) A[m] = sto_load<S>(q + (long long)(m - 1) * p.N + n);
+    for (int m = 0; m < nc; ++m) B[m] = sto_load<S>(q + (long long)(nc - 1 + m) * p.N + n);
     GEq e = g_equilibrium(p.split, p.cv, rho, ux, uy, T, sqrt(T));
     B[slot(0, 0)] += e.b00;
     B[slot(1, 0)] += e.b10;
@@ -103,19 +105,25 @@ __device__ __forceinline__ void node_coefficients(const AuxParams& p, long long 
 }
 
 // Moments of the populations (Sec. II): rho = A_00, rho u = rho u_frame + sqrt(T) (A_10, A_01),
-// total split E = B_00, T = (E/rho - |u|^2/2)/c_v; internal split T = B_00/(rho c_v).
+// total split E = B_00, T = (E/rho - |u|^2/2)/c_v; internal split T = B_00/(rho c_v);
+// non-translational split E = B_00 + sum |C|^2/2 f with
+// sum |C|^2/2 f = (T (A_20 + A_02 + 2 rho) + 2 sqrt(T) u_frame . (A_10, A_01) + |u_frame|^2 rho)/2.
 template <class S>
 __global__ void moments_kernel(AuxParams p, double* out_rho, double* out_ux, double* out_uy,
                                double* out_T)
 {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    double A[NCOEF], B[NCOEF], rho, ux, uy, T;
+    double A[NCMAX], B[NCMAX], rho, ux, uy, T;
     node_coefficients<S>(p, n, A, B, rho, ux, uy, T);
     double sT = sqrt(T);
     double vx = ux + sT * A[slot(1, 0)] / rho;
     double vy = uy + sT * A[slot(0, 1)] / rho;
-    double t = (p.split == 0) ? (B[0] / rho - 0.5 * (vx * vx + vy * vy)) / p.cv : B[0] / (rho * p.cv);
+    double E = B[0];
+    if (p.split == 2)
+        E += 0.5 * (T * (A[slot(2, 0)] + A[slot(0, 2)] + 2.0 * rho) +
+                    2.0 * sT * (ux * A[slot(1, 0)] + uy * A[slot(0, 1)]) + (ux * ux + uy * uy) * rho);
+    double t = (p.split == 1) ? B[0] / (rho * p.cv) : (E / rho - 0.5 * (vx * vx + vy * vy)) / p.cv;
     if (out_rho) out_rho[n] = rho;
     if (out_ux) out_ux[n] = vx;
     if (out_uy) out_uy[n] = vy;
@@ -129,14 +137,14 @@ __global__ void get_pops_kernel(AuxParams p, double* f, double* g, double* oux, 
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
     const Lattice& L = p.lat;
-    double A[NCOEF], B[NCOEF], rho, ux, uy, T;
+    double A[NCMAX], B[NCMAX], rho, ux, uy, T;
     node_coefficients<S>(p, n, A, B, rho, ux, uy, T);
-    const int q1 = L.q1;
+    const int q1 = L.q1, no = p.nord;
     for (int b = 0; b < q1; ++b)
         for (int a = 0; a < q1; ++a) {
             double sf = 0.0, sg = 0.0;
-            for (int pp = 0; pp <= 3; ++pp)
-                for (int qq = 0; qq <= 3 - pp; ++qq) {
+            for (int pp = 0; pp <= no; ++pp)
+                for (int qq = 0; qq <= no - pp; ++qq) {
                     double h = L.hn[a][pp] * L.hn[b][qq];
                     sf += A[slot(pp, qq)] * h;
                     sg += B[slot(pp, qq)] * h;
@@ -160,7 +168,7 @@ __global__ void get_pops_kernel(AuxParams p, double* f, double* g, double* oux, 
 // (Du = d_t u + u . grad u), and it is added to the non-equilibrium part of g.
 template <class S>
 __device__ __forceinline__ void internal_source_node(long long n, int nx, int ny, int bc_x, int bc_y,
-                                                     long long N, const double* mac,
+                                                     long long N, int nord, const double* mac,
                                                      const double* mac_prev, void* neq)
 {
     const int x = (int)(n % nx), y = (int)(n / nx);
@@ -181,7 +189,7 @@ __device__ __forceinline__ void internal_source_node(long long n, int nx, int ny
     double G[6] = {-rT * (dxux + dyuy), -rsT * Dux, -rsT * Duy, -2.0 * rT * dxux,
                    -rT * (dyux + dxuy), -2.0 * rT * dyuy};
     for (int m = 0; m < 6; ++m) {
-        S* a = q + (long long)(9 + m) * N + n;
+        S* a = q + (long long)(ncoef(nord) - 1 + m) * N + n;
         sto_put<S, double>(a, sto_load<S>(a) + G[m]);
     }
 }
@@ -191,7 +199,7 @@ __global__ void internal_source_kernel(AuxParams p)
 {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    internal_source_node<S>(n, p.nx, p.ny, p.bc_x, p.bc_y, p.N, p.mac, p.mac_prev, p.neq);
+    internal_source_node<S>(n, p.nx, p.ny, p.bc_x, p.bc_y, p.N, p.nord, p.mac, p.mac_prev, p.neq);
 }
 
 // Batched form: block b works on nodes [256 (b - block_start[c]), ...) of case c (the last case
@@ -211,7 +219,7 @@ __global__ void internal_source_batch_kernel(const CaseDesc* cases, const int* b
     const long long n = (long long)(b - block_start[lo]) * blockDim.x + threadIdx.x;
     if (n >= c.N) return;
     const int in = c.cur ^ flip;          // the state before the step; the new one is in ^ 1
-    internal_source_node<S>(n, c.nx, c.ny, c.bc_x, c.bc_y, c.N, c.mac[in ^ 1], c.mac[in], c.neq[in ^ 1]);
+    internal_source_node<S>(n, c.nx, c.ny, c.bc_x, c.bc_y, c.N, c.nord, c.mac[in ^ 1], c.mac[in], c.neq[in ^ 1]);
 }
 
 }  // namespace pond

@@ -3,13 +3,14 @@
 // storage conversions.  Everything here is written for sm_103a (GB300).
 //
 // State representation.  After the collision every node's populations lie in the span of
-// the reduced Grad basis (Eq. gradGeneralTransform, N = 3): the frame transformation
-// projects onto it and both BGK equilibria lie in it.  So the 2Q populations of a node are
-// kept, without loss, as (rho, u_x, u_y, T) in FP64 plus the non-equilibrium parts of the
-// ten Hermite coefficients of f and of g of total order <= 3 in the node's own frame:
+// the reduced Grad basis of order N (Eq. gradGeneralTransform; N = 3 on D2Q16, 4 on D2Q25):
+// the frame transformation projects onto it and both BGK equilibria lie in it.  So the 2Q
+// populations of a node are kept, without loss, as (rho, u_x, u_y, T) in FP64 plus the
+// non-equilibrium parts of the (N+1)(N+2)/2 Hermite coefficients of f and of g of total
+// order <= N in the node's own frame:
 //     A_pq = sum_i f_i He_p(c_ia) He_q(c_ib),   B_pq = sum_i g_i He_p(c_ia) He_q(c_ib),
 // f stores A_pq for (p,q) != (0,0) (A_00 = rho), g stores B_pq - B_pq^eq(rho, u, T).
-// The populations are f_i = w_i sum_{p+q<=3} A_pq He_p(c_ia) He_q(c_ib) / (p! q!).
+// The populations are f_i = w_i sum_{p+q<=N} A_pq He_p(c_ia) He_q(c_ib) / (p! q!).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -21,14 +22,21 @@
 
 namespace pond {
 
-constexpr int NCOEF = 10;   // Hermite coefficients with p + q <= 3 in 2-D
-constexpr int NNEQ = 19;    // stored per node: 9 for f (all but (0,0)), 10 for g
+// Hermite coefficients with p + q <= N in 2-D, and the planes stored per node (f without
+// (0,0), g complete).
+__host__ __device__ constexpr int ncoef(int N) { return (N + 1) * (N + 2) / 2; }
+__host__ __device__ constexpr int nneq(int N) { return 2 * ncoef(N) - 1; }
+constexpr int NCMAX = 15;   // N <= 4
 constexpr int NMAC = 4;     // rho, u_x, u_y, T (FP64)
 
-// Coefficient slots: (p,q) = 00 10 01 20 11 02 30 21 12 03.
+// The Grad order of a lattice: the total Hermite order its nodes carry (3 for D1Q4-based
+// D2Q16, 4 for D1Q5-based D2Q25).
+__host__ __device__ constexpr int grad_order_of_q1(int q1) { return q1 == 5 ? 4 : 3; }
+
+// Coefficient slots by total order: (p,q) = 00 | 10 01 | 20 11 02 | 30 21 12 03 | 40 31 22 13 04.
 __host__ __device__ constexpr int slot(int p, int q)
 {
-    return (p + q == 0) ? 0 : (p + q == 1) ? 1 + q : (p + q == 2) ? 3 + q : 6 + q;
+    return (p + q) * (p + q + 1) / 2 + q;
 }
 
 // Tables of the 1-D Gauss-Hermite rules of Table I (q1 = 4 or 5), in both precisions.
@@ -36,10 +44,10 @@ __host__ __device__ constexpr int slot(int p, int q)
 struct Lattice {
     int q1;
     double c[5], w[5];
-    double he[5][4];     // He_p(c_a), p = 0..3 (probabilists' Hermite polynomials)
-    double hn[5][4];     // He_p(c_a) / p!
+    double he[5][5];     // He_p(c_a), p = 0..4 (probabilists' Hermite polynomials)
+    double hn[5][5];     // He_p(c_a) / p!
     float cf[5], wf[5];
-    float hef[5][4], hnf[5][4];
+    float hef[5][5], hnf[5][5];
     double cmax;         // largest |c_a|
 };
 
@@ -68,74 +76,87 @@ __device__ __forceinline__ R lat_hn(const Lattice& L, int a, int p)
 // Re-centring of Hermite coefficients between frames.  For populations whose velocities
 // are xi_old = (C - u_old)/sqrt(T_old), the new variable is xi_new = s xi_old + d with
 // s = sqrt(T_old / T_new), d = (u_old - u_new)/sqrt(T_new).  He_n(s xi + d) expands in
-// He_k(xi) with the lower-triangular matrix below (e = s^2 - 1 + d^2); in 2-D the map is
-// the tensor product of one such matrix per axis.  Because it needs only coefficients of
-// order <= n, it reproduces the frame transformation of Eq. (gradGeneralTransform) with
-// N = 3 exactly.
+// He_k(xi) with the lower-triangular matrix
+//   t_nk = (n!/k!) s^k sum_j d^(n-k-2j) (sigma/2)^j / (j! (n-k-2j)!),   sigma = s^2 - 1,
+// written out below for n <= 4 in terms of sigma (formed accurately by the caller) so that
+// no s^2 - 1 cancels in FP32.  In 2-D the map is the tensor product of one matrix per axis.
+// Because it needs only coefficients of order <= n, it reproduces the frame transformation
+// of Eq. (gradGeneralTransform) with order N exactly.
 // ---------------------------------------------------------------------------------------
-template <class R>
+template <class R, int N>
 struct Tau {
-    R t10, t11, t20, t21, t22, t30, t31, t32, t33;   // t00 = 1
+    R t[N + 1][N + 1];   // t[n][k] for k <= n; t[0][0] = 1
+    R u1[N + 1];         // t[n][1] / s (n >= 1)
+    R u2[N + 1];         // t[n][2] / s^2 (n >= 2)
 };
 
-template <class R>
-__device__ __forceinline__ Tau<R> make_tau(R s, R d)
+// Re-centring matrix from s, d and an accurately formed sigma = s^2 - 1.
+template <class R, int N>
+__device__ __forceinline__ Tau<R, N> make_tau_sig(R s, R d, R sig)
 {
-    Tau<R> t;
-    R s2 = s * s;
-    R e = s2 - R(1) + d * d;
-    t.t10 = d;
-    t.t11 = s;
-    t.t20 = e;
-    t.t21 = R(2) * s * d;
-    t.t22 = s2;
-    t.t30 = d * (R(3) * e - R(2) * d * d);
-    t.t31 = R(3) * s * e;
-    t.t32 = R(3) * s2 * d;
-    t.t33 = s2 * s;
+    Tau<R, N> t;
+    const R e = sig + d * d;
+    t.t[0][0] = R(1);
+    t.t[1][0] = d;
+    t.t[1][1] = s;
+    t.t[2][0] = e;
+    t.t[2][1] = R(2) * s * d;
+    t.t[2][2] = R(1) + sig;
+    t.t[3][0] = d * (R(3) * e - R(2) * d * d);
+    t.t[3][1] = R(3) * s * e;
+    t.t[3][2] = R(3) * (R(1) + sig) * d;
+    t.t[3][3] = (R(1) + sig) * s;
+    t.u1[1] = R(1);
+    t.u1[2] = R(2) * d;
+    t.u1[3] = R(3) * e;
+    t.u2[2] = R(1);
+    t.u2[3] = R(3) * d;
+    if constexpr (N >= 4) {
+        const R d2 = d * d;
+        t.t[4][0] = d2 * d2 + R(6) * d2 * sig + R(3) * sig * sig;
+        t.u1[4] = R(4) * d * (d2 + R(3) * sig);
+        t.t[4][1] = s * t.u1[4];
+        t.u2[4] = R(6) * e;
+        t.t[4][2] = (R(1) + sig) * t.u2[4];
+        t.t[4][3] = R(4) * (R(1) + sig) * s * d;
+        t.t[4][4] = (R(1) + sig) * (R(1) + sig);
+    }
     return t;
 }
 
-// B_pq = sum_{k<=p, l<=q} tx_pk ty_ql A_kl for p + q <= 3 (A may alias B).
-template <class R>
-__device__ __forceinline__ void retarget(const Tau<R>& x, const Tau<R>& y, const R* A, R* B)
+// B_pq = sum_{k<=p, l<=q} tx_pk ty_ql A_kl for p + q <= N (A may alias B).
+template <class R, int N>
+__device__ __forceinline__ void retarget(const Tau<R, N>& x, const Tau<R, N>& y, const R* A, R* B)
 {
+    constexpr int NC = ncoef(N);
+    R X[NC];
     // x pass: X_{p,l} = sum_{k<=p} tx_pk A_{k,l}
-    R a00 = A[slot(0, 0)], a10 = A[slot(1, 0)], a20 = A[slot(2, 0)], a30 = A[slot(3, 0)];
-    R a01 = A[slot(0, 1)], a11 = A[slot(1, 1)], a21 = A[slot(2, 1)];
-    R a02 = A[slot(0, 2)], a12 = A[slot(1, 2)];
-    R a03 = A[slot(0, 3)];
-    R x00 = a00;
-    R x10 = x.t10 * a00 + x.t11 * a10;
-    R x20 = x.t20 * a00 + x.t21 * a10 + x.t22 * a20;
-    R x30 = x.t30 * a00 + x.t31 * a10 + x.t32 * a20 + x.t33 * a30;
-    R x01 = a01;
-    R x11 = x.t10 * a01 + x.t11 * a11;
-    R x21 = x.t20 * a01 + x.t21 * a11 + x.t22 * a21;
-    R x02 = a02;
-    R x12 = x.t10 * a02 + x.t11 * a12;
-    R x03 = a03;
+#pragma unroll
+    for (int l = 0; l <= N; ++l)
+#pragma unroll
+        for (int p = 0; p <= N - l; ++p) {
+            R v = (p == 0) ? A[slot(0, l)] : x.t[p][0] * A[slot(0, l)];
+#pragma unroll
+            for (int k = 1; k <= p; ++k) v += x.t[p][k] * A[slot(k, l)];
+            X[slot(p, l)] = v;
+        }
     // y pass: B_{p,q} = sum_{l<=q} ty_ql X_{p,l}
-    B[slot(0, 0)] = x00;
-    B[slot(1, 0)] = x10;
-    B[slot(2, 0)] = x20;
-    B[slot(3, 0)] = x30;
-    B[slot(0, 1)] = y.t10 * x00 + y.t11 * x01;
-    B[slot(1, 1)] = y.t10 * x10 + y.t11 * x11;
-    B[slot(2, 1)] = y.t10 * x20 + y.t11 * x21;
-    B[slot(0, 2)] = y.t20 * x00 + y.t21 * x01 + y.t22 * x02;
-    B[slot(1, 2)] = y.t20 * x10 + y.t21 * x11 + y.t22 * x12;
-    B[slot(0, 3)] = y.t30 * x00 + y.t31 * x01 + y.t32 * x02 + y.t33 * x03;
+#pragma unroll
+    for (int p = 0; p <= N; ++p)
+#pragma unroll
+        for (int q = 0; q <= N - p; ++q) {
+            R v = (q == 0) ? X[slot(p, 0)] : y.t[q][0] * X[slot(p, 0)];
+#pragma unroll
+            for (int l = 1; l <= q; ++l) v += y.t[q][l] * X[slot(p, l)];
+            B[slot(p, q)] = v;
+        }
 }
 
-// Entry (n, k) of a Tau matrix (k <= n <= 3).
-template <class R>
-__device__ __forceinline__ R tau_at(const Tau<R>& t, int n, int k)
+// Entry (n, k) of a re-centring matrix (k <= n <= N).
+template <class R, int N>
+__device__ __forceinline__ R tau_at(const Tau<R, N>& t, int n, int k)
 {
-    if (n == 0) return R(1);
-    if (n == 1) return k == 0 ? t.t10 : t.t11;
-    if (n == 2) return k == 0 ? t.t20 : (k == 1 ? t.t21 : t.t22);
-    return k == 0 ? t.t30 : (k == 1 ? t.t31 : (k == 2 ? t.t32 : t.t33));
+    return n == 0 ? R(1) : t.t[n][k];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -212,7 +233,8 @@ __device__ __forceinline__ void sto_put(S* p, R v)
 // Equilibrium Hermite coefficients of g in its own frame (Sec. II g_eq, Sec. III.A lattice):
 // total split    B_00 = rho (c_v T + |u|^2/2), B_10 = rho sqrt(T) u_x, B_01 = rho sqrt(T) u_y,
 //                B_20 = B_02 = rho T, others 0;
-// internal split B_00 = rho c_v T, B_20 = B_02 = rho T, others 0.
+// internal split B_00 = rho c_v T, B_20 = B_02 = rho T, others 0;
+// non-translational split B_00 = U' = rho (c_v - 1) T, others 0.
 struct GEq {
     double b00, b10, b01, b20;   // b02 = b20
 };
@@ -224,12 +246,16 @@ __device__ __forceinline__ GEq g_equilibrium(int split, double cv, double rho, d
         e.b00 = rho * (cv * T + 0.5 * (ux * ux + uy * uy));
         e.b10 = rho * sqrtT * ux;
         e.b01 = rho * sqrtT * uy;
-    } else {
+    } else if (split == 1) {
         e.b00 = rho * cv * T;
         e.b10 = 0.0;
         e.b01 = 0.0;
+    } else {
+        e.b00 = rho * (cv - 1.0) * T;
+        e.b10 = 0.0;
+        e.b01 = 0.0;
     }
-    e.b20 = rho * T;
+    e.b20 = split == 2 ? 0.0 : rho * T;
     return e;
 }
 

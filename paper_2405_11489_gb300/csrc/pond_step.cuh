@@ -44,6 +44,7 @@ namespace pond {
 // a batched launch carries a device table of cases and the first tile of each.
 struct CaseDesc {
     int nx, ny, bc_x, bc_y, split, pc_max_iter, pc_fixed;
+    int nord;                   // Grad order N of the state (3 or 4; the lattice's)
     int tiles_x;                // tiles along x (tile index -> tile coordinates)
     long long N;                // nx * ny
     double cv, inv_cv, mu, pc_tol;
@@ -111,9 +112,9 @@ template <class R>
 struct RefState {
     double rho, ux, uy, T;
     R rhoR, uxR, uyR, TR;
-    R ER;       // E_r (total split) or U_r (internal split) = B_00^eq of the reference node
+    R ER;       // B_00^eq of the reference node: E_r (total), U_r (internal), U'_r (non-translational)
     R PR;       // p_r = rho_r T_r
-    R eR;       // E_r / rho_r (total) or c_v T_r (internal)
+    R eR;       // energy per mass whose balance gives T: E_r / rho_r (total, non-translational), c_v T_r (internal)
     R isT;      // 1 / sqrt(T_r)
     R invT;     // 1 / T_r
     R cvR;
@@ -125,107 +126,118 @@ struct BaseFrame {
     R P, isT, invT;
 };
 
-// 1-D re-centring matrix with an accurately formed sigma = s^2 - 1 (see make_tau).
-template <class R>
-__device__ __forceinline__ Tau<R> make_tau_sig(R s, R d, R sig)
-{
-    Tau<R> t;
-    R e = sig + d * d;
-    t.t10 = d;
-    t.t11 = s;
-    t.t20 = e;
-    t.t21 = R(2) * s * d;
-    t.t22 = R(1) + sig;
-    t.t30 = d * (R(3) * e - R(2) * d * d);
-    t.t31 = R(3) * s * e;
-    t.t32 = R(3) * (R(1) + sig) * d;
-    t.t33 = (R(1) + sig) * s;
-    return t;
-}
-
 template <class R>
 __device__ __forceinline__ R sqrt_r(R v)
 {
     if constexpr (std::is_same<R, double>::value) return sqrt(v); else return sqrtf(v);
 }
 
+// x and y factors of a moved equilibrium for order p: X0 = t_p0, X1 = t_p1/s, X2 = t_p2/s^2.
+template <class R, int N>
+__device__ __forceinline__ R tx0(const Tau<R, N>& t, int p) { return p == 0 ? R(1) : t.t[p][0]; }
+template <class R, int N>
+__device__ __forceinline__ R tx1(const Tau<R, N>& t, int p) { return p >= 1 ? t.u1[p] : R(0); }
+template <class R, int N>
+__device__ __forceinline__ R tx2(const Tau<R, N>& t, int p) { return p >= 2 ? t.u2[p] : R(0); }
+
 // g equilibrium of a node (Sec. II g_eq in its own frame), moved into a base frame by tx, ty,
 // minus the equilibrium of the base frame itself, for the slots (p,q) != (0,0) plus dE at
-// (0,0).  Added into G.  Node values: E or U (ES), p (PS), u (uxS, uyS), T (TS); differences
-// node - base: dP, dux, duy, dT; moving shifts dx, dy = (u - u_base)/sqrt(T_base) and
-// sig = T/T_base - 1.  Every term is a product of small differences with O(1) values.
-template <class R>
-__device__ __forceinline__ void add_g_eq_dev(int split, const BaseFrame<R>& bf, const Tau<R>& tx,
-                                             const Tau<R>& ty, R dx, R dy, R sig, R ES, R dE, R PS,
+// (0,0).  Added into G.  Node values: B_00^eq (ES: E, U or U'), p (PS), u (uxS, uyS), T (TS);
+// differences node - base: dP, dux, duy, dT; moving shifts dx, dy = (u - u_base)/sqrt(T_base)
+// and sig = T/T_base - 1.  Every term is a product of small differences with O(1) values.
+// Orders 0-2 carry the base equilibrium and are written out; orders >= 3 have none and follow
+//   B_pq = ES X0_p Y0_q + s b10 X1_p Y0_q + s b01 X0_p Y1_q + s^2 p (X2_p Y0_q + X0_p Y2_q).
+template <class R, int N>
+__device__ __forceinline__ void add_g_eq_dev(int split, const BaseFrame<R>& bf, const Tau<R, N>& tx,
+                                             const Tau<R, N>& ty, R dx, R dy, R sig, R ES, R dE, R PS,
                                              R uxS, R uyS, R dP, R dux, R duy, R TS, R dT, R* G)
 {
+    if (split == 2) {
+        // non-translational: only B_00 = U' in the node's frame, moved like f's equilibrium
+        G[slot(0, 0)] += dE;
+#pragma unroll
+        for (int pp = 0; pp <= N; ++pp)
+#pragma unroll
+            for (int q = 0; q <= N - pp; ++q)
+                if (pp + q > 0) G[slot(pp, q)] += ES * tx0(tx, pp) * tx0(ty, q);
+        return;
+    }
     const R dPT = dP * TS + bf.P * dT;                    // p T - p_b T_b
     const R PsR = PS * (R(1) + sig);                      // s^2 p
+    R PuxR = R(0), PuyR = R(0);                           // s b10, s b01 (total split)
     if (split == 0) {
-        const R PuxR = PS * uxS * bf.isT, PuyR = PS * uyS * bf.isT;   // s b10, s b01
+        PuxR = PS * uxS * bf.isT;
+        PuyR = PS * uyS * bf.isT;
         const R dPux = dP * uxS + bf.P * dux;             // p u - p_b u_b
         const R dPuy = dP * uyS + bf.P * duy;
         G[slot(0, 0)] += dE;
         G[slot(1, 0)] += dx * ES + dPux * bf.isT;
         G[slot(0, 1)] += dy * ES + dPuy * bf.isT;
-        G[slot(2, 0)] += tx.t20 * ES + R(2) * dx * PuxR + dPT * bf.invT;
-        G[slot(0, 2)] += ty.t20 * ES + R(2) * dy * PuyR + dPT * bf.invT;
+        G[slot(2, 0)] += tx.t[2][0] * ES + R(2) * dx * PuxR + dPT * bf.invT;
+        G[slot(0, 2)] += ty.t[2][0] * ES + R(2) * dy * PuyR + dPT * bf.invT;
         G[slot(1, 1)] += dx * dy * ES + dx * PuyR + dy * PuxR;
-        G[slot(3, 0)] += tx.t30 * ES + R(3) * tx.t20 * PuxR + R(3) * dx * PsR;
-        G[slot(0, 3)] += ty.t30 * ES + R(3) * ty.t20 * PuyR + R(3) * dy * PsR;
-        G[slot(2, 1)] += tx.t20 * dy * ES + tx.t20 * PuyR + R(2) * dx * dy * PuxR + dy * PsR;
-        G[slot(1, 2)] += ty.t20 * dx * ES + ty.t20 * PuxR + R(2) * dx * dy * PuyR + dx * PsR;
+        G[slot(3, 0)] += tx.t[3][0] * ES + R(3) * tx.t[2][0] * PuxR + R(3) * dx * PsR;
+        G[slot(0, 3)] += ty.t[3][0] * ES + R(3) * ty.t[2][0] * PuyR + R(3) * dy * PsR;
+        G[slot(2, 1)] += tx.t[2][0] * dy * ES + tx.t[2][0] * PuyR + R(2) * dx * dy * PuxR + dy * PsR;
+        G[slot(1, 2)] += ty.t[2][0] * dx * ES + ty.t[2][0] * PuxR + R(2) * dx * dy * PuyR + dx * PsR;
     } else {
         G[slot(0, 0)] += dE;
         G[slot(1, 0)] += dx * ES;
         G[slot(0, 1)] += dy * ES;
-        G[slot(2, 0)] += tx.t20 * ES + dPT * bf.invT;
-        G[slot(0, 2)] += ty.t20 * ES + dPT * bf.invT;
+        G[slot(2, 0)] += tx.t[2][0] * ES + dPT * bf.invT;
+        G[slot(0, 2)] += ty.t[2][0] * ES + dPT * bf.invT;
         G[slot(1, 1)] += dx * dy * ES;
-        G[slot(3, 0)] += tx.t30 * ES + R(3) * dx * PsR;
-        G[slot(0, 3)] += ty.t30 * ES + R(3) * dy * PsR;
-        G[slot(2, 1)] += tx.t20 * dy * ES + dy * PsR;
-        G[slot(1, 2)] += ty.t20 * dx * ES + dx * PsR;
+        G[slot(3, 0)] += tx.t[3][0] * ES + R(3) * dx * PsR;
+        G[slot(0, 3)] += ty.t[3][0] * ES + R(3) * dy * PsR;
+        G[slot(2, 1)] += tx.t[2][0] * dy * ES + dy * PsR;
+        G[slot(1, 2)] += ty.t[2][0] * dx * ES + dx * PsR;
     }
+#pragma unroll
+    for (int pp = 0; pp <= N; ++pp)
+#pragma unroll
+        for (int q = 0; q <= N - pp; ++q)
+            if (pp + q >= 4)
+                G[slot(pp, q)] += ES * tx0(tx, pp) * tx0(ty, q) + PuxR * tx1(tx, pp) * tx0(ty, q) +
+                                  PuyR * tx0(tx, pp) * tx1(ty, q) +
+                                  PsR * (tx2(tx, pp) * tx0(ty, q) + tx0(tx, pp) * tx2(ty, q));
 }
 
 // Deviation of node nd's coefficients, moved into the reference frame, from the reference
-// node's equilibrium coefficients (f into Df, g into Dg).
-template <class S, class R>
+// node's equilibrium coefficients (f into Df, g into Dg; ncoef(N) values each).
+template <class S, class R, int N>
 __device__ __forceinline__ void source_dev(const CaseRun& p, const RefState<R>& rf, long long nd,
                                            R* Df, R* Dg)
 {
-    const long long N = p.N;
+    constexpr int NC = ncoef(N);
+    const long long Nn = p.N;
     const S* neq = reinterpret_cast<const S*>(p.neq_in);
     // the only FP64 operations: differences of the primitive variables from the reference
     const R drho = R(p.mac_in[nd] - rf.rho);
-    const R dux = R(p.mac_in[N + nd] - rf.ux);
-    const R duy = R(p.mac_in[2 * N + nd] - rf.uy);
-    const R dT = R(p.mac_in[3 * N + nd] - rf.T);
+    const R dux = R(p.mac_in[Nn + nd] - rf.ux);
+    const R duy = R(p.mac_in[2 * Nn + nd] - rf.uy);
+    const R dT = R(p.mac_in[3 * Nn + nd] - rf.T);
     const R rhoS = rf.rhoR + drho, uxS = rf.uxR + dux, uyS = rf.uyR + duy, TS = rf.TR + dT;
     const R dx = dux * rf.isT, dy = duy * rf.isT;
     const R sig = dT * rf.invT;                       // T/T_r - 1
     const R s = sqrt_r<R>(R(1) + sig);                // sqrt(T/T_r)
-    const Tau<R> tx = make_tau_sig<R>(s, dx, sig);
-    const Tau<R> ty = make_tau_sig<R>(s, dy, sig);
+    const Tau<R, N> tx = make_tau_sig<R, N>(s, dx, sig);
+    const Tau<R, N> ty = make_tau_sig<R, N>(s, dy, sig);
     // non-equilibrium parts, moved
-    R A[NCOEF], B[NCOEF];
+    R A[NC], B[NC];
     A[0] = R(0);
 #pragma unroll
-    for (int k = 1; k < NCOEF; ++k) A[k] = sto_get<S, R>(neq + (long long)(k - 1) * N + nd);
+    for (int k = 1; k < NC; ++k) A[k] = sto_get<S, R>(neq + (long long)(k - 1) * Nn + nd);
 #pragma unroll
-    for (int k = 0; k < NCOEF; ++k) B[k] = sto_get<S, R>(neq + (long long)(9 + k) * N + nd);
-    retarget(tx, ty, A, Df);
-    retarget(tx, ty, B, Dg);
+    for (int k = 0; k < NC; ++k) B[k] = sto_get<S, R>(neq + (long long)(NC - 1 + k) * Nn + nd);
+    retarget<R, N>(tx, ty, A, Df);
+    retarget<R, N>(tx, ty, B, Dg);
     // f equilibrium rho tx_p0 ty_q0 minus K_f = rho_r at (0,0)
-    const R hx[4] = {R(1), tx.t10, tx.t20, tx.t30};
-    const R hy[4] = {R(1), ty.t10, ty.t20, ty.t30};
     Df[0] += drho;
 #pragma unroll
-    for (int pp = 0; pp <= 3; ++pp)
+    for (int pp = 0; pp <= N; ++pp)
 #pragma unroll
-        for (int q = 0; q <= 3 - pp; ++q)
-            if (pp + q > 0) Df[slot(pp, q)] += rhoS * hx[pp] * hy[q];
+        for (int q = 0; q <= N - pp; ++q)
+            if (pp + q > 0) Df[slot(pp, q)] += rhoS * tx0(tx, pp) * tx0(ty, q);
     // g equilibrium moved, minus K_g
     const R dP = drho * TS + rf.rhoR * dT;           // p - p_r
     const R PS = rf.PR + dP;
@@ -236,84 +248,138 @@ __device__ __forceinline__ void source_dev(const CaseRun& p, const RefState<R>& 
         // E - E_r = (rho - rho_r) e + rho_r (c_v (T - T_r) + (u - u_r).(u + u_r)/2)
         dE = drho * eS + rf.rhoR * (rf.cvR * dT + R(0.5) * (dux * (R(2) * rf.uxR + dux) +
                                                               duy * (R(2) * rf.uyR + duy)));
-    } else {
+    } else if (p.split == 1) {
         ES = rf.cvR * PS;
         dE = rf.cvR * dP;
+    } else {
+        ES = (rf.cvR - R(1)) * PS;                    // U' = rho (c_v - 1) T
+        dE = (rf.cvR - R(1)) * dP;
     }
     const BaseFrame<R> bf = {rf.PR, rf.isT, rf.invT};
-    add_g_eq_dev<R>(p.split, bf, tx, ty, dx, dy, sig, ES, dE, PS, uxS, uyS, dP, dux, duy, TS, dT, Dg);
+    add_g_eq_dev<R, N>(p.split, bf, tx, ty, dx, dy, sig, ES, dE, PS, uxS, uyS, dP, dux, duy, TS, dT, Dg);
 }
 
 // Per-population lattice values, kept in shared memory so that the population loops can run
 // without unrolling (the unrolled body would not fit the instruction cache).
 template <class R>
 struct LatRow {
-    R c, w, he[4], hn[4];
+    R c, w, he[5], hn[5];
 };
 
-// Folded x factors of population column a for the FP32 2-D path.  A population (a, b) of the
-// target frame is w_a w_b sum_q hn_b(q) sum_l ty_ql sum_{p <= 3-q} hn_a(p) sum_{k <= p} tx_pk R_kl
+// Folded x factors of population column a.  A population (a, b) of the target frame is
+//   w_a w_b sum_q hn_b(q) sum_l ty_ql sum_{p <= N-q} hn_a(p) sum_{k <= p} tx_pk R_kl
 // (the move lambda_r -> lambda_bar and the Grad reconstruction, R = interpolated coefficients
 // in lambda_r).  Everything but hn_b(q) and the y interpolation is independent of b, so each
-// x-interpolated row X (10 values) is contracted at once into four values
-//   Z_q = sum_{l <= q, k <= 3-q} phi_q(k, l) X_kl,  phi_q(k, l) = ty_ql w_a sum_{p=k}^{3-q} hn_a(p) tx_pk,
-// and only the Z_q are interpolated along y.  phi holds the 20 factors in the order z_contract
-// reads them: q = 0..3, then l = 0..q, then k = 0..3-q.
-template <class R>
-__device__ __forceinline__ void make_phi(const LatRow<R>& la, const Tau<R>& tx, const Tau<R>& ty, R* phi)
+// x-interpolated row X (ncoef(N) values) is contracted at once into N + 1 values
+//   Z_q = sum_{l <= q, k <= N-q} phi_q(k, l) X_kl,  phi_q(k, l) = ty_ql w_a sum_{p=k}^{N-q} hn_a(p) tx_pk,
+// and only the Z_q are interpolated along y.  phi holds the factors in the order z_contract
+// reads them: q = 0..N, then l = 0..q, then k = 0..N-q (20 for N = 3, 35 for N = 4).
+__host__ __device__ constexpr int nphi(int N)
+{
+    int n = 0;
+    for (int q = 0; q <= N; ++q) n += (q + 1) * (N - q + 1);
+    return n;
+}
+
+template <class R, int N>
+__device__ __forceinline__ void make_phi(const LatRow<R>& la, const Tau<R, N>& tx, const Tau<R, N>& ty, R* phi)
 {
     int n = 0;
 #pragma unroll
-    for (int q = 0; q <= 3; ++q) {
-        R S[4];
+    for (int q = 0; q <= N; ++q) {
+        R S[N + 1];
 #pragma unroll
-        for (int k = 0; k <= 3 - q; ++k) {
+        for (int k = 0; k <= N - q; ++k) {
             R v = R(0);
 #pragma unroll
-            for (int p = k; p <= 3 - q; ++p) v += la.hn[p] * tau_at(tx, p, k);
+            for (int p = k; p <= N - q; ++p) v += la.hn[p] * tau_at(tx, p, k);
             S[k] = la.w * v;
         }
 #pragma unroll
         for (int l = 0; l <= q; ++l)
 #pragma unroll
-            for (int k = 0; k <= 3 - q; ++k) phi[n++] = tau_at(ty, q, l) * S[k];
+            for (int k = 0; k <= N - q; ++k) phi[n++] = tau_at(ty, q, l) * S[k];
     }
 }
 
-template <class R>
+template <class R, int N>
 __device__ __forceinline__ void z_contract(const R* phi, const R* X, R* Z)
 {
     int n = 0;
 #pragma unroll
-    for (int q = 0; q <= 3; ++q) {
+    for (int q = 0; q <= N; ++q) {
         R z = R(0);
 #pragma unroll
         for (int l = 0; l <= q; ++l)
 #pragma unroll
-            for (int k = 0; k <= 3 - q; ++k) z += phi[n++] * X[slot(k, l)];
+            for (int k = 0; k <= N - q; ++k) z += phi[n++] * X[slot(k, l)];
         Z[q] = z;
     }
 }
 
-// Node-interleaved shared-memory records: 20 values per node, f in 0..9 and g in 10..19.
-template <class R>
-__device__ __forceinline__ void store20(R* dst, const R* v)
+// Node-interleaved shared-memory records.  N = 3: 20 values per node, f in 0..9 and g in
+// 10..19.  N = 4, FP32: f in 0..14 and g in 16..30 (each distribution 16-byte aligned) in
+// records of 36 floats; FP64: f in 0..14 and g in 15..29, records of 30 doubles (the box must
+// fit shared memory).  Both strides (36 and 60 words) put the eight lanes of a 16-byte load
+// phase on distinct banks.
+template <class R, int N>
+__host__ __device__ constexpr int rec_len() { return N == 3 ? 20 : (sizeof(R) == 4 ? 36 : 30); }
+template <class R, int N>
+__host__ __device__ constexpr int rec_goff() { return N == 3 ? 10 : (sizeof(R) == 4 ? 16 : 15); }
+
+template <class R, int N>
+__device__ __forceinline__ void store_rec(R* dst, const R* Df, const R* Dg)
 {
-    if constexpr (std::is_same<R, float>::value) {
+    constexpr int NC = ncoef(N);
+    if constexpr (N == 3) {
+        R v[20];
 #pragma unroll
-        for (int k = 0; k < 5; ++k)
-            reinterpret_cast<float4*>(dst)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        for (int m = 0; m < NC; ++m) { v[m] = Df[m]; v[NC + m] = Dg[m]; }
+        if constexpr (std::is_same<R, float>::value) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                reinterpret_cast<float4*>(dst)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 10; ++k) reinterpret_cast<double2*>(dst)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+        }
     } else {
 #pragma unroll
-        for (int k = 0; k < 10; ++k) reinterpret_cast<double2*>(dst)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+        for (int m = 0; m < NC; ++m) { dst[m] = Df[m]; dst[rec_goff<R, N>() + m] = Dg[m]; }
     }
 }
 
-// The ten values of distribution D (0 = f, 1 = g) of one record.
-template <class R, int D>
-__device__ __forceinline__ void load10(const R* rec, R* v)
+// The ncoef(N) values of distribution D (0 = f, 1 = g) of one record.
+template <class R, int N, int D>
+__device__ __forceinline__ void load_one(const R* rec, R* v)
 {
-    if constexpr (std::is_same<R, float>::value) {
+    if constexpr (N == 4) {
+        const R* q = rec + D * rec_goff<R, 4>();
+        if constexpr (std::is_same<R, float>::value) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 t = reinterpret_cast<const float4*>(q)[k];
+                v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z;
+                if (k < 3) v[4 * k + 3] = t.w;
+            }
+        } else if constexpr (D == 0) {              // 0..13 in pairs, then 14
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                const double2 t = reinterpret_cast<const double2*>(q)[k];
+                v[2 * k] = t.x;
+                v[2 * k + 1] = t.y;
+            }
+            v[14] = q[14];
+        } else {                                    // 15, then 16..29 in pairs
+            v[0] = q[0];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                const double2 t = reinterpret_cast<const double2*>(q + 1)[k];
+                v[1 + 2 * k] = t.x;
+                v[2 + 2 * k] = t.y;
+            }
+        }
+    } else if constexpr (std::is_same<R, float>::value) {
         if constexpr (D == 0) {
             const float4 a = reinterpret_cast<const float4*>(rec)[0];
             const float4 b = reinterpret_cast<const float4*>(rec)[1];
@@ -332,18 +398,20 @@ __device__ __forceinline__ void load10(const R* rec, R* v)
     } else {
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            const double2 t = reinterpret_cast<const double2*>(rec + D * NCOEF)[k];
+            const double2 t = reinterpret_cast<const double2*>(rec + D * 10)[k];
             v[2 * k] = t.x;
             v[2 * k + 1] = t.y;
         }
     }
 }
 
-// The values of ND distributions of one record starting at distribution d0 (ND = 2: all 20).
-template <class R, int ND>
+// The values of ND distributions of one record starting at distribution d0 (ND = 2, N = 3:
+// all 20 values with five or ten 16-byte loads).
+template <class R, int N, int ND>
 __device__ __forceinline__ void load_dist(const R* rec, int d0, R* v)
 {
     if constexpr (ND == 2) {
+        static_assert(N == 3, "both distributions in one pass only for N = 3");
         if constexpr (std::is_same<R, float>::value) {
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
@@ -358,7 +426,7 @@ __device__ __forceinline__ void load_dist(const R* rec, int d0, R* v)
             }
         }
     } else {
-        if (d0 == 0) load10<R, 0>(rec, v); else load10<R, 1>(rec, v);
+        if (d0 == 0) load_one<R, N, 0>(rec, v); else load_one<R, N, 1>(rec, v);
     }
 }
 
@@ -373,11 +441,13 @@ __device__ __forceinline__ R pick(const R* w, int j, int n)
     return v;
 }
 
-// Bytes of dynamic shared memory of the step kernel: the staged box, 20 values per node.
+// Bytes of dynamic shared memory of the step kernel: the staged box, one record per node.
 __host__ __device__ constexpr size_t step_smem_bytes(int rbytes, int q1, bool one_d, int box_w,
                                                      int box_h, int nodes)
 {
-    return (void)q1, (void)one_d, (void)nodes, (size_t)box_w * box_h * 2 * NCOEF * rbytes;
+    return (void)one_d, (void)nodes,
+           (size_t)box_w * box_h * rbytes *
+               (q1 == 5 ? (rbytes == 4 ? 36 : 30) : 20);
 }
 
 template <class R>
@@ -387,7 +457,7 @@ __device__ __forceinline__ LatRow<R> lat_row(const Lattice& L, int a)
     r.c = lat_c<R>(L, a);
     r.w = lat_w<R>(L, a);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         r.he[k] = lat_he<R>(L, a, k);
         r.hn[k] = lat_hn<R>(L, a, k);
     }
@@ -408,15 +478,17 @@ __device__ __forceinline__ RefState<R> tile_reference(const CaseRun& p, int TX, 
     rf.uy = p.mac_in[2 * N + c];
     rf.T = p.mac_in[3 * N + c];
     const double P = rf.rho * rf.T;
-    const double E = (p.split == 0) ? rf.rho * (p.cv * rf.T + 0.5 * (rf.ux * rf.ux + rf.uy * rf.uy))
-                                    : p.cv * P;
+    const double Etot = rf.rho * (p.cv * rf.T + 0.5 * (rf.ux * rf.ux + rf.uy * rf.uy));
+    // B_00 of g's equilibrium, and the energy per mass whose balance gives T
+    const double E = p.split == 0 ? Etot : (p.split == 1 ? p.cv * P : (p.cv - 1.0) * P);
+    const double e = p.split == 1 ? p.cv * rf.T : Etot / rf.rho;
     rf.rhoR = R(rf.rho);
     rf.uxR = R(rf.ux);
     rf.uyR = R(rf.uy);
     rf.TR = R(rf.T);
     rf.ER = R(E);
     rf.PR = R(P);
-    rf.eR = R(E / rf.rho);
+    rf.eR = R(e);
     rf.isT = R(1.0 / sqrt(rf.T));
     rf.invT = R(1.0 / rf.T);
     rf.cvR = R(p.cv);
@@ -472,34 +544,34 @@ __device__ __forceinline__ void footprint_box(const CaseRun& p, const StepParams
 // Frame of the final moments lambda* and the maps of the collision (Sec. III.A, collision in the
 // frame of the streamed populations' moments).  Inputs are the deviations of the last
 // iteration: u - u_bar, T - T_bar, u - u_r, T - T_r, rho - rho_r.
-template <class R>
+template <class R, int N>
 struct FinalFrame {
-    Tau<R> dx, dy;          // lambda_bar -> lambda* (deviation part)
-    Tau<R> rx, ry;          // lambda_r -> lambda* (reference part)
+    Tau<R, N> dx, dy;       // lambda_bar -> lambda* (deviation part)
+    Tau<R, N> rx, ry;       // lambda_r -> lambda* (reference part)
     R rdx, rdy, rsig;       // (u_r - u*)/sqrt(T*), T_r/T* - 1
     R isTn, iTn, TnR, rhoN, keep;
 };
 
-template <class R>
-__device__ __forceinline__ FinalFrame<R> final_frame(const RefState<R>& rf, double mu, R drho, R dubx,
-                                                     R duby, R durx, R dury, R dTr, R dTb)
+template <class R, int N>
+__device__ __forceinline__ FinalFrame<R, N> final_frame(const RefState<R>& rf, double mu, R drho, R dubx,
+                                                        R duby, R durx, R dury, R dTr, R dTb)
 {
-    FinalFrame<R> ff;
+    FinalFrame<R, N> ff;
     ff.TnR = rf.TR + dTr;
     ff.isTn = R(1) / sqrt_r<R>(ff.TnR);
     ff.iTn = ff.isTn * ff.isTn;
     {
         const R sig = -dTb * ff.iTn;                          // T_bar/T* - 1
         const R s = sqrt_r<R>(R(1) + sig);
-        ff.dx = make_tau_sig<R>(s, -dubx * ff.isTn, sig);
-        ff.dy = make_tau_sig<R>(s, -duby * ff.isTn, sig);
+        ff.dx = make_tau_sig<R, N>(s, -dubx * ff.isTn, sig);
+        ff.dy = make_tau_sig<R, N>(s, -duby * ff.isTn, sig);
     }
     ff.rsig = -dTr * ff.iTn;                                  // T_r/T* - 1
     const R s = sqrt_r<R>(R(1) + ff.rsig);
     ff.rdx = -durx * ff.isTn;                                 // (u_r - u*)/sqrt(T*)
     ff.rdy = -dury * ff.isTn;
-    ff.rx = make_tau_sig<R>(s, ff.rdx, ff.rsig);
-    ff.ry = make_tau_sig<R>(s, ff.rdy, ff.rsig);
+    ff.rx = make_tau_sig<R, N>(s, ff.rdx, ff.rsig);
+    ff.ry = make_tau_sig<R, N>(s, ff.rdy, ff.rsig);
     ff.rhoN = rf.rhoR + drho;
     const R tau = R(mu) / (ff.rhoN * ff.TnR);                 // tau = mu / (rho T)
     ff.keep = R(1) - R(1) / (tau + R(0.5));                   // 1 - omega
@@ -510,40 +582,43 @@ __device__ __forceinline__ FinalFrame<R> final_frame(const RefState<R>& rf, doub
 // moved into lambda*, the reference part rho_r moved lambda_r -> lambda* is added (its order
 // 0 and 1 terms are the equilibrium's), and the non-equilibrium part is relaxed and written.
 // A*_10 = A*_01 = 0 hold by definition of lambda*.
-template <class S, class R>
-__device__ __forceinline__ void collide_f(const FinalFrame<R>& ff, const RefState<R>& rf, R* Af, S* nout,
-                                          long long N, long long node)
+template <class S, class R, int N>
+__device__ __forceinline__ void collide_f(const FinalFrame<R, N>& ff, const RefState<R>& rf, R* Af, S* nout,
+                                          long long Nn, long long node)
 {
-    retarget(ff.dx, ff.dy, Af, Af);
-    const R hx[4] = {R(1), ff.rx.t10, ff.rx.t20, ff.rx.t30};
-    const R hy[4] = {R(1), ff.ry.t10, ff.ry.t20, ff.ry.t30};
+    constexpr int NC = ncoef(N);
+    retarget<R, N>(ff.dx, ff.dy, Af, Af);
 #pragma unroll
-    for (int pp = 0; pp <= 3; ++pp)
+    for (int pp = 0; pp <= N; ++pp)
 #pragma unroll
-        for (int q = 0; q <= 3 - pp; ++q)
-            if (pp + q >= 2) Af[slot(pp, q)] += rf.rhoR * hx[pp] * hy[q];
-    sto_put<S, R>(nout + 0 * N + node, R(0));
-    sto_put<S, R>(nout + 1 * N + node, R(0));
+        for (int q = 0; q <= N - pp; ++q)
+            if (pp + q >= 2) Af[slot(pp, q)] += rf.rhoR * tx0(ff.rx, pp) * tx0(ff.ry, q);
+    sto_put<S, R>(nout + 0 * Nn + node, R(0));
+    sto_put<S, R>(nout + 1 * Nn + node, R(0));
 #pragma unroll
-    for (int m = 3; m < NCOEF; ++m) sto_put<S, R>(nout + (long long)(m - 1) * N + node, ff.keep * Af[m]);
+    for (int m = 3; m < NC; ++m) sto_put<S, R>(nout + (long long)(m - 1) * Nn + node, ff.keep * Af[m]);
 }
 
 // BGK relaxation of g in lambda*: the reference equilibrium moved into lambda* minus the
 // equilibrium of lambda* itself (the same expansion as for a staged node, with the reference as
-// the node and lambda* as the base) is added; B*_00 = B_00^eq holds by definition of T*.
-template <class S, class R>
-__device__ __forceinline__ void collide_g(int split, const FinalFrame<R>& ff, const RefState<R>& rf,
-                                          R drho, R durx, R dury, R dTr, R* Ag, S* nout, long long N,
+// the node and lambda* as the base) is added.  Total and internal splits: B*_00 = B_00^eq by
+// definition of T*.  Non-translational split: T* also takes f's second moment, so B*_00 - U'*
+// balances f's non-equilibrium A*_20 + A*_02 and is relaxed like the other coefficients.
+template <class S, class R, int N>
+__device__ __forceinline__ void collide_g(int split, const FinalFrame<R, N>& ff, const RefState<R>& rf,
+                                          R drho, R durx, R dury, R dTr, R* Ag, S* nout, long long Nn,
                                           long long node)
 {
-    retarget(ff.dx, ff.dy, Ag, Ag);
+    constexpr int NC = ncoef(N);
+    retarget<R, N>(ff.dx, ff.dy, Ag, Ag);
     const R dP = -(drho * ff.TnR + rf.rhoR * dTr);            // p_r - p*
     const BaseFrame<R> bf = {rf.PR - dP, ff.isTn, ff.iTn};    // p* = rho T*
-    add_g_eq_dev<R>(split, bf, ff.rx, ff.ry, ff.rdx, ff.rdy, ff.rsig, rf.ER, R(0), rf.PR, rf.uxR, rf.uyR,
-                    dP, -durx, -dury, rf.TR, -dTr, Ag);
-    sto_put<S, R>(nout + 9 * N + node, R(0));
+    const R dE = split == 2 ? (rf.cvR - R(1)) * dP : R(0);    // U'_r - U'*
+    add_g_eq_dev<R, N>(split, bf, ff.rx, ff.ry, ff.rdx, ff.rdy, ff.rsig, rf.ER, dE, rf.PR, rf.uxR, rf.uyR,
+                       dP, -durx, -dury, rf.TR, -dTr, Ag);
+    sto_put<S, R>(nout + (long long)(NC - 1) * Nn + node, split == 2 ? ff.keep * Ag[0] : R(0));
 #pragma unroll
-    for (int m = 1; m < NCOEF; ++m) sto_put<S, R>(nout + (long long)(9 + m) * N + node, ff.keep * Ag[m]);
+    for (int m = 1; m < NC; ++m) sto_put<S, R>(nout + (long long)(NC - 1 + m) * Nn + node, ff.keep * Ag[m]);
 }
 
 // Per-warp sums of the step statistics, one atomic per warp (every lane of the warp calls it).
@@ -591,6 +666,9 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     const bool active = (x < p.nx) && (y < p.ny);
     const long long N = p.N;
     const long long node = active ? (long long)y * p.nx + x : 0;
+    constexpr int NG = grad_order_of_q1(Q1);                 // Grad order of the lattice
+    constexpr int NC = ncoef(NG);
+    constexpr int REC = rec_len<R, NG>();
 
     if (tid < Q1) lat[tid] = lat_row<R>(pp.lat, tid);
     // ---- own frame (predictor) and the tile's reference state ------------------------------
@@ -615,9 +693,9 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
         int lx = i % bw, ly = i / bw;
         int sx = bc_map(ox + lx, p.nx, p.bc_x);
         int sy = ONE_D ? 0 : bc_map(oy + ly, p.ny, p.bc_y);
-        R D[2 * NCOEF];
-        source_dev<S, R>(p, rf, (long long)sy * p.nx + sx, D, D + NCOEF);
-        store20<R>(sm + (size_t)i * 2 * NCOEF, D);
+        R D[2 * NC];
+        source_dev<S, R, NG>(p, rf, (long long)sy * p.nx + sx, D, D + NC);
+        store_rec<R, NG>(sm + (size_t)i * REC, D, D + NC);
     }
     __syncthreads();
 
@@ -628,7 +706,7 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     double ubx = ux0, uby = uy0, Tb = T0;
     double unx = ux0, uny = uy0, Tn = T0;
     R drho = R(0), dubx = R(0), duby = R(0), durx = R(0), dury = R(0), dTr = R(0), dTb = R(0);
-    R Af[NCOEF], Ag[NCOEF];   // deviation coefficients of the streamed populations in lambda_bar
+    R Af[NC], Ag[NC];         // deviation coefficients of the streamed populations in lambda_bar
 
     if (active) {
         while (true) {
@@ -640,11 +718,11 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
             const R iTb = isT * isT;
             const R sig_t = rbT * iTb;                             // T_r / T_bar - 1
             const R s_rb = sTr * isT, dx_rb = rbx * isT, dy_rb = rby * isT;   // lambda_r -> lambda_bar
-            const Tau<R> txr = make_tau_sig<R>(s_rb, dx_rb, sig_t);
-            const Tau<R> tyr = make_tau_sig<R>(s_rb, dy_rb, sig_t);
+            const Tau<R, NG> txr = make_tau_sig<R, NG>(s_rb, dx_rb, sig_t);
+            const Tau<R, NG> tyr = make_tau_sig<R, NG>(s_rb, dy_rb, sig_t);
             const R ubxr = rf.uxR - rbx, ubyr = rf.uyR - rby;      // u_bar
 #pragma unroll
-            for (int m = 0; m < NCOEF; ++m) { Af[m] = R(0); Ag[m] = R(0); }
+            for (int m = 0; m < NC; ++m) { Af[m] = R(0); Ag[m] = R(0); }
 
             if constexpr (!ONE_D) {
                 // y stencils of all b (shared by every a and both distributions)
@@ -665,46 +743,46 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                     const int jx = lagrange<R, P>(-(sT * la.c + ubxr), wx);
                     const int tx0 = x + jx - ox;
                     const bool cols_in = tx0 >= 0 && tx0 + P <= bw;
-                    R phi[2 * NCOEF];
+                    R phi[nphi(NG)];
                     {
                         // the iteration's moves, rebuilt here so that only four scalars stay live
-                        const Tau<R> tx = make_tau_sig<R>(s_rb, dx_rb, sig_t);
-                        const Tau<R> ty = make_tau_sig<R>(s_rb, dy_rb, sig_t);
-                        make_phi<R>(la, tx, ty, phi);
+                        const Tau<R, NG> tx = make_tau_sig<R, NG>(s_rb, dx_rb, sig_t);
+                        const Tau<R, NG> ty = make_tau_sig<R, NG>(s_rb, dy_rb, sig_t);
+                        make_phi<R, NG>(la, tx, ty, phi);
                     }
-                    // FP32: both distributions in one pass over the rows (each record is five
-                    // 16-byte loads and the row overhead is shared); FP64: one pass each
-                    constexpr int ND = std::is_same<R, float>::value ? 2 : 1;
+                    // FP32, N = 3: both distributions in one pass over the rows (each record is
+                    // five 16-byte loads and the row overhead is shared); otherwise one pass each
+                    constexpr int ND = (std::is_same<R, float>::value && NG == 3) ? 2 : 1;
 #pragma unroll
                     for (int d0 = 0; d0 < 2; d0 += ND) {
                         // x pass once per row of the union of the y stencils, folded into Z_q,
                         // then added to the b's whose y stencil contains the row
-                        R acc[ND][Q1][4];
+                        R acc[ND][Q1][NG + 1];
 #pragma unroll
                         for (int e = 0; e < ND; ++e)
 #pragma unroll
                             for (int b = 0; b < Q1; ++b)
 #pragma unroll
-                                for (int q = 0; q < 4; ++q) acc[e][b][q] = R(0);
+                                for (int q = 0; q <= NG; ++q) acc[e][b][q] = R(0);
                         if (rows_in && cols_in) {
-                            const R* rowp = sm + ((size_t)(y + rmin - oy) * bw + tx0) * 2 * NCOEF;
+                            const R* rowp = sm + ((size_t)(y + rmin - oy) * bw + tx0) * REC;
 #pragma unroll 1
-                            for (int r = rmin; r <= rmax; ++r, rowp += (size_t)bw * 2 * NCOEF) {
-                                R X[ND][NCOEF];
+                            for (int r = rmin; r <= rmax; ++r, rowp += (size_t)bw * REC) {
+                                R X[ND][NC];
 #pragma unroll
                                 for (int ii = 0; ii < P; ++ii) {
-                                    R v[ND * NCOEF];
-                                    load_dist<R, ND>(rowp + ii * 2 * NCOEF, d0, v);
+                                    R v[ND * NC];
+                                    load_dist<R, NG, ND>(rowp + ii * REC, d0, v);
 #pragma unroll
                                     for (int e = 0; e < ND; ++e)
 #pragma unroll
-                                        for (int m = 0; m < NCOEF; ++m)
-                                            X[e][m] = (ii == 0) ? wx[0] * v[e * NCOEF + m]
-                                                                : X[e][m] + wx[ii] * v[e * NCOEF + m];
+                                        for (int m = 0; m < NC; ++m)
+                                            X[e][m] = (ii == 0) ? wx[0] * v[e * NC + m]
+                                                                : X[e][m] + wx[ii] * v[e * NC + m];
                                 }
-                                R Z[ND][4];
+                                R Z[ND][NG + 1];
 #pragma unroll
-                                for (int e = 0; e < ND; ++e) z_contract<R>(phi, X[e], Z[e]);
+                                for (int e = 0; e < ND; ++e) z_contract<R, NG>(phi, X[e], Z[e]);
 #pragma unroll
                                 for (int b = 0; b < Q1; ++b) {
                                     const int j = r - jy[b];
@@ -713,7 +791,7 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
 #pragma unroll
                                         for (int e = 0; e < ND; ++e)
 #pragma unroll
-                                            for (int q = 0; q < 4; ++q) acc[e][b][q] += w * Z[e][q];
+                                            for (int q = 0; q <= NG; ++q) acc[e][b][q] += w * Z[e][q];
                                     }
                                 }
                             }
@@ -730,14 +808,14 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                                     for (int ii = 0; ii < P; ++ii) {
                                         const R wxi = pick<R>(wx, ii, P);
                                         const int sx = bc_map(x + jx + ii, p.nx, p.bc_x);
-                                        R D[2 * NCOEF];
-                                        source_dev<S, R>(p, rf, (long long)sy * p.nx + sx, D, D + NCOEF);
+                                        R D[2 * NC];
+                                        source_dev<S, R, NG>(p, rf, (long long)sy * p.nx + sx, D, D + NC);
 #pragma unroll
                                         for (int e = 0; e < ND; ++e) {
-                                            R Z[4];
-                                            z_contract<R>(phi, D + (d0 + e) * NCOEF, Z);
+                                            R Z[NG + 1];
+                                            z_contract<R, NG>(phi, D + (d0 + e) * NC, Z);
 #pragma unroll
-                                            for (int q = 0; q < 4; ++q) acc[e][b][q] += wyj * wxi * Z[q];
+                                            for (int q = 0; q <= NG; ++q) acc[e][b][q] += wyj * wxi * Z[q];
                                         }
                                     }
                                 }
@@ -745,21 +823,23 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                         // populations (a, b): f'_ab = w_b sum_q hn_b(q) acc_b(q); their moments
 #pragma unroll
                         for (int e = 0; e < ND; ++e) {
-                            R Sq[4] = {R(0), R(0), R(0), R(0)};
+                            R Sq[NG + 1];
+#pragma unroll
+                            for (int q = 0; q <= NG; ++q) Sq[q] = R(0);
 #pragma unroll
                             for (int b = 0; b < Q1; ++b) {
                                 const LatRow<R>& lb = lat[b];
                                 R val = R(0);
 #pragma unroll
-                                for (int q = 0; q < 4; ++q) val += lb.hn[q] * acc[e][b][q];
+                                for (int q = 0; q <= NG; ++q) val += lb.hn[q] * acc[e][b][q];
                                 val *= lb.w;
 #pragma unroll
-                                for (int q = 0; q < 4; ++q) Sq[q] += val * lb.he[q];
+                                for (int q = 0; q <= NG; ++q) Sq[q] += val * lb.he[q];
                             }
 #pragma unroll
-                            for (int pq = 0; pq <= 3; ++pq)
+                            for (int pq = 0; pq <= NG; ++pq)
 #pragma unroll
-                                for (int q = 0; q <= 3 - pq; ++q) {
+                                for (int q = 0; q <= NG - pq; ++q) {
                                     if (d0 + e == 0) Af[slot(pq, q)] += la.he[pq] * Sq[q];
                                     else Ag[slot(pq, q)] += la.he[pq] * Sq[q];
                                 }
@@ -775,19 +855,19 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                     R wx[P];
                     const int jx = lagrange<R, P>(-(sT * la.c + ubxr), wx);
                     const int tx0 = x + jx - ox;
-                    R Ri[2 * NCOEF];
+                    R Ri[2 * NC];
 #pragma unroll
-                    for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] = R(0);
+                    for (int m = 0; m < 2 * NC; ++m) Ri[m] = R(0);
                     if (tx0 >= 0 && tx0 + P <= bw) {
 #pragma unroll
                         for (int ii = 0; ii < P; ++ii) {
-                            R v[NCOEF];
-                            load10<R, 0>(sm + (size_t)(tx0 + ii) * 2 * NCOEF, v);
+                            R v[NC];
+                            load_one<R, NG, 0>(sm + (size_t)(tx0 + ii) * REC, v);
 #pragma unroll
-                            for (int m = 0; m < NCOEF; ++m) Ri[m] += wx[ii] * v[m];
-                            load10<R, 1>(sm + (size_t)(tx0 + ii) * 2 * NCOEF, v);
+                            for (int m = 0; m < NC; ++m) Ri[m] += wx[ii] * v[m];
+                            load_one<R, NG, 1>(sm + (size_t)(tx0 + ii) * REC, v);
 #pragma unroll
-                            for (int m = 0; m < NCOEF; ++m) Ri[NCOEF + m] += wx[ii] * v[m];
+                            for (int m = 0; m < NC; ++m) Ri[NC + m] += wx[ii] * v[m];
                         }
                     } else {
                         ++fallbacks;
@@ -795,40 +875,42 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                         for (int ii = 0; ii < P; ++ii) {
                             const R W = pick<R>(wx, ii, P);
                             const int sx = bc_map(x + jx + ii, p.nx, p.bc_x);
-                            R D[2 * NCOEF];
-                            source_dev<S, R>(p, rf, (long long)sx, D, D + NCOEF);
+                            R D[2 * NC];
+                            source_dev<S, R, NG>(p, rf, (long long)sx, D, D + NC);
 #pragma unroll
-                            for (int m = 0; m < 2 * NCOEF; ++m) Ri[m] += W * D[m];
+                            for (int m = 0; m < 2 * NC; ++m) Ri[m] += W * D[m];
                         }
                     }
                     // the y taps all read row 0 with weights summing to one, so every b sees
                     // the same folded values Z (see make_phi)
-                    R phi[2 * NCOEF], Zf[4], Zg[4];
-                    make_phi<R>(la, txr, tyr, phi);
-                    z_contract<R>(phi, Ri, Zf);
-                    z_contract<R>(phi, Ri + NCOEF, Zg);
-                    R Sf[4] = {R(0), R(0), R(0), R(0)}, Sg[4] = {R(0), R(0), R(0), R(0)};
+                    R phi[nphi(NG)], Zf[NG + 1], Zg[NG + 1];
+                    make_phi<R, NG>(la, txr, tyr, phi);
+                    z_contract<R, NG>(phi, Ri, Zf);
+                    z_contract<R, NG>(phi, Ri + NC, Zg);
+                    R Sf[NG + 1], Sg[NG + 1];
+#pragma unroll
+                    for (int q = 0; q <= NG; ++q) { Sf[q] = R(0); Sg[q] = R(0); }
 #pragma unroll
                     for (int b = 0; b < Q1; ++b) {
                         const LatRow<R>& lb = lat[b];
                         R f = R(0), g = R(0);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q <= NG; ++q) {
                             f += lb.hn[q] * Zf[q];
                             g += lb.hn[q] * Zg[q];
                         }
                         f *= lb.w;
                         g *= lb.w;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q <= NG; ++q) {
                             Sf[q] += f * lb.he[q];
                             Sg[q] += g * lb.he[q];
                         }
                     }
 #pragma unroll
-                    for (int pp = 0; pp <= 3; ++pp)
+                    for (int pp = 0; pp <= NG; ++pp)
 #pragma unroll
-                        for (int q = 0; q <= 3 - pp; ++q) {
+                        for (int q = 0; q <= NG - pp; ++q) {
                             Af[slot(pp, q)] += la.he[pp] * Sf[q];
                             Ag[slot(pp, q)] += la.he[pp] * Sg[q];
                         }
@@ -844,9 +926,16 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
             duby = (rf.rhoR * rby + sT * Af[slot(0, 1)]) * irho;
             durx = dubx - rbx;                                        // u - u_r
             dury = duby - rby;
-            // c_v (T - T_r) = (dE - e_r drho)/rho [- (u - u_r).(u + u_r)/2 for the total split]
-            R cvdT = (Ag[slot(0, 0)] - rf.eR * drho) * irho;
-            if (p.split == 0)
+            // energy deviation: sum g' (total, internal), plus sum |C|^2/2 f' for the
+            // non-translational split, |C|^2 = T_bar (He_2(c_x) + He_2(c_y) + 2) + 2 sqrt(T_bar) c.u_bar + u_bar^2
+            R dEt = Ag[slot(0, 0)];
+            if (p.split == 2)
+                dEt += R(0.5) * (sT * sT * (Af[slot(2, 0)] + Af[slot(0, 2)] + R(2) * drho) +
+                                 R(2) * sT * (ubxr * Af[slot(1, 0)] + ubyr * Af[slot(0, 1)]) +
+                                 (ubxr * ubxr + ubyr * ubyr) * drho);
+            // c_v (T - T_r) = (dE - e_r drho)/rho [- (u - u_r).(u + u_r)/2 unless internal split]
+            R cvdT = (dEt - rf.eR * drho) * irho;
+            if (p.split != 1)
                 cvdT -= R(0.5) * (durx * (R(2) * rf.uxR + durx) + dury * (R(2) * rf.uyR + dury));
             dTr = cvdT * R(p.inv_cv);                                 // T - T_r
             dTb = dTr + rbT;                                          // T - T_bar
@@ -875,11 +964,11 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
         p.mac_out[2 * N + node] = uny;
         p.mac_out[3 * N + node] = Tn;
         if (!bad) {
-            const FinalFrame<R> ff = final_frame<R>(rf, p.mu, drho, dubx, duby, durx, dury, dTr, dTb);
-            collide_f<S, R>(ff, rf, Af, nout, N, node);
-            collide_g<S, R>(p.split, ff, rf, drho, durx, dury, dTr, Ag, nout, N, node);
+            const FinalFrame<R, NG> ff = final_frame<R, NG>(rf, p.mu, drho, dubx, duby, durx, dury, dTr, dTb);
+            collide_f<S, R, NG>(ff, rf, Af, nout, N, node);
+            collide_g<S, R, NG>(p.split, ff, rf, drho, durx, dury, dTr, Ag, nout, N, node);
         } else {
-            for (int m = 0; m < NNEQ; ++m) sto_put<S, R>(nout + (long long)m * N + node, R(NAN));
+            for (int m = 0; m < nneq(NG); ++m) sto_put<S, R>(nout + (long long)m * N + node, R(NAN));
         }
     }
     report_stats(p.status, tid, active ? (unsigned int)k : 0u, (active && nonconv) ? 1u : 0u, fallbacks,

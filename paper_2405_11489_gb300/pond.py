@@ -23,13 +23,13 @@ LIB_PATH = os.environ.get("POND_LIB") or os.path.join(_HERE, "_build", "libpond.
 
 POND_OK, POND_EINVAL, POND_ENOMEM, POND_ECUDA, POND_ENONPHYSICAL, POND_ENOCONV = 0, -1, -2, -3, -4, -5
 POND_D2Q16, POND_D2Q25 = 16, 25
-POND_SPLIT_TOTAL, POND_SPLIT_INTERNAL = 0, 1
+POND_SPLIT_TOTAL, POND_SPLIT_INTERNAL, POND_SPLIT_NT = 0, 1, 2
 POND_FP64, POND_MIXED_FP32, POND_MIXED_FP16, POND_MIXED_BF16 = 0, 1, 2, 3
 POND_BC_PERIODIC, POND_BC_OUTFLOW = 0, 1
 
 PRECISIONS = {"fp64": POND_FP64, "fp32": POND_MIXED_FP32, "fp16": POND_MIXED_FP16,
               "bf16": POND_MIXED_BF16}
-SPLITS = {"total": POND_SPLIT_TOTAL, "internal": POND_SPLIT_INTERNAL}
+SPLITS = {"total": POND_SPLIT_TOTAL, "internal": POND_SPLIT_INTERNAL, "nt": POND_SPLIT_NT}
 BCS = {"periodic": POND_BC_PERIODIC, "outflow": POND_BC_OUTFLOW}
 
 # Symbols the header declares (checked by the ABI test).
@@ -49,7 +49,8 @@ class pond_config(ctypes.Structure):
                 ("interp_order", ctypes.c_int32), ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
                 ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("pc_tol", ctypes.c_double),
                 ("pc_max_iter", ctypes.c_int32), ("pc_fixed_iters", ctypes.c_int32),
-                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("halo", ctypes.c_int32)]
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("halo", ctypes.c_int32),
+                ("grad_order", ctypes.c_int32)]
 
 
 class pond_stats(ctypes.Structure):
@@ -288,6 +289,7 @@ class Config:
     tile_x: int = 0
     tile_y: int = 0
     halo: int = 0
+    grad_order: int = 0       # 0: the lattice's (3 on D2Q16, 4 on D2Q25)
 
     def to_c(self) -> pond_config:
         tol = self.pc_tol if self.pc_tol is not None else (1e-12 if self.precision == "fp64" else 1e-6)
@@ -296,7 +298,7 @@ class Config:
                            bc_x=BCS[self.bc_x], bc_y=BCS[self.bc_y], gamma=self.gamma, mu=self.mu,
                            pc_tol=tol, pc_max_iter=self.pc_max_iter,
                            pc_fixed_iters=self.pc_fixed_iters, tile_x=self.tile_x,
-                           tile_y=self.tile_y, halo=self.halo)
+                           tile_y=self.tile_y, halo=self.halo, grad_order=self.grad_order)
 
     @property
     def Q(self) -> int:

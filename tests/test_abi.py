@@ -51,7 +51,8 @@ def test_host_side_calls_without_gpu(lib):
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("lattice", 9), ("gamma", 2.5), ("gamma", 1.0),
                                          ("mu", 0.0), ("interp_order", 5), ("pc_max_iter", 0),
-                                         ("bc_x", 7), ("precision", 9), ("tile_x", 48)])
+                                         ("bc_x", 7), ("precision", 9), ("tile_x", 48), ("split", 3),
+                                         ("grad_order", 4), ("grad_order", 2)])
 def test_invalid_configs_are_rejected(lib, field, value):
     from paper_2405_11489_gb300 import pond
     cfg = pond.pond_config_default(16, 16)

@@ -55,7 +55,7 @@ def make_pair(pond, orc, nx, ny, lattice=16, split="total", order=3, bc=("period
               K=2, tol=1e-12, precision="fp64", halo=0, gamma=1.4, mu=0.02, maxit=20):
     ocfg = orc.make_config(nx, ny, lattice=lattice, split=split, interp_order=order, bc_x=bc[0],
                            bc_y=bc[1], gamma=gamma, mu=mu, pc_tol=tol, pc_max_iter=maxit,
-                           pc_fixed_iters=K, grad_order=3)
+                           pc_fixed_iters=K)
     gcfg = pond.Config(nx=nx, ny=ny, lattice=lattice, split=split, precision=precision,
                        interp_order=order, bc_x=bc[0], bc_y=bc[1], gamma=gamma, mu=mu, pc_tol=tol,
                        pc_max_iter=maxit, pc_fixed_iters=K, halo=halo)
@@ -99,6 +99,9 @@ CASES = [
     (29, 10, 25, "total", 3, ("periodic", "periodic")),
     (26, 7, 25, "internal", 3, ("outflow", "periodic")),
     (31, 9, 16, "total", 2, ("periodic", "periodic")),
+    (27, 8, 25, "nt", 3, ("periodic", "periodic")),
+    (30, 7, 16, "nt", 3, ("outflow", "periodic")),
+    (25, 9, 25, "nt", 2, ("outflow", "outflow")),
 ]
 
 
@@ -208,13 +211,14 @@ def test_nonconvergence_is_reported(pond, orc):
     sim.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_checkpoint_resume_is_bit_identical(pond, orc, precision):
+@pytest.mark.parametrize("precision,lattice,split", [("fp64", 16, "total"), ("fp32", 16, "total"),
+                                                    ("fp32", 25, "nt"), ("fp64", 25, "total")])
+def test_checkpoint_resume_is_bit_identical(pond, orc, precision, lattice, split):
     """Export after 3 steps, import into a fresh simulation, 3 more steps: identical to 6
     straight steps (device and host checkpoints)."""
     from paper_2405_11489_gb300 import workloads as W
     c = W.shear_wave(n=48, ny=20, ma=1.0, amp=0.05, mu=0.05)
-    cfg = pond.Config(nx=c.nx, ny=c.ny, precision=precision, mu=c.mu)
+    cfg = pond.Config(nx=c.nx, ny=c.ny, precision=precision, mu=c.mu, lattice=lattice, split=split)
     a = pond.Simulation(cfg)
     a.set_state(c.rho, c.ux, c.uy, c.T)
     a.step(6)

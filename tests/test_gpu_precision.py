@@ -42,22 +42,26 @@ def _l1(a, b, scale):
 BOUNDS = {"fp32": (5e-8, 1e-7), "fp16": (2e-6, 2e-5), "bf16": (2e-5, 2e-4)}
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
-@pytest.mark.parametrize("split", ["total", "internal"])
-def test_mixed_precision_l1_bounds(pond, orc, precision, split):
+MIXED_CASES = [(prec, 16, split) for prec in ("fp32", "fp16", "bf16")
+               for split in ("total", "internal", "nt")] + \
+              [("fp32", 25, "total"), ("fp32", 25, "nt"), ("bf16", 25, "nt")]
+
+
+@pytest.mark.parametrize("precision,lattice,split", MIXED_CASES)
+def test_mixed_precision_l1_bounds(pond, orc, precision, lattice, split):
     nx, ny, steps = 48, 40, 20
     y, x = np.mgrid[0:ny, 0:nx]
     rho = 1.0 + 0.02 * np.sin(2 * math.pi * x / nx) * np.cos(2 * math.pi * y / ny)
     ux = 0.6 + 0.03 * np.cos(2 * math.pi * y / ny)
     uy = -0.2 + 0.03 * np.sin(2 * math.pi * x / nx)
     T = 0.8 * (1.0 + 0.02 * np.cos(2 * math.pi * (x / nx + y / ny)))
-    ocfg = orc.make_config(nx, ny, split=split, mu=0.04, pc_fixed_iters=2)
+    ocfg = orc.make_config(nx, ny, lattice=lattice, split=split, mu=0.04, pc_fixed_iters=2)
     st = orc.init_state(ocfg, rho, ux, uy, T)
     for _ in range(steps):
         st = orc.step(ocfg, st).state
     o = orc.moments(ocfg, st)
-    sim = pond.Simulation(pond.Config(nx=nx, ny=ny, precision=precision, split=split, mu=0.04,
-                                      pc_fixed_iters=2))
+    sim = pond.Simulation(pond.Config(nx=nx, ny=ny, lattice=lattice, precision=precision, split=split,
+                                      mu=0.04, pc_fixed_iters=2))
     sim.set_state(rho, ux, uy, T)
     sim.step(steps)
     g = sim.moments()
@@ -65,7 +69,7 @@ def test_mixed_precision_l1_bounds(pond, orc, precision, split):
     speed = max(np.abs(o[1]).max(), np.abs(o[2]).max(), math.sqrt(o[3].max()))
     errs = {"rho": _l1(g[0], o[0], np.mean(np.abs(o[0]))), "T": _l1(g[3], o[3], np.mean(o[3])),
             "ux": _l1(g[1], o[1], speed), "uy": _l1(g[2], o[2], speed)}
-    print(precision, split, errs)
+    print(precision, lattice, split, errs)
     assert errs["rho"] <= brt and errs["T"] <= brt, errs
     assert errs["ux"] <= bu and errs["uy"] <= bu, errs
     sim.close()

@@ -37,21 +37,23 @@ def _fields(nx, ny):
     return rho, ux, uy, T
 
 
-def _views(torch, mac, neq, precision, nx, ny):
+def _views(torch, mac, neq, precision, nx, ny, planes=19):
     dt = {"fp64": torch.float64, "fp32": torch.float32, "fp16": torch.float16,
           "bf16": torch.bfloat16}[precision]
     N = nx * ny
     return (mac[: 4 * N * 8].view(torch.float64).cpu().numpy().reshape(4, N),
-            neq[: 19 * N * torch.tensor([], dtype=dt).element_size()].view(dt).float()
-            .cpu().numpy().astype(np.float64).reshape(19, N))
+            neq[: planes * N * torch.tensor([], dtype=dt).element_size()].view(dt).float()
+            .cpu().numpy().astype(np.float64).reshape(planes, N))
 
 
-@pytest.mark.parametrize("precision,split,tol", [("fp64", "total", 1e-12), ("fp32", "total", 1e-6),
-                                                 ("fp64", "internal", 1e-12)])
-def test_static_step_matches_pond_step_on_two_calls(P, precision, split, tol):
+@pytest.mark.parametrize("precision,split,tol,lattice", [("fp64", "total", 1e-12, 16), ("fp32", "total", 1e-6, 16),
+                                                         ("fp64", "internal", 1e-12, 16),
+                                                         ("fp32", "nt", 1e-6, 25)])
+def test_static_step_matches_pond_step_on_two_calls(P, precision, split, tol, lattice):
     import torch
     nx, ny = 70, 45
-    cfg = P.Config(nx=nx, ny=ny, precision=precision, split=split, mu=0.05)
+    planes = 19 if lattice == 16 else 29
+    cfg = P.Config(nx=nx, ny=ny, precision=precision, split=split, mu=0.05, lattice=lattice)
     sim = P.Simulation(cfg)
     sim.set_state(*_fields(nx, ny))
     mac, neq = sim.export_state(on_device=True)      # the caller's own device buffers
@@ -63,8 +65,8 @@ def test_static_step_matches_pond_step_on_two_calls(P, precision, split, tol):
         assert st.node_updates == nsteps * nx * ny and st.pc_iters_total >= st.node_updates
         sim.step(nsteps)
         ref_mac, ref_neq = sim.export_state(on_device=True)
-        a_mac, a_neq = _views(torch, mac, neq, precision, nx, ny)
-        r_mac, r_neq = _views(torch, ref_mac, ref_neq, precision, nx, ny)
+        a_mac, a_neq = _views(torch, mac, neq, precision, nx, ny, planes)
+        r_mac, r_neq = _views(torch, ref_mac, ref_neq, precision, nx, ny, planes)
         for k in range(4):
             scale = max(np.max(np.abs(r_mac[k])), 1.0 if k in (1, 2) else 0.0)
             assert np.max(np.abs(a_mac[k] - r_mac[k])) <= tol * scale, (call, k)
