@@ -55,7 +55,7 @@ typedef enum {
 enum { POND_D2Q16 = 16, POND_D2Q25 = 25 };                       /* Table I lattices */
 enum { POND_SPLIT_TOTAL = 0, POND_SPLIT_INTERNAL = 1, POND_SPLIT_NT = 2 };   /* Eq. Es, lines 1-3 */
 enum { POND_FP64 = 0, POND_MIXED_FP32 = 1, POND_MIXED_FP16 = 2, POND_MIXED_BF16 = 3 };
-enum { POND_BC_PERIODIC = 0, POND_BC_OUTFLOW = 1 };
+enum { POND_BC_PERIODIC = 0, POND_BC_OUTFLOW = 1, POND_BC_WALL = 2 };
 
 typedef struct {
     int32_t nx, ny;            /* grid; ny = 1 runs the quasi-1-D form (all y taps on row 0) */
@@ -68,7 +68,11 @@ typedef struct {
                                   equilibrium, FP64 rho/u/T and frame update, non-equilibrium
                                   state stored in FP32 / FP16 / BF16 */
     int32_t interp_order;      /* 3: 4-point cubic Lagrange (default); 2: 3-point (Sec. III.A.2) */
-    int32_t bc_x, bc_y;        /* POND_BC_PERIODIC (index mod n) or POND_BC_OUTFLOW (clamp) */
+    int32_t bc_x, bc_y;        /* POND_BC_PERIODIC (index mod n), POND_BC_OUTFLOW (clamp: zero-gradient
+                                  copy of the edge node) or POND_BC_WALL (not in the paper: every
+                                  position beyond the wall holds the equilibrium at the wall's
+                                  state, given in wall[]; the wall lies half a cell beyond the last
+                                  node; not for y when ny = 1) */
     double gamma;              /* adiabatic exponent, 1 < gamma <= 2 (c_v = 1/(gamma - 1)) */
     double mu;                 /* dynamic viscosity > 0; tau = mu / (rho T) per node */
     double pc_tol;             /* predictor-corrector tolerance on max(|du|/sqrt(T), |dT|/T) */
@@ -82,6 +86,9 @@ typedef struct {
     int32_t grad_order;        /* Grad expansion order N of the frame transformation
                                   (Eq. gradGeneralTransform): 0 = the lattice's, which is the
                                   only value accepted: 3 on D2Q16, 4 on D2Q25 */
+    double wall[4][4];         /* states of the walls x-low, x-high, y-low, y-high:
+                                  (u_x, u_y, T, rho), used where bc_x / bc_y = POND_BC_WALL
+                                  (T > 0, rho > 0) */
 } pond_config;
 
 typedef struct {

@@ -57,16 +57,22 @@ class Config(ctypes.Structure):
         ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("pc_tol", ctypes.c_double),
         ("pc_max_iter", ctypes.c_int32), ("pc_fixed_iters", ctypes.c_int32),
         ("grad_order", ctypes.c_int32),
+        ("wall", (ctypes.c_double * 4) * 4),
     ]
 
 
 def make_config(nx, ny, lattice=16, split="total", interp_order=3, bc_x="periodic",
                 bc_y="periodic", gamma=1.4, mu=1e-4, pc_tol=1e-12, pc_max_iter=20,
-                pc_fixed_iters=0, grad_order=0) -> Config:
+                pc_fixed_iters=0, grad_order=0, walls=None) -> Config:
     """split: "total", "internal" or "nt" (non-translational); grad_order: N = 3 or 4
-    (0: the lattice's, 3 on D2Q16 and 4 on D2Q25)."""
-    bc = {"periodic": 0, "outflow": 1}
-    return Config(nx=nx, ny=ny, q1={16: 4, 25: 5}[lattice],
+    (0: the lattice's, 3 on D2Q16 and 4 on D2Q25); bc "wall" with walls = four (u_x, u_y, T, rho)
+    for the x-low, x-high, y-low and y-high walls."""
+    bc = {"periodic": 0, "outflow": 1, "wall": 2}
+    w = ((ctypes.c_double * 4) * 4)()
+    for k, state in enumerate(walls or [(0.0, 0.0, 1.0, 1.0)] * 4):
+        for j in range(4):
+            w[k][j] = float(state[j])
+    return Config(nx=nx, ny=ny, q1={16: 4, 25: 5}[lattice], wall=w,
                   split={"total": 0, "internal": 1, "nt": 2}[split], interp_order=interp_order,
                   bc_x=bc[bc_x], bc_y=bc[bc_y], gamma=gamma, mu=mu, pc_tol=pc_tol,
                   pc_max_iter=pc_max_iter, pc_fixed_iters=pc_fixed_iters, grad_order=grad_order)

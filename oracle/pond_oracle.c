@@ -35,7 +35,10 @@
  *   - collision in the frame of the final moments, after projecting into it;
  *   - internal-energy split source: f -> f_eq inside the source, backward time
  *     difference of u against the frame before the step, central space differences;
- *   - non-translational split: E = sum g + sum |C|^2/2 f, g_eq = (U'/rho) f_eq.
+ *   - non-translational split: E = sum g + sum |C|^2/2 f, g_eq = (U'/rho) f_eq;
+ *   - walls (not in the paper): every position beyond a wall holds the equilibrium at the
+ *     wall's state (rho_w, u_w, T_w), so the wall lies half-way between the last node and
+ *     the first position beyond it; the internal-split gradients take the wall velocity.
  */
 #include <math.h>
 #include <stdint.h>
@@ -50,12 +53,13 @@ typedef struct {
     int32_t q1;            /* 4 -> D2Q16, 5 -> D2Q25 (Table I) */
     int32_t split;         /* 0 total, 1 internal, 2 non-translational energy split (Eq. Es) */
     int32_t interp_order;  /* 3 -> 4-point cubic Lagrange, 2 -> 3-point quadratic */
-    int32_t bc_x, bc_y;    /* 0 periodic, 1 outflow (index clamp, zero gradient) */
+    int32_t bc_x, bc_y;    /* 0 periodic, 1 outflow (index clamp, zero gradient), 2 wall */
     double gamma, mu;      /* adiabatic exponent (Eq. spec_heat), dynamic viscosity (Eq. kin_visc) */
     double pc_tol;
     int32_t pc_max_iter;
     int32_t pc_fixed_iters; /* > 0: exactly this many predictor-corrector iterations */
     int32_t grad_order;     /* Grad expansion order N: 3 or 4; 0 = the lattice's (3 on D2Q16, 4 on D2Q25) */
+    double wall[4][4];      /* walls x-low, x-high, y-low, y-high: (u_x, u_y, T, rho) of each */
 } or_config;
 
 static int grad_order_of(const or_config *cfg)
@@ -356,9 +360,18 @@ static int bc_map(int j, int n, int bc)
         int r = j % n;
         return r < 0 ? r + n : r;
     }
-    if (j < 0) return 0;        /* outflow: zero-gradient copy of the edge node */
+    if (j < 0) return 0;        /* outflow: zero-gradient copy of the edge node; wall: edge node */
     if (j > n - 1) return n - 1;
     return j;
+}
+
+/* Which wall (0 x-low, 1 x-high, 2 y-low, 3 y-high) a position lies beyond, or -1.  A position
+ * beyond both a y wall and an x wall belongs to the y wall. */
+static int wall_of(const or_config *cfg, int gx, int gy)
+{
+    if (cfg->bc_y == 2 && (gy < 0 || gy > cfg->ny - 1)) return gy < 0 ? 2 : 3;
+    if (cfg->bc_x == 2 && (gx < 0 || gx > cfg->nx - 1)) return gx < 0 ? 0 : 1;
+    return -1;
 }
 
 /* Lagrange weights of a p-point stencil around the departure coordinate xd; returns the
@@ -407,19 +420,37 @@ static void memo_clear(or_memo *M)
     for (int k = 0; k < OR_MEMO; ++k) M->key[k] = -1;
 }
 
-/* Grad coefficients of source node (sx, sy) in the target frame, memoised per target frame. */
-static void source_coefficients(const or_src *S, or_memo *M, int sx, int sy, or_frame dst,
+/* Grad coefficients, in the target frame, of the populations at position (gx, gy): the node
+ * the boundaries map it to, or a wall's ghost equilibrium; memoised per target frame. */
+static void source_coefficients(const or_src *S, or_memo *M, int gx, int gy, or_frame dst,
                                 const or_tensors **Af, const or_tensors **Ag)
 {
-    int nx = S->cfg->nx;
-    size_t N = (size_t)nx * S->cfg->ny;
-    int64_t node = (int64_t)sy * nx + sx;
-    int slot = (int)(((sx & 1023) + 37 * (sy & 1023)) & (OR_MEMO - 1));
-    if (M->key[slot] != node) {
-        or_frame src = {S->fux[node], S->fuy[node], S->fT[node]};
-        grad_coefficients(S->L, S->f + node, (int)N, src, dst, &M->Af[slot]);
-        grad_coefficients(S->L, S->g + node, (int)N, src, dst, &M->Ag[slot]);
-        M->key[slot] = node;
+    const or_config *cfg = S->cfg;
+    int nx = cfg->nx;
+    size_t N = (size_t)nx * cfg->ny;
+    int sx = bc_map(gx, nx, cfg->bc_x), sy = bc_map(gy, cfg->ny, cfg->bc_y);
+    int wall = wall_of(cfg, gx, gy);
+    int64_t key = wall < 0 ? (int64_t)sy * nx + sx : -1 - (((int64_t)(gy + 4096) << 20) + (gx + 4096));
+    int slot = (int)(((gx & 1023) + 37 * (gy & 1023)) & (OR_MEMO - 1));
+    if (M->key[slot] != key) {
+        int64_t node = (int64_t)sy * nx + sx;
+        if (wall < 0) {
+            or_frame src = {S->fux[node], S->fuy[node], S->fT[node]};
+            grad_coefficients(S->L, S->f + node, (int)N, src, dst, &M->Af[slot]);
+            grad_coefficients(S->L, S->g + node, (int)N, src, dst, &M->Ag[slot]);
+        } else {
+            /* ghost: equilibrium at the wall state */
+            or_frame wf = {cfg->wall[wall][0], cfg->wall[wall][1], cfg->wall[wall][2]};
+            double rho_g = cfg->wall[wall][3];
+            double fg[OR_MAXQ], gg[OR_MAXQ];
+            for (int i = 0; i < S->L->Q; ++i) {
+                fg[i] = feq_pop(S->L, i, rho_g);
+                gg[i] = geq_pop(S->L, i, cfg->split, rho_g, wf, cv_of(cfg->gamma));
+            }
+            grad_coefficients(S->L, fg, 1, wf, dst, &M->Af[slot]);
+            grad_coefficients(S->L, gg, 1, wf, dst, &M->Ag[slot]);
+        }
+        M->key[slot] = key;
     }
     *Af = &M->Af[slot];
     *Ag = &M->Ag[slot];
@@ -440,11 +471,9 @@ static void stream_node(const or_src *S, or_memo *M, int x, int y, or_frame bar,
         int by = lagrange_stencil(yd, cfg->interp_order, wy);
         double fi = 0.0, gi = 0.0;
         for (int ky = 0; ky < p; ++ky) {
-            int sy = bc_map(by + ky, cfg->ny, cfg->bc_y);
             for (int kx = 0; kx < p; ++kx) {
-                int sx = bc_map(bx + kx, cfg->nx, cfg->bc_x);
                 const or_tensors *Af, *Ag;
-                source_coefficients(S, M, sx, sy, bar, &Af, &Ag);
+                source_coefficients(S, M, bx + kx, by + ky, bar, &Af, &Ag);
                 double W = wx[kx] * wy[ky];
                 fi += W * grad_population(L, Af, i, grad_order_of(cfg));
                 gi += W * grad_population(L, Ag, i, grad_order_of(cfg));
@@ -514,12 +543,22 @@ static void internal_source(const or_config *cfg, const or_lattice *L, double *g
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t n = (size_t)y * nx + x;
-            size_t xp = (size_t)y * nx + bc_map(x + 1, nx, cfg->bc_x);
-            size_t xm = (size_t)y * nx + bc_map(x - 1, nx, cfg->bc_x);
-            size_t yp = (size_t)bc_map(y + 1, ny, cfg->bc_y) * nx + x;
-            size_t ym = (size_t)bc_map(y - 1, ny, cfg->bc_y) * nx + x;
-            double dxux = 0.5 * (ux1[xp] - ux1[xm]), dyux = 0.5 * (ux1[yp] - ux1[ym]);
-            double dxuy = 0.5 * (uy1[xp] - uy1[xm]), dyuy = 0.5 * (uy1[yp] - uy1[ym]);
+            /* neighbour velocities: mapped nodes, or the wall's velocity beyond a wall */
+            const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
+            double vx[4], vy[4];
+            for (int k = 0; k < 4; ++k) {
+                int w = wall_of(cfg, nb[k][0], nb[k][1]);
+                if (w >= 0) {
+                    vx[k] = cfg->wall[w][0];
+                    vy[k] = cfg->wall[w][1];
+                } else {
+                    size_t m = (size_t)bc_map(nb[k][1], ny, cfg->bc_y) * nx + bc_map(nb[k][0], nx, cfg->bc_x);
+                    vx[k] = ux1[m];
+                    vy[k] = uy1[m];
+                }
+            }
+            double dxux = 0.5 * (vx[0] - vx[1]), dyux = 0.5 * (vx[2] - vx[3]);
+            double dxuy = 0.5 * (vy[0] - vy[1]), dyuy = 0.5 * (vy[2] - vy[3]);
             double dtux = ux1[n] - ux0[n], dtuy = uy1[n] - uy0[n];   /* delta_t = 1 */
             double sT = sqrt(T1[n]);
             for (int i = 0; i < L->Q; ++i) {

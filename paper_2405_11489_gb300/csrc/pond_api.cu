@@ -100,7 +100,15 @@ int check_config(const pond_config* c)
     if (c->grad_order != 0 && c->grad_order != (c->lattice == POND_D2Q25 ? 4 : 3)) return POND_EINVAL;
     if (c->precision < POND_FP64 || c->precision > POND_MIXED_BF16) return POND_EINVAL;
     if (c->interp_order != 2 && c->interp_order != 3) return POND_EINVAL;
-    if ((c->bc_x != 0 && c->bc_x != 1) || (c->bc_y != 0 && c->bc_y != 1)) return POND_EINVAL;
+    if (c->bc_x < 0 || c->bc_x > 2 || c->bc_y < 0 || c->bc_y > 2) return POND_EINVAL;
+    if (c->bc_y == POND_BC_WALL && c->ny == 1) return POND_EINVAL;   // quasi-1-D grids have no y walls
+    for (int w = 0; w < 4; ++w) {
+        const bool used = (w < 2 ? c->bc_x : c->bc_y) == POND_BC_WALL;
+        const double* st = c->wall[w];
+        if (used && !(st[2] > 0.0 && st[3] > 0.0 && std::isfinite(st[0]) && std::isfinite(st[1]) &&
+                      std::isfinite(st[2]) && std::isfinite(st[3])))
+            return POND_EINVAL;
+    }
     if (!(c->gamma > 1.0 && c->gamma <= 2.0)) return POND_EINVAL;   // U' >= 0 in 2-D needs gamma <= 2
     if (!(c->mu > 0.0) || !std::isfinite(c->mu)) return POND_EINVAL;
     if (!(c->pc_tol >= 0.0)) return POND_EINVAL;
@@ -148,6 +156,7 @@ AuxParams aux_params(pond_sim* s, int k)
     a.bc_y = s->cfg.bc_y;
     a.split = s->cfg.split;
     a.nord = grad_order(s->cfg);
+    std::memcpy(a.wall, s->cfg.wall, sizeof(a.wall));
     a.N = (long long)s->cfg.nx * s->cfg.ny;
     a.cv = 1.0 / (s->cfg.gamma - 1.0);
     a.mac = mac_ptr(s, k);
@@ -223,6 +232,7 @@ void fill_case(const pond_config& c, DevStatus* status, CaseDesc& d)
     d.pc_tol = c.pc_tol;
     d.cur = 0;
     d.status = status;
+    std::memcpy(d.wall, c.wall, sizeof(d.wall));
 }
 
 // Launch shape of the step kernel: the tile (tile_x * tile_y nodes per CTA; 0 = default,
@@ -1054,6 +1064,7 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     a.bc_y = cfg->bc_y;
     a.split = cfg->split;
     a.nord = grad_order(*cfg);
+    std::memcpy(a.wall, cfg->wall, sizeof(a.wall));
     a.N = N;
     a.cv = p.one.cv;
     a.status = st;

@@ -17,6 +17,7 @@ struct AuxParams {
     void* neq;          // [nneq(N)][N] storage type
     const double* mac_prev;  // internal source: frames before the step
     DevStatus* status;
+    double wall[4][4];       // wall states (u_x, u_y, T, rho) for boundary type 2
 };
 
 // Equilibrium state from rho, u, T (device arrays [N]): f_i = rho w_i, g_i = g_eq_i in the
@@ -169,17 +170,28 @@ __global__ void get_pops_kernel(AuxParams p, double* f, double* g, double* oux, 
 template <class S>
 __device__ __forceinline__ void internal_source_node(long long n, int nx, int ny, int bc_x, int bc_y,
                                                      long long N, int nord, const double* mac,
-                                                     const double* mac_prev, void* neq)
+                                                     const double* mac_prev, void* neq,
+                                                     const double (*wall)[4])
 {
     const int x = (int)(n % nx), y = (int)(n / nx);
     const double* ux1 = mac + N;
     const double* uy1 = mac + 2 * N;
-    long long xp = (long long)y * nx + bc_map(x + 1, nx, bc_x);
-    long long xm = (long long)y * nx + bc_map(x - 1, nx, bc_x);
-    long long yp = (long long)bc_map(y + 1, ny, bc_y) * nx + x;
-    long long ym = (long long)bc_map(y - 1, ny, bc_y) * nx + x;
-    double dxux = 0.5 * (ux1[xp] - ux1[xm]), dyux = 0.5 * (ux1[yp] - ux1[ym]);
-    double dxuy = 0.5 * (uy1[xp] - uy1[xm]), dyuy = 0.5 * (uy1[yp] - uy1[ym]);
+    // neighbour velocities: mapped nodes, or the wall's velocity beyond a wall
+    const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
+    double vx[4], vy[4];
+    for (int k = 0; k < 4; ++k) {
+        const int w = wall_of(bc_x, bc_y, nx, ny, nb[k][0], nb[k][1]);
+        if (w >= 0) {
+            vx[k] = wall[w][0];
+            vy[k] = wall[w][1];
+        } else {
+            const long long m = (long long)bc_map(nb[k][1], ny, bc_y) * nx + bc_map(nb[k][0], nx, bc_x);
+            vx[k] = ux1[m];
+            vy[k] = uy1[m];
+        }
+    }
+    double dxux = 0.5 * (vx[0] - vx[1]), dyux = 0.5 * (vx[2] - vx[3]);
+    double dxuy = 0.5 * (vy[0] - vy[1]), dyuy = 0.5 * (vy[2] - vy[3]);
     double rho = mac[n], ux = ux1[n], uy = uy1[n], T = mac[3 * N + n];
     double dtux = ux - mac_prev[N + n], dtuy = uy - mac_prev[2 * N + n];
     double Dux = dtux + ux * dxux + uy * dyux;
@@ -199,7 +211,7 @@ __global__ void internal_source_kernel(AuxParams p)
 {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    internal_source_node<S>(n, p.nx, p.ny, p.bc_x, p.bc_y, p.N, p.nord, p.mac, p.mac_prev, p.neq);
+    internal_source_node<S>(n, p.nx, p.ny, p.bc_x, p.bc_y, p.N, p.nord, p.mac, p.mac_prev, p.neq, p.wall);
 }
 
 // Batched form: block b works on nodes [256 (b - block_start[c]), ...) of case c (the last case
@@ -219,7 +231,8 @@ __global__ void internal_source_batch_kernel(const CaseDesc* cases, const int* b
     const long long n = (long long)(b - block_start[lo]) * blockDim.x + threadIdx.x;
     if (n >= c.N) return;
     const int in = c.cur ^ flip;          // the state before the step; the new one is in ^ 1
-    internal_source_node<S>(n, c.nx, c.ny, c.bc_x, c.bc_y, c.N, c.nord, c.mac[in ^ 1], c.mac[in], c.neq[in ^ 1]);
+    internal_source_node<S>(n, c.nx, c.ny, c.bc_x, c.bc_y, c.N, c.nord, c.mac[in ^ 1], c.mac[in], c.neq[in ^ 1],
+                            c.wall);
 }
 
 }  // namespace pond

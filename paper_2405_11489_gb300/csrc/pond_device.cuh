@@ -187,7 +187,9 @@ __device__ __forceinline__ int lagrange(R off, R* w)
     }
 }
 
-// Boundary maps: 0 periodic (index mod n), 1 outflow (clamp to the edge node).
+// Boundary maps: 0 periodic (index mod n), 1 outflow (clamp to the edge node); positions
+// beyond a wall (2) map to the edge node here and are replaced by the wall's ghost state by
+// the callers that stream from them.
 __device__ __forceinline__ int bc_map(int j, int n, int bc)
 {
     if (bc == 0) {

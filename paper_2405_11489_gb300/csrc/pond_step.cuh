@@ -49,9 +49,10 @@ struct CaseDesc {
     long long N;                // nx * ny
     double cv, inv_cv, mu, pc_tol;
     double* mac[2];             // [4][N]: rho, u_x, u_y, T
-    void* neq[2];               // [19][N] storage type S
+    void* neq[2];               // [nneq(N)][N] storage type S
     int cur;                    // buffer holding the state when flip = 0
     DevStatus* status;
+    double wall[4][4];          // walls x-low, x-high, y-low, y-high: (u_x, u_y, T, rho)
 };
 
 struct StepParams {
@@ -75,6 +76,7 @@ struct CaseRun {
     double* mac_out;
     void* neq_out;
     DevStatus* status;
+    double wall[4][4];
 };
 
 __device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r)
@@ -105,6 +107,19 @@ __device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r)
     r.mac_out = c->mac[in ^ 1];
     r.neq_out = c->neq[in ^ 1];
     r.status = c->status;
+    for (int w = 0; w < 4; ++w)
+        for (int k = 0; k < 4; ++k) r.wall[w][k] = c->wall[w][k];
+}
+
+// Walls (boundary type 2; the paper gives none): every position beyond a wall holds the
+// equilibrium at the wall's state (rho_w, u_w, T_w), so the wall lies half-way between the
+// last node and the first position beyond it.  Which wall (0 x-low, 1 x-high, 2 y-low,
+// 3 y-high) position (gx, gy) lies beyond, or -1; the y walls own the corners.
+__device__ __forceinline__ int wall_of(int bc_x, int bc_y, int nx, int ny, int gx, int gy)
+{
+    if (bc_y == 2 && (gy < 0 || gy > ny - 1)) return gy < 0 ? 2 : 3;
+    if (bc_x == 2 && (gx < 0 || gx > nx - 1)) return gx < 0 ? 0 : 1;
+    return -1;
 }
 
 // Tile reference state: the centre node's frame (FP64) and derived values in R.
@@ -202,20 +217,22 @@ __device__ __forceinline__ void add_g_eq_dev(int split, const BaseFrame<R>& bf, 
                                   PsR * (tx2(tx, pp) * tx0(ty, q) + tx0(tx, pp) * tx2(ty, q));
 }
 
-// Deviation of node nd's coefficients, moved into the reference frame, from the reference
-// node's equilibrium coefficients (f into Df, g into Dg; ncoef(N) values each).
+// Deviation of a source's coefficients, moved into the reference frame, from the reference
+// node's equilibrium coefficients (f into Df, g into Dg; ncoef(N) values each).  The source is
+// node nd (neq = its non-equilibrium planes) or, with neq = nullptr, the equilibrium at the
+// primitive state (rho, ux, uy, T).
 template <class S, class R, int N>
-__device__ __forceinline__ void source_dev(const CaseRun& p, const RefState<R>& rf, long long nd,
-                                           R* Df, R* Dg)
+__device__ __forceinline__ void source_dev_state(const CaseRun& p, const RefState<R>& rf, double rho,
+                                                 double ux, double uy, double T, const S* neq,
+                                                 long long nd, R* Df, R* Dg)
 {
     constexpr int NC = ncoef(N);
     const long long Nn = p.N;
-    const S* neq = reinterpret_cast<const S*>(p.neq_in);
     // the only FP64 operations: differences of the primitive variables from the reference
-    const R drho = R(p.mac_in[nd] - rf.rho);
-    const R dux = R(p.mac_in[Nn + nd] - rf.ux);
-    const R duy = R(p.mac_in[2 * Nn + nd] - rf.uy);
-    const R dT = R(p.mac_in[3 * Nn + nd] - rf.T);
+    const R drho = R(rho - rf.rho);
+    const R dux = R(ux - rf.ux);
+    const R duy = R(uy - rf.uy);
+    const R dT = R(T - rf.T);
     const R rhoS = rf.rhoR + drho, uxS = rf.uxR + dux, uyS = rf.uyR + duy, TS = rf.TR + dT;
     const R dx = dux * rf.isT, dy = duy * rf.isT;
     const R sig = dT * rf.invT;                       // T/T_r - 1
@@ -223,14 +240,19 @@ __device__ __forceinline__ void source_dev(const CaseRun& p, const RefState<R>& 
     const Tau<R, N> tx = make_tau_sig<R, N>(s, dx, sig);
     const Tau<R, N> ty = make_tau_sig<R, N>(s, dy, sig);
     // non-equilibrium parts, moved
-    R A[NC], B[NC];
-    A[0] = R(0);
+    if (neq) {
+        R A[NC], B[NC];
+        A[0] = R(0);
 #pragma unroll
-    for (int k = 1; k < NC; ++k) A[k] = sto_get<S, R>(neq + (long long)(k - 1) * Nn + nd);
+        for (int k = 1; k < NC; ++k) A[k] = sto_get<S, R>(neq + (long long)(k - 1) * Nn + nd);
 #pragma unroll
-    for (int k = 0; k < NC; ++k) B[k] = sto_get<S, R>(neq + (long long)(NC - 1 + k) * Nn + nd);
-    retarget<R, N>(tx, ty, A, Df);
-    retarget<R, N>(tx, ty, B, Dg);
+        for (int k = 0; k < NC; ++k) B[k] = sto_get<S, R>(neq + (long long)(NC - 1 + k) * Nn + nd);
+        retarget<R, N>(tx, ty, A, Df);
+        retarget<R, N>(tx, ty, B, Dg);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) { Df[k] = R(0); Dg[k] = R(0); }
+    }
     // f equilibrium rho tx_p0 ty_q0 minus K_f = rho_r at (0,0)
     Df[0] += drho;
 #pragma unroll
@@ -257,6 +279,30 @@ __device__ __forceinline__ void source_dev(const CaseRun& p, const RefState<R>& 
     }
     const BaseFrame<R> bf = {rf.PR, rf.isT, rf.invT};
     add_g_eq_dev<R, N>(p.split, bf, tx, ty, dx, dy, sig, ES, dE, PS, uxS, uyS, dP, dux, duy, TS, dT, Dg);
+}
+
+template <class S, class R, int N>
+__device__ __forceinline__ void source_dev(const CaseRun& p, const RefState<R>& rf, long long nd,
+                                           R* Df, R* Dg)
+{
+    const long long Nn = p.N;
+    source_dev_state<S, R, N>(p, rf, p.mac_in[nd], p.mac_in[Nn + nd], p.mac_in[2 * Nn + nd],
+                              p.mac_in[3 * Nn + nd], reinterpret_cast<const S*>(p.neq_in), nd, Df, Dg);
+}
+
+// The source at position (gx, gy): the node the boundary maps it to, or a wall's ghost.
+template <class S, class R, int N>
+__device__ __forceinline__ void source_at(const CaseRun& p, const RefState<R>& rf, int gx, int gy,
+                                          R* Df, R* Dg)
+{
+    const int w = wall_of(p.bc_x, p.bc_y, p.nx, p.ny, gx, gy);
+    if (w >= 0) {
+        source_dev_state<S, R, N>(p, rf, p.wall[w][3], p.wall[w][0], p.wall[w][1], p.wall[w][2],
+                                  static_cast<const S*>(nullptr), 0, Df, Dg);
+    } else {
+        const int sx = bc_map(gx, p.nx, p.bc_x), sy = bc_map(gy, p.ny, p.bc_y);
+        source_dev<S, R, N>(p, rf, (long long)sy * p.nx + sx, Df, Dg);
+    }
 }
 
 // Per-population lattice values, kept in shared memory so that the population loops can run
@@ -691,10 +737,8 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     // so each tap of one distribution is three vector loads.
     for (int i = tid; i < bn; i += TPB) {
         int lx = i % bw, ly = i / bw;
-        int sx = bc_map(ox + lx, p.nx, p.bc_x);
-        int sy = ONE_D ? 0 : bc_map(oy + ly, p.ny, p.bc_y);
         R D[2 * NC];
-        source_dev<S, R, NG>(p, rf, (long long)sy * p.nx + sx, D, D + NC);
+        source_at<S, R, NG>(p, rf, ox + lx, ONE_D ? 0 : oy + ly, D, D + NC);
         store_rec<R, NG>(sm + (size_t)i * REC, D, D + NC);
     }
     __syncthreads();
@@ -803,13 +847,11 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
 #pragma unroll 1
                                 for (int j = 0; j < P; ++j) {
                                     const R wyj = pick<R>(wy[b], j, P);
-                                    const int sy = bc_map(y + jy[b] + j, p.ny, p.bc_y);
 #pragma unroll 1
                                     for (int ii = 0; ii < P; ++ii) {
                                         const R wxi = pick<R>(wx, ii, P);
-                                        const int sx = bc_map(x + jx + ii, p.nx, p.bc_x);
                                         R D[2 * NC];
-                                        source_dev<S, R, NG>(p, rf, (long long)sy * p.nx + sx, D, D + NC);
+                                        source_at<S, R, NG>(p, rf, x + jx + ii, y + jy[b] + j, D, D + NC);
 #pragma unroll
                                         for (int e = 0; e < ND; ++e) {
                                             R Z[NG + 1];
@@ -874,9 +916,8 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
 #pragma unroll 1
                         for (int ii = 0; ii < P; ++ii) {
                             const R W = pick<R>(wx, ii, P);
-                            const int sx = bc_map(x + jx + ii, p.nx, p.bc_x);
                             R D[2 * NC];
-                            source_dev<S, R, NG>(p, rf, (long long)sx, D, D + NC);
+                            source_at<S, R, NG>(p, rf, x + jx + ii, 0, D, D + NC);
 #pragma unroll
                             for (int m = 0; m < 2 * NC; ++m) Ri[m] += W * D[m];
                         }

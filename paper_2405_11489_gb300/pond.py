@@ -25,12 +25,12 @@ POND_OK, POND_EINVAL, POND_ENOMEM, POND_ECUDA, POND_ENONPHYSICAL, POND_ENOCONV =
 POND_D2Q16, POND_D2Q25 = 16, 25
 POND_SPLIT_TOTAL, POND_SPLIT_INTERNAL, POND_SPLIT_NT = 0, 1, 2
 POND_FP64, POND_MIXED_FP32, POND_MIXED_FP16, POND_MIXED_BF16 = 0, 1, 2, 3
-POND_BC_PERIODIC, POND_BC_OUTFLOW = 0, 1
+POND_BC_PERIODIC, POND_BC_OUTFLOW, POND_BC_WALL = 0, 1, 2
 
 PRECISIONS = {"fp64": POND_FP64, "fp32": POND_MIXED_FP32, "fp16": POND_MIXED_FP16,
               "bf16": POND_MIXED_BF16}
 SPLITS = {"total": POND_SPLIT_TOTAL, "internal": POND_SPLIT_INTERNAL, "nt": POND_SPLIT_NT}
-BCS = {"periodic": POND_BC_PERIODIC, "outflow": POND_BC_OUTFLOW}
+BCS = {"periodic": POND_BC_PERIODIC, "outflow": POND_BC_OUTFLOW, "wall": POND_BC_WALL}
 
 # Symbols the header declares (checked by the ABI test).
 EXPORTS = ("pond_config_default", "pond_workspace_bytes", "pond_create", "pond_set_state",
@@ -50,7 +50,7 @@ class pond_config(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("pc_tol", ctypes.c_double),
                 ("pc_max_iter", ctypes.c_int32), ("pc_fixed_iters", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("halo", ctypes.c_int32),
-                ("grad_order", ctypes.c_int32)]
+                ("grad_order", ctypes.c_int32), ("wall", (ctypes.c_double * 4) * 4)]
 
 
 class pond_stats(ctypes.Structure):
@@ -290,6 +290,7 @@ class Config:
     tile_y: int = 0
     halo: int = 0
     grad_order: int = 0       # 0: the lattice's (3 on D2Q16, 4 on D2Q25)
+    walls: tuple | None = None  # four (u_x, u_y, T, rho): x-low, x-high, y-low, y-high
 
     def to_c(self) -> pond_config:
         tol = self.pc_tol if self.pc_tol is not None else (1e-12 if self.precision == "fp64" else 1e-6)
@@ -298,7 +299,15 @@ class Config:
                            bc_x=BCS[self.bc_x], bc_y=BCS[self.bc_y], gamma=self.gamma, mu=self.mu,
                            pc_tol=tol, pc_max_iter=self.pc_max_iter,
                            pc_fixed_iters=self.pc_fixed_iters, tile_x=self.tile_x,
-                           tile_y=self.tile_y, halo=self.halo, grad_order=self.grad_order)
+                           tile_y=self.tile_y, halo=self.halo, grad_order=self.grad_order,
+                           wall=self._walls())
+
+    def _walls(self):
+        w = ((ctypes.c_double * 4) * 4)()
+        for k, state in enumerate(self.walls or [(0.0, 0.0, 1.0, 1.0)] * 4):
+            for j in range(4):
+                w[k][j] = float(state[j])
+        return w
 
     @property
     def Q(self) -> int:

@@ -51,14 +51,18 @@ def random_state(orc, ocfg, seed, amp=0.05, ux0=0.3, uy0=-0.2, T0=0.8, neq=0.01)
     return st
 
 
+# wall states (u_x, u_y, T, rho) for x-low, x-high, y-low, y-high, used where a bc is "wall"
+WALLS = [(0.2, 0.05, 0.75, 1.0), (0.45, -0.1, 0.9, 1.1), (0.3, 0.0, 0.85, 0.95), (-0.2, 0.0, 0.7, 1.05)]
+
+
 def make_pair(pond, orc, nx, ny, lattice=16, split="total", order=3, bc=("periodic", "periodic"),
               K=2, tol=1e-12, precision="fp64", halo=0, gamma=1.4, mu=0.02, maxit=20):
     ocfg = orc.make_config(nx, ny, lattice=lattice, split=split, interp_order=order, bc_x=bc[0],
                            bc_y=bc[1], gamma=gamma, mu=mu, pc_tol=tol, pc_max_iter=maxit,
-                           pc_fixed_iters=K)
+                           pc_fixed_iters=K, walls=WALLS)
     gcfg = pond.Config(nx=nx, ny=ny, lattice=lattice, split=split, precision=precision,
                        interp_order=order, bc_x=bc[0], bc_y=bc[1], gamma=gamma, mu=mu, pc_tol=tol,
-                       pc_max_iter=maxit, pc_fixed_iters=K, halo=halo)
+                       pc_max_iter=maxit, pc_fixed_iters=K, halo=halo, walls=tuple(WALLS))
     return ocfg, pond.Simulation(gcfg)
 
 
@@ -102,6 +106,9 @@ CASES = [
     (27, 8, 25, "nt", 3, ("periodic", "periodic")),
     (30, 7, 16, "nt", 3, ("outflow", "periodic")),
     (25, 9, 25, "nt", 2, ("outflow", "outflow")),
+    (28, 10, 16, "total", 3, ("periodic", "wall")),
+    (24, 11, 25, "nt", 3, ("wall", "wall")),
+    (30, 8, 16, "internal", 3, ("wall", "outflow")),
 ]
 
 
@@ -236,3 +243,24 @@ def test_checkpoint_resume_is_bit_identical(pond, orc, precision, lattice, split
             assert np.array_equal(x, y)
         d.close()
     a.close()
+
+
+def test_couette_flow_on_the_gpu(pond):
+    """Thermal Couette flow (Sec. III.B) between walls in both precisions on 32 cells: the
+    steady temperature follows the analytic profile, the velocity is linear."""
+    import math
+    gamma, cp, T0, T1, Ec, mu, ny = 1.4, 3.5, 1.0, 1.005, 8.0, 0.1, 32
+    u0 = math.sqrt(Ec * cp * (T1 - T0))
+    walls = ((0, 0, 1, 1), (0, 0, 1, 1), (0.0, 0.0, T0, 1.0), (u0, 0.0, T1, 1.0 / T1))
+    eta = (np.arange(ny) + 0.5) / ny
+    exact = eta + 0.5 * Ec * eta * (1.0 - eta)
+    for precision in ("fp64", "fp32"):
+        sim = pond.Simulation(pond.Config(nx=1, ny=ny, precision=precision, bc_y="wall", walls=walls,
+                                          gamma=gamma, mu=mu))
+        sim.set_state(np.ones((ny, 1)), (u0 * eta)[:, None], np.zeros((ny, 1)), (T0 + (T1 - T0) * eta)[:, None])
+        sim.step(int(2.5 * ny * ny / mu))
+        rho, ux, uy, T = sim.moments()
+        theta = (T[:, 0] - T0) / (T1 - T0)
+        assert np.max(np.abs(theta - exact)) < 0.05, precision
+        assert np.max(np.abs(ux[:, 0] / u0 - eta)) < 0.02, precision
+        sim.close()
