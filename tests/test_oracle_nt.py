@@ -159,3 +159,27 @@ def test_d2q25_needs_order_4_at_high_mach(orc):
         out[N] = (status, np.nanmax(np.abs(T - 1.0)), r.iters.max())
     assert out[3][0] == -5 or out[3][1] > 1e-2           # N = 3: non-convergence / growth
     assert out[4][0] == 0 and out[4][1] < 1.01e-3 and out[4][2] <= 2
+
+
+@pytest.mark.parametrize("split,lattice,gamma", [("total", 16, 1.4), ("total", 16, 1.8),
+                                                 ("nt", 16, 1.4), ("nt", 25, 1.8)])
+def test_sound_attenuation_gives_the_bulk_viscosity(orc, split, lattice, gamma):
+    """A standing isentropic sound wave decays at Gamma = (k^2/2)[(2 - 2/D) nu + eta/rho +
+    (gamma - 1) alpha] (linearised Navier-Stokes-Fourier), which with the bulk viscosity of
+    Sec. II, eta = (2/D - r/c_v) mu, D = 2 and Pr = 1 (alpha = nu) is nu k^2 for every gamma.
+    Without the bulk viscosity it would be gamma nu k^2 / 2 (0.7 or 0.9 of it)."""
+    n, mu, A = 64, 0.05, 1e-4
+    cfg = orc.make_config(n, 1, lattice=lattice, split=split, gamma=gamma, mu=mu, pc_tol=1e-13)
+    x = np.arange(n)[None, :]
+    k = 2 * math.pi / n
+    rho = 1.0 + A * np.sin(k * x)
+    st = orc.init_state(cfg, rho, np.zeros((1, n)), np.zeros((1, n)), rho ** (gamma - 1.0))
+    ts, es = [], []
+    for s in range(480):                 # about nine periods of the wave
+        st = orc.step(cfg, st).state
+        if s % 4 == 3:
+            r, ux, uy, T, E = orc.moments(cfg, st)
+            ts.append(s + 1)
+            es.append(np.mean(r * ux * ux + gamma * (r - 1.0) ** 2))   # acoustic energy
+    rate = -np.polyfit(ts, np.log(es), 1)[0] / 2.0
+    assert abs(rate / (mu * k * k) - 1.0) < 0.02
