@@ -123,7 +123,7 @@ typedef struct {
 
 static double kron(int a, int b) { return a == b ? 1.0 : 0.0; }
 
-static void hermite_tensors(double xi_x, double xi_y, or_tensors *H)
+static void hermite_tensors(double xi_x, double xi_y, int order, or_tensors *H)
 {
     double xi[2] = {xi_x, xi_y};
     H->h0 = 1.0;
@@ -135,6 +135,7 @@ static void hermite_tensors(double xi_x, double xi_y, or_tensors *H)
             for (int g = 0; g < 2; ++g)
                 H->h3[a][b][g] = xi[a] * xi[b] * xi[g]
                                - xi[a] * kron(b, g) - xi[b] * kron(a, g) - xi[g] * kron(a, b);
+    if (order < 4) return;                 /* rank 4 only for the order-4 transformation */
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             for (int g = 0; g < 2; ++g)
@@ -153,7 +154,7 @@ static void hermite_tensors(double xi_x, double xi_y, or_tensors *H)
 /* ---------------------------------------------------------------------------------- */
 typedef struct { double ux, uy, T; } or_frame;
 
-static void grad_coefficients(const or_lattice *L, const double *pops, int stride,
+static void grad_coefficients(const or_lattice *L, const double *pops, int stride, int order,
                               or_frame src, or_frame dst, or_tensors *A)
 {
     memset(A, 0, sizeof(*A));
@@ -164,7 +165,7 @@ static void grad_coefficients(const or_lattice *L, const double *pops, int strid
         double xix = (Cx - dst.ux) / sTd;
         double xiy = (Cy - dst.uy) / sTd;
         or_tensors H;
-        hermite_tensors(xix, xiy, &H);
+        hermite_tensors(xix, xiy, order, &H);
         double fj = pops[(size_t)j * stride];
         A->h0 += fj * H.h0;
         for (int a = 0; a < 2; ++a) A->h1[a] += fj * H.h1[a];
@@ -173,10 +174,11 @@ static void grad_coefficients(const or_lattice *L, const double *pops, int strid
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
                 for (int g = 0; g < 2; ++g) A->h3[a][b][g] += fj * H.h3[a][b][g];
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b)
-                for (int g = 0; g < 2; ++g)
-                    for (int d = 0; d < 2; ++d) A->h4[a][b][g][d] += fj * H.h4[a][b][g][d];
+        if (order >= 4)
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    for (int g = 0; g < 2; ++g)
+                        for (int d = 0; d < 2; ++d) A->h4[a][b][g][d] += fj * H.h4[a][b][g][d];
     }
 }
 
@@ -184,7 +186,7 @@ static void grad_coefficients(const or_lattice *L, const double *pops, int strid
 static double grad_population(const or_lattice *L, const or_tensors *A, int i, int order)
 {
     or_tensors H;
-    hermite_tensors(L->cx[i], L->cy[i], &H);
+    hermite_tensors(L->cx[i], L->cy[i], order, &H);
     double s0 = A->h0 * H.h0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
     for (int a = 0; a < 2; ++a) s1 += A->h1[a] * H.h1[a];
     for (int a = 0; a < 2; ++a)
@@ -208,7 +210,7 @@ void or_grad_transform(int q1, const double *pops_src, double sux, double suy, d
     make_lattice(q1, &L);
     or_frame s = {sux, suy, sT}, d = {dux, duy, dT};
     or_tensors A;
-    grad_coefficients(&L, pops_src, 1, s, d, &A);
+    grad_coefficients(&L, pops_src, 1, 3, s, d, &A);
     for (int i = 0; i < L.Q; ++i) pops_dst[i] = grad_population(&L, &A, i, 3);
 }
 
@@ -220,7 +222,7 @@ void or_grad_transform_n(int q1, int order, const double *pops_src, double sux, 
     make_lattice(q1, &L);
     or_frame s = {sux, suy, sT}, d = {dux, duy, dT};
     or_tensors A;
-    grad_coefficients(&L, pops_src, 1, s, d, &A);
+    grad_coefficients(&L, pops_src, 1, order, s, d, &A);
     for (int i = 0; i < L.Q; ++i) pops_dst[i] = grad_population(&L, &A, i, order);
 }
 
@@ -233,7 +235,7 @@ void or_grad_coefficients(int q1, const double *pops_src, double sux, double suy
     make_lattice(q1, &L);
     or_frame s = {sux, suy, sT}, d = {dux, duy, dT};
     or_tensors A;
-    grad_coefficients(&L, pops_src, 1, s, d, &A);
+    grad_coefficients(&L, pops_src, 1, 3, s, d, &A);
     int k = 0;
     out15[k++] = A.h0;
     for (int a = 0; a < 2; ++a) out15[k++] = A.h1[a];
@@ -436,8 +438,8 @@ static void source_coefficients(const or_src *S, or_memo *M, int gx, int gy, or_
         int64_t node = (int64_t)sy * nx + sx;
         if (wall < 0) {
             or_frame src = {S->fux[node], S->fuy[node], S->fT[node]};
-            grad_coefficients(S->L, S->f + node, (int)N, src, dst, &M->Af[slot]);
-            grad_coefficients(S->L, S->g + node, (int)N, src, dst, &M->Ag[slot]);
+            grad_coefficients(S->L, S->f + node, (int)N, grad_order_of(cfg), src, dst, &M->Af[slot]);
+            grad_coefficients(S->L, S->g + node, (int)N, grad_order_of(cfg), src, dst, &M->Ag[slot]);
         } else {
             /* ghost: equilibrium at the wall state */
             or_frame wf = {cfg->wall[wall][0], cfg->wall[wall][1], cfg->wall[wall][2]};
@@ -447,8 +449,8 @@ static void source_coefficients(const or_src *S, or_memo *M, int gx, int gy, or_
                 fg[i] = feq_pop(S->L, i, rho_g);
                 gg[i] = geq_pop(S->L, i, cfg->split, rho_g, wf, cv_of(cfg->gamma));
             }
-            grad_coefficients(S->L, fg, 1, wf, dst, &M->Af[slot]);
-            grad_coefficients(S->L, gg, 1, wf, dst, &M->Ag[slot]);
+            grad_coefficients(S->L, fg, 1, grad_order_of(cfg), wf, dst, &M->Af[slot]);
+            grad_coefficients(S->L, gg, 1, grad_order_of(cfg), wf, dst, &M->Ag[slot]);
         }
         M->key[slot] = key;
     }
@@ -509,8 +511,8 @@ static void collide_node(const or_lattice *L, const or_config *cfg, const double
     double cv = cv_of(cfg->gamma);
     or_frame star = {m.ux, m.uy, m.T};
     or_tensors Af, Ag;
-    grad_coefficients(L, P, 1, bar, star, &Af);   /* project the streamed populations into lambda* */
-    grad_coefficients(L, G, 1, bar, star, &Ag);
+    grad_coefficients(L, P, 1, grad_order_of(cfg), bar, star, &Af);   /* project the streamed populations into lambda* */
+    grad_coefficients(L, G, 1, grad_order_of(cfg), bar, star, &Ag);
     double rho = m.rho;
     double tau = cfg->mu / (rho * m.T);             /* Eq. kin_visc: tau = mu / p, p = rho T */
     double omega = 1.0 / (tau + 0.5);
