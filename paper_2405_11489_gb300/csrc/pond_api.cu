@@ -269,12 +269,14 @@ int make_shape(const pond_config& c, int tile_x, int tile_y, int halo, Shape* sh
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return cuda_status(e);
-    if (sh->smem + 1024 > (size_t)smem_optin) return POND_EINVAL;   // box too large: lower halo or tile
     // The limit is an attribute of the kernel, shared by every simulation of the process: set
-    // it to the device's largest (less room for the static part), never to this shape's need,
+    // it to the device's largest (less the kernel's static part), never to this shape's need,
     // so that a smaller shape set later cannot shrink it under a larger one.
-    e = kSmem[c.precision][q1 == 5][sh->one_d](c.interp_order, (size_t)smem_optin - 1024);
-    return cuda_status(e);
+    size_t static_bytes = 0;
+    e = kSmem[c.precision][q1 == 5][sh->one_d](c.interp_order, (size_t)smem_optin, &static_bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (sh->smem + static_bytes > (size_t)smem_optin) return POND_EINVAL;   // box too large: lower halo or tile
+    return POND_OK;
 }
 
 int apply_shape(pond_sim* s, int tile_x, int tile_y, int halo)

@@ -79,10 +79,15 @@ struct CaseRun {
     double wall[4][4];
 };
 
-__device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r)
+// Resolves the block's case (warp 0 calls it).  In a batched launch every lane runs the same
+// binary search over the tile prefix, the warp copies the case record into shared memory in
+// one round of 8-byte loads, and lane 0 fills the block's CaseRun from that copy.
+static_assert(sizeof(CaseDesc) % 8 == 0, "CaseDesc is copied in 8-byte words");
+
+__device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r, CaseDesc& sdesc, int lane)
 {
     const CaseDesc* c = &p.one;
-    int tile = 0;
+    int tile_x = blockIdx.x, tile_y = blockIdx.y;
     if (p.ncase > 0) {
         int lo = 0, hi = p.ncase - 1;             // last case with tile_start <= blockIdx.x
         const int b = (int)blockIdx.x;
@@ -90,14 +95,18 @@ __device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r)
             const int mid = (lo + hi + 1) >> 1;
             if (p.tile_start[mid] <= b) lo = mid; else hi = mid - 1;
         }
-        c = p.cases + lo;
-        tile = b - p.tile_start[lo];
-        r.tile_x = tile % c->tiles_x;
-        r.tile_y = tile / c->tiles_x;
-    } else {
-        r.tile_x = blockIdx.x;
-        r.tile_y = blockIdx.y;
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p.cases + lo);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sdesc);
+        for (int k = lane; k < (int)(sizeof(CaseDesc) / 8); k += 32) dst[k] = src[k];
+        __syncwarp();
+        c = &sdesc;
+        const int tile = b - p.tile_start[lo];
+        tile_x = tile % c->tiles_x;
+        tile_y = tile / c->tiles_x;
     }
+    if (lane != 0) return;
+    r.tile_x = tile_x;
+    r.tile_y = tile_y;
     r.nx = c->nx; r.ny = c->ny; r.bc_x = c->bc_x; r.bc_y = c->bc_y; r.split = c->split;
     r.pc_max_iter = c->pc_max_iter; r.pc_fixed = c->pc_fixed;
     r.N = c->N; r.cv = c->cv; r.inv_cv = c->inv_cv; r.mu = c->mu; r.pc_tol = c->pc_tol;
@@ -704,7 +713,8 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     __shared__ CaseRun scase;
     const int TX = blockDim.x, TY = blockDim.y;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    if (tid == 0) resolve_case(pp, scase);
+    __shared__ CaseDesc sdesc;
+    if (tid < 32) resolve_case(pp, scase, sdesc, tid);
     __syncthreads();
     const CaseRun& p = scase;
     const int x = p.tile_x * TX + threadIdx.x;

@@ -17,13 +17,25 @@ cudaError_t POND_CAT(step, POND_TAG)(const StepParams& p, int order, const Launc
     return cudaGetLastError();
 }
 
-cudaError_t POND_CAT(smem, POND_TAG)(int order, size_t bytes)
+template <class K>
+static cudaError_t set_smem_limit(K kernel, size_t optin, size_t* static_bytes)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    *static_bytes = fa.sharedSizeBytes;
+    if (fa.sharedSizeBytes >= optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(optin - fa.sharedSizeBytes));
+}
+
+cudaError_t POND_CAT(smem, POND_TAG)(int order, size_t optin, size_t* static_bytes)
 {
     if (order == 3)
-        return cudaFuncSetAttribute(step_kernel<POND_S, POND_R, POND_Q1, 4, POND_ONED, kStepThreads>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return cudaFuncSetAttribute(step_kernel<POND_S, POND_R, POND_Q1, 3, POND_ONED, kStepThreads>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        return set_smem_limit(step_kernel<POND_S, POND_R, POND_Q1, 4, POND_ONED, kStepThreads>, optin,
+                              static_bytes);
+    return set_smem_limit(step_kernel<POND_S, POND_R, POND_Q1, 3, POND_ONED, kStepThreads>, optin,
+                          static_bytes);
 }
 
 }  // namespace pond
