@@ -318,7 +318,8 @@ def decay_physics(torch, pond, device, steps=2000):
     """The 256^2 decay configuration over `steps` steps in mixed FP32 and in FP64: decay of the
     shear wave's Fourier mode against exp(-nu k^2 t), nu = mu / rho (Sec. III.B), of the
     thermal pulse's peak against 2-D diffusion sigma0^2 / (sigma0^2 + 2 alpha t) with
-    alpha = nu (Pr = 1), the drift of total mass, momentum and energy, and the per-field
+    alpha = nu (Pr = 1) (in the combined grids and, without the shear wave, in pulse-only
+    grids on the same backgrounds), the drift of total mass, momentum and energy, and the per-field
     relative L1 difference of the FP32 result from the FP64 one."""
     k = 2 * math.pi / NX
     shear_expected = math.exp(-MU * k * k * steps)
@@ -351,19 +352,31 @@ def decay_physics(torch, pond, device, steps=2000):
     finals = {}
     for prec in ("fp32", "fp64"):
         stream = torch.cuda.current_stream(device)
-        sims, batch = make_sims(pond, prec, device, stream)
-        f0 = [s.moments() for s in sims]
+        sims, _ = make_sims(pond, prec, device, stream)
+        # the pulse alone on the same backgrounds: its decay without the shear wave's heating
+        solo = []
+        for ma in MACHS:
+            c = W.thermal_pulse(n=NX, amp=1e-3, width=sigma0, gamma=GAMMA, mu=MU, ma=ma)
+            s = pond.Simulation(pond.Config(nx=NX, ny=NY, precision=prec, gamma=GAMMA, mu=MU),
+                                device=device, stream=stream)
+            s.set_state(c.rho, c.ux, c.uy, c.T)
+            solo.append(s)
+        batch = pond.Batch(sims + solo, stream=stream)
+        f0 = [s.moments() for s in sims + solo]
         batch.step(steps)
         stream.synchronize()
-        f1 = [s.moments() for s in sims]
-        res = [measure(a, b) for a, b in zip(f0, f1)]
+        f1 = [s.moments() for s in sims + solo]
+        n = len(sims)
+        res = [measure(a, b) for a, b in zip(f0[:n], f1[:n])]
+        res_solo = [measure(a, b) for a, b in zip(f0[n:], f1[n:])]
         out[prec] = {"shear_ratio_over_expected": [r[0] / shear_expected for r in res],
                      "pulse_ratio_over_expected": [r[1] / pulse_expected for r in res],
+                     "pulse_only_ratio_over_expected": [r[1] / pulse_expected for r in res_solo],
                      "max_rel_drift_mass_momx_momy_energy": np.max([r[2] for r in res], axis=0).tolist(),
-                     "statuses": sorted({pond.strerror(s.stats()[0]) for s in sims})}
-        finals[prec] = f1
+                     "statuses": sorted({pond.strerror(s.stats()[0]) for s in sims + solo})}
+        finals[prec] = f1[:n]
         batch.close()
-        for s in sims:
+        for s in sims + solo:
             s.close()
     l1 = {}
     for name, idx in (("rho", 0), ("ux", 1), ("uy", 2), ("T", 3)):
@@ -376,22 +389,28 @@ def decay_physics(torch, pond, device, steps=2000):
 
 
 def e2e_rate(torch, pond, device, steps, warmup):
-    """MLUPS through the public C-ABI with host buffers: every step uploads the step's input
-    fields from pinned host memory (pond_set_state), advances one time step (pond_step) and
-    reads the resulting fields back (pond_get_moments), all inside the timed region."""
-    s = pond.Simulation(pond.Config(nx=NX, ny=NY, precision="fp32", gamma=GAMMA, mu=MU), device=device)
-    fields = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case_fields(1.0)]
-    outs = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in range(4)]
-    host_in = [a.numpy() for a in fields]
+    """MLUPS of the benchmark's workload (the four grids, one batched launch per time step)
+    through the public C-ABI with host buffers: every step uploads each grid's input fields
+    from pinned host memory (pond_set_state), advances the batch one time step
+    (pond_batch_step) and reads every grid's resulting fields back (pond_get_moments), all
+    inside the timed region."""
+    stream = torch.cuda.Stream(device)
+    sims = [pond.Simulation(pond.Config(nx=NX, ny=NY, precision="fp32", gamma=GAMMA, mu=MU),
+                            device=device, stream=stream) for _ in MACHS]
+    host_in = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case_fields(ma)]
+               for ma in MACHS]
+    outs = [[torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in range(4)]
+            for _ in MACHS]
     lib = pond.load_library()
+    batch = pond.Batch(sims, stream=stream)
 
     def one():
-        rc = lib.pond_set_state(s.handle, *[a.ctypes.data for a in host_in], 0)
-        assert rc == 0
-        assert lib.pond_step(s.handle, 1) == 0
-        rc = lib.pond_get_moments(s.handle, *[o.data_ptr() for o in outs], 0)
-        assert rc in (0, pond.POND_ENOCONV)
-        return outs[0][0, 0].item()
+        for s, fin in zip(sims, host_in):
+            assert lib.pond_set_state(s.handle, *[a.data_ptr() for a in fin], 0) == 0
+        assert lib.pond_batch_step(batch.handle, 1) == 0
+        for s, fout in zip(sims, outs):
+            assert lib.pond_get_moments(s.handle, *[o.data_ptr() for o in fout], 0) in (0, pond.POND_ENOCONV)
+        return outs[0][0][0, 0].item()
 
     for _ in range(warmup):
         one()
@@ -400,12 +419,14 @@ def e2e_rate(torch, pond, device, steps, warmup):
     for _ in range(steps):
         one()
     t = time.perf_counter() - t0
-    s.close()
-    nbytes_in = 4 * NX * NY * 8
-    nbytes_out = 4 * NX * NY * 8
-    return {"value": NX * NY * steps / t / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nbytes_in,
-            "d2h_bytes_per_step": nbytes_out,
-            "note": "per step: pond_set_state(host) + pond_step(1) + pond_get_moments(host), Ma = 1 grid"}
+    batch.close()
+    for s in sims:
+        s.close()
+    nbytes = len(MACHS) * 4 * NX * NY * 8          # four FP64 fields per grid, each direction
+    return {"value": len(MACHS) * NX * NY * steps / t / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "note": "per step: pond_set_state(host) x 4 grids + pond_batch_step(1) + "
+                    "pond_get_moments(host) x 4 grids; host wall clock"}
 
 
 def cpu_baseline(target_seconds=10.0):
