@@ -58,24 +58,39 @@ class Config(ctypes.Structure):
         ("pc_max_iter", ctypes.c_int32), ("pc_fixed_iters", ctypes.c_int32),
         ("grad_order", ctypes.c_int32),
         ("wall", (ctypes.c_double * 4) * 4),
+        ("profile", ctypes.c_void_p * 4),
     ]
 
 
 def make_config(nx, ny, lattice=16, split="total", interp_order=3, bc_x="periodic",
                 bc_y="periodic", gamma=1.4, mu=1e-4, pc_tol=1e-12, pc_max_iter=20,
-                pc_fixed_iters=0, grad_order=0, walls=None) -> Config:
+                pc_fixed_iters=0, grad_order=0, walls=None, profiles=None) -> Config:
     """split: "total", "internal" or "nt" (non-translational); grad_order: N = 3 or 4
-    (0: the lattice's, 3 on D2Q16 and 4 on D2Q25); bc "wall" with walls = four (u_x, u_y, T, rho)
-    for the x-low, x-high, y-low and y-high walls."""
-    bc = {"periodic": 0, "outflow": 1, "wall": 2}
+    (0: the lattice's, 3 on D2Q16 and 4 on D2Q25).  Boundaries per axis: "periodic",
+    "outflow", "wall" (both sides prescribed) or "inflow" (low side prescribed, high side
+    outflow).  walls = four uniform states (u_x, u_y, T, rho) of the sides x-low, x-high,
+    y-low, y-high; profiles = four arrays [n][4] of per-position states along the sides
+    (n = ny for the x sides, nx for the y sides) or None each."""
+    bc = {"periodic": 0, "outflow": 1, "wall": 2, "inflow": 3}
     w = ((ctypes.c_double * 4) * 4)()
     for k, state in enumerate(walls or [(0.0, 0.0, 1.0, 1.0)] * 4):
         for j in range(4):
             w[k][j] = float(state[j])
-    return Config(nx=nx, ny=ny, q1={16: 4, 25: 5}[lattice], wall=w,
-                  split={"total": 0, "internal": 1, "nt": 2}[split], interp_order=interp_order,
-                  bc_x=bc[bc_x], bc_y=bc[bc_y], gamma=gamma, mu=mu, pc_tol=pc_tol,
-                  pc_max_iter=pc_max_iter, pc_fixed_iters=pc_fixed_iters, grad_order=grad_order)
+    prof = (ctypes.c_void_p * 4)()
+    keep = []
+    for k, arr in enumerate(profiles or [None] * 4):
+        if arr is not None:
+            arr = np.ascontiguousarray(arr, dtype=np.float64)
+            if arr.shape != ((ny if k < 2 else nx), 4):
+                raise ValueError("profile %d: shape %s" % (k, arr.shape))
+            keep.append(arr)
+            prof[k] = arr.ctypes.data
+    cfg = Config(nx=nx, ny=ny, q1={16: 4, 25: 5}[lattice], wall=w, profile=prof,
+                 split={"total": 0, "internal": 1, "nt": 2}[split], interp_order=interp_order,
+                 bc_x=bc[bc_x], bc_y=bc[bc_y], gamma=gamma, mu=mu, pc_tol=pc_tol,
+                 pc_max_iter=pc_max_iter, pc_fixed_iters=pc_fixed_iters, grad_order=grad_order)
+    cfg._profiles = keep          # the C side reads the arrays through the pointers
+    return cfg
 
 
 _D = ctypes.POINTER(ctypes.c_double)

@@ -38,7 +38,13 @@
  *   - non-translational split: E = sum g + sum |C|^2/2 f, g_eq = (U'/rho) f_eq;
  *   - walls (not in the paper): every position beyond a wall holds the equilibrium at the
  *     wall's state (rho_w, u_w, T_w), so the wall lies half-way between the last node and
- *     the first position beyond it; the internal-split gradients take the wall velocity.
+ *     the first position beyond it; the internal-split gradients take the wall velocity;
+ *   - inflow (the prescribed conditions of the jet, Sec. III.C; the paper gives no
+ *     discretisation): the low side of the axis is a prescribed side treated like a wall,
+ *     the high side is outflow;
+ *   - a prescribed side's state may vary along it (a profile, one state per position along
+ *     the side; positions beyond the grid's ends take the nearest entry); without one it is
+ *     the side's uniform state.
  */
 #include <math.h>
 #include <stdint.h>
@@ -53,13 +59,16 @@ typedef struct {
     int32_t q1;            /* 4 -> D2Q16, 5 -> D2Q25 (Table I) */
     int32_t split;         /* 0 total, 1 internal, 2 non-translational energy split (Eq. Es) */
     int32_t interp_order;  /* 3 -> 4-point cubic Lagrange, 2 -> 3-point quadratic */
-    int32_t bc_x, bc_y;    /* 0 periodic, 1 outflow (index clamp, zero gradient), 2 wall */
+    int32_t bc_x, bc_y;    /* 0 periodic, 1 outflow (index clamp, zero gradient), 2 wall,
+                              3 inflow at the low side and outflow at the high side */
     double gamma, mu;      /* adiabatic exponent (Eq. spec_heat), dynamic viscosity (Eq. kin_visc) */
     double pc_tol;
     int32_t pc_max_iter;
     int32_t pc_fixed_iters; /* > 0: exactly this many predictor-corrector iterations */
     int32_t grad_order;     /* Grad expansion order N: 3 or 4; 0 = the lattice's (3 on D2Q16, 4 on D2Q25) */
-    double wall[4][4];      /* walls x-low, x-high, y-low, y-high: (u_x, u_y, T, rho) of each */
+    double wall[4][4];      /* prescribed sides x-low, x-high, y-low, y-high: (u_x, u_y, T, rho) */
+    const double *profile[4]; /* NULL, or per position along the side: [n][4] (u_x, u_y, T, rho),
+                                 n = ny for the x sides, nx for the y sides */
 } or_config;
 
 static int grad_order_of(const or_config *cfg)
@@ -367,13 +376,27 @@ static int bc_map(int j, int n, int bc)
     return j;
 }
 
-/* Which wall (0 x-low, 1 x-high, 2 y-low, 3 y-high) a position lies beyond, or -1.  A position
- * beyond both a y wall and an x wall belongs to the y wall. */
+/* Which prescribed side (0 x-low, 1 x-high, 2 y-low, 3 y-high) a position lies beyond, or -1:
+ * both sides of a wall axis (2), the low side of an inflow axis (3).  A position beyond both
+ * a prescribed y side and a prescribed x side belongs to the y side. */
 static int wall_of(const or_config *cfg, int gx, int gy)
 {
-    if (cfg->bc_y == 2 && (gy < 0 || gy > cfg->ny - 1)) return gy < 0 ? 2 : 3;
-    if (cfg->bc_x == 2 && (gx < 0 || gx > cfg->nx - 1)) return gx < 0 ? 0 : 1;
+    if ((cfg->bc_y == 2 || cfg->bc_y == 3) && gy < 0) return 2;
+    if (cfg->bc_y == 2 && gy > cfg->ny - 1) return 3;
+    if ((cfg->bc_x == 2 || cfg->bc_x == 3) && gx < 0) return 0;
+    if (cfg->bc_x == 2 && gx > cfg->nx - 1) return 1;
     return -1;
+}
+
+/* The prescribed state (u_x, u_y, T, rho) at position (gx, gy) beyond side w: the profile's
+ * entry at the position along the side, clamped to the grid, or the side's uniform state. */
+static const double *side_state(const or_config *cfg, int w, int gx, int gy)
+{
+    if (!cfg->profile[w]) return cfg->wall[w];
+    int along = w < 2 ? gy : gx, n = w < 2 ? cfg->ny : cfg->nx;
+    if (along < 0) along = 0;
+    if (along > n - 1) along = n - 1;
+    return cfg->profile[w] + 4 * (size_t)along;
 }
 
 /* Lagrange weights of a p-point stencil around the departure coordinate xd; returns the
@@ -441,9 +464,10 @@ static void source_coefficients(const or_src *S, or_memo *M, int gx, int gy, or_
             grad_coefficients(S->L, S->f + node, (int)N, grad_order_of(cfg), src, dst, &M->Af[slot]);
             grad_coefficients(S->L, S->g + node, (int)N, grad_order_of(cfg), src, dst, &M->Ag[slot]);
         } else {
-            /* ghost: equilibrium at the wall state */
-            or_frame wf = {cfg->wall[wall][0], cfg->wall[wall][1], cfg->wall[wall][2]};
-            double rho_g = cfg->wall[wall][3];
+            /* ghost: equilibrium at the prescribed state */
+            const double *st = side_state(cfg, wall, gx, gy);
+            or_frame wf = {st[0], st[1], st[2]};
+            double rho_g = st[3];
             double fg[OR_MAXQ], gg[OR_MAXQ];
             for (int i = 0; i < S->L->Q; ++i) {
                 fg[i] = feq_pop(S->L, i, rho_g);
@@ -545,14 +569,15 @@ static void internal_source(const or_config *cfg, const or_lattice *L, double *g
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t n = (size_t)y * nx + x;
-            /* neighbour velocities: mapped nodes, or the wall's velocity beyond a wall */
+            /* neighbour velocities: mapped nodes, or the prescribed velocity beyond a prescribed side */
             const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
             double vx[4], vy[4];
             for (int k = 0; k < 4; ++k) {
                 int w = wall_of(cfg, nb[k][0], nb[k][1]);
                 if (w >= 0) {
-                    vx[k] = cfg->wall[w][0];
-                    vy[k] = cfg->wall[w][1];
+                    const double *st = side_state(cfg, w, nb[k][0], nb[k][1]);
+                    vx[k] = st[0];
+                    vy[k] = st[1];
                 } else {
                     size_t m = (size_t)bc_map(nb[k][1], ny, cfg->bc_y) * nx + bc_map(nb[k][0], nx, cfg->bc_x);
                     vx[k] = ux1[m];
