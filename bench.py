@@ -240,9 +240,12 @@ def config_rates(torch, pond, device, steps=6):
     (internal vs total energy split, D2Q25 vs D2Q16), each measured on one GPU."""
     def rate(case, steps, **kw):
         stream = torch.cuda.current_stream(device)
+        walls = case.meta.get("walls")
         cfg = pond.Config(nx=case.nx, ny=case.ny, gamma=case.gamma, mu=case.mu, bc_x=case.bc_x,
-                          bc_y=case.bc_y, **kw)
+                          bc_y=case.bc_y, walls=tuple(walls) if walls else None, **kw)
         s = pond.Simulation(cfg, device=device, stream=stream)
+        if case.meta.get("profile") is not None:
+            s.set_boundary_profile("x_low", case.meta["profile"])
         s.set_state(case.rho, case.ux, case.uy, case.T)
         tuning = s.autotune(steps=2, apply=True)
         s.step(2)
@@ -275,6 +278,10 @@ def config_rates(torch, pond, device, steps=6):
     out["decay_256_d2q16_nt_fp32"] = rate(dec, 4 * steps, split="nt")
     out["nt_over_total_time_d2q25"] = (out["decay_256_d2q25_fp32"]["mlups"]
                                        / out["decay_256_d2q25_nt_fp32"]["mlups"])
+    # the jet of Sec. III.C at its resolution (2000 x 1000, D = 100, the paper's jet and
+    # ambient states) through a profiled inflow side, at Mach 1.5 (the paper's Mach 80 turns
+    # non-physical within a few steps, also in the FP64 oracle)
+    out["jet_2000x1000_ma1.5_fp32"] = rate(W.jet(ma=1.5), steps)
     sod = W.sod(nx=400, ny=4)
     out["sod_400x4_fp64"] = rate(sod, 50, precision="fp64")
     out["grad_order"] = {"d2q16": 3, "d2q25": 4}

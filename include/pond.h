@@ -55,7 +55,7 @@ typedef enum {
 enum { POND_D2Q16 = 16, POND_D2Q25 = 25 };                       /* Table I lattices */
 enum { POND_SPLIT_TOTAL = 0, POND_SPLIT_INTERNAL = 1, POND_SPLIT_NT = 2 };   /* Eq. Es, lines 1-3 */
 enum { POND_FP64 = 0, POND_MIXED_FP32 = 1, POND_MIXED_FP16 = 2, POND_MIXED_BF16 = 3 };
-enum { POND_BC_PERIODIC = 0, POND_BC_OUTFLOW = 1, POND_BC_WALL = 2 };
+enum { POND_BC_PERIODIC = 0, POND_BC_OUTFLOW = 1, POND_BC_WALL = 2, POND_BC_INFLOW = 3 };
 
 typedef struct {
     int32_t nx, ny;            /* grid; ny = 1 runs the quasi-1-D form (all y taps on row 0) */
@@ -69,10 +69,14 @@ typedef struct {
                                   state stored in FP32 / FP16 / BF16 */
     int32_t interp_order;      /* 3: 4-point cubic Lagrange (default); 2: 3-point (Sec. III.A.2) */
     int32_t bc_x, bc_y;        /* POND_BC_PERIODIC (index mod n), POND_BC_OUTFLOW (clamp: zero-gradient
-                                  copy of the edge node) or POND_BC_WALL (not in the paper: every
+                                  copy of the edge node), POND_BC_WALL (not in the paper: every
                                   position beyond the wall holds the equilibrium at the wall's
                                   state, given in wall[]; the wall lies half a cell beyond the last
-                                  node; not for y when ny = 1) */
+                                  node; not for y when ny = 1) or POND_BC_INFLOW (the prescribed
+                                  conditions of the jet's inlet, Sec. III.C: the low side is
+                                  prescribed like a wall, the high side is outflow; not for y when
+                                  ny = 1).  A prescribed side's state may vary along it:
+                                  pond_set_boundary_profile */
     double gamma;              /* adiabatic exponent, 1 < gamma <= 2 (c_v = 1/(gamma - 1)) */
     double mu;                 /* dynamic viscosity > 0; tau = mu / (rho T) per node */
     double pc_tol;             /* predictor-corrector tolerance on max(|du|/sqrt(T), |dT|/T) */
@@ -86,9 +90,10 @@ typedef struct {
     int32_t grad_order;        /* Grad expansion order N of the frame transformation
                                   (Eq. gradGeneralTransform): 0 = the lattice's, which is the
                                   only value accepted: 3 on D2Q16, 4 on D2Q25 */
-    double wall[4][4];         /* states of the walls x-low, x-high, y-low, y-high:
-                                  (u_x, u_y, T, rho), used where bc_x / bc_y = POND_BC_WALL
-                                  (T > 0, rho > 0) */
+    double wall[4][4];         /* uniform states of the sides x-low, x-high, y-low, y-high:
+                                  (u_x, u_y, T, rho), used on the prescribed sides (both sides
+                                  of a POND_BC_WALL axis, the low side of a POND_BC_INFLOW axis;
+                                  T > 0, rho > 0) */
 } pond_config;
 
 typedef struct {
@@ -109,7 +114,8 @@ typedef struct pond_sim pond_sim;
 int pond_config_default(pond_config *cfg, int32_t nx, int32_t ny);
 
 /* Bytes of device workspace a simulation with this configuration needs (two copies of the
- * state, see pond_state_bytes, and a status block).  For admission by free HBM. */
+ * state, see pond_state_bytes, a status block and the prescribed sides' profiles).  For
+ * admission by free HBM. */
 int pond_workspace_bytes(const pond_config *cfg, size_t *bytes);
 
 /* Create a simulation on the current device.  dev_workspace: caller-owned device memory
@@ -133,6 +139,19 @@ int pond_set_state(pond_sim *sim, const double *rho, const double *ux, const dou
  * (on_device must be 1, else POND_EINVAL).  Resets statistics and the sticky status. */
 int pond_set_populations(pond_sim *sim, const double *f, const double *g, const double *ux,
                          const double *uy, const double *T, int on_device);
+
+/* Per-position states of a prescribed side (not in the paper; the jet's inlet of Sec. III.C
+ * is prescribed over part of a side).  side: 0 x-low, 1 x-high, 2 y-low, 3 y-high; it must
+ * be prescribed by the configuration (both sides of a POND_BC_WALL axis, the low side of a
+ * POND_BC_INFLOW axis), else POND_EINVAL.  state: [n][4] (u_x, u_y, T, rho) along the side,
+ * n = ny for the x sides and nx for the y sides; the ghost position beyond the side at
+ * coordinate k along it (clamped to 0 .. n - 1; corners belong to the y sides) holds the
+ * equilibrium at state[k].  NULL restores the uniform state cfg->wall[side] (the state at
+ * pond_create).  Host (on_device = 0; checked: T > 0, rho > 0, finite, else POND_EINVAL)
+ * or device pointers (unchecked: a non-physical state shows in the next step's status).
+ * The library copies the states into the workspace; every later step, batched step and
+ * captured graph replay reads them.  Not part of pond_export_state. */
+int pond_set_boundary_profile(pond_sim *sim, int32_t side, const double *state, int on_device);
 
 /* Advance nsteps >= 0 time steps, asynchronously on the simulation's stream. */
 int pond_step(pond_sim *sim, int32_t nsteps);

@@ -68,11 +68,22 @@ Lattice make_lattice(int q1)
 }
 
 struct Layout {
-    size_t mac[2], neq[2], status, total;
+    size_t mac[2], neq[2], status, prof[4], total;   // prof[side] = 0: the side takes no profile
 };
 
 // Grad order of a configuration: the lattice's (3 on D2Q16, 4 on D2Q25).
 int grad_order(const pond_config& c) { return c.lattice == POND_D2Q25 ? 4 : 3; }
+
+// Whether side w (0 x-low, 1 x-high, 2 y-low, 3 y-high) is prescribed: both sides of a wall
+// axis, the low side of an inflow axis.
+bool side_prescribed(const pond_config& c, int w)
+{
+    const int bc = w < 2 ? c.bc_x : c.bc_y;
+    return bc == POND_BC_WALL || (bc == POND_BC_INFLOW && (w % 2) == 0);
+}
+
+// Positions along side w: ny for the x sides, nx for the y sides.
+int side_length(const pond_config& c, int w) { return w < 2 ? c.ny : c.nx; }
 
 Layout layout_of(const pond_config& c)
 {
@@ -84,6 +95,12 @@ Layout layout_of(const pond_config& c)
     for (int k = 0; k < 2; ++k) { l.neq[k] = off; off = align_up(off + planes * N * storage_bytes(c.precision)); }
     l.status = off;
     off = align_up(off + sizeof(DevStatus));
+    for (int w = 0; w < 4; ++w) {
+        l.prof[w] = 0;
+        if (!side_prescribed(c, w)) continue;
+        l.prof[w] = off;
+        off = align_up(off + 4 * (size_t)side_length(c, w) * sizeof(double));
+    }
     l.total = off;
     return l;
 }
@@ -100,10 +117,11 @@ int check_config(const pond_config* c)
     if (c->grad_order != 0 && c->grad_order != (c->lattice == POND_D2Q25 ? 4 : 3)) return POND_EINVAL;
     if (c->precision < POND_FP64 || c->precision > POND_MIXED_BF16) return POND_EINVAL;
     if (c->interp_order != 2 && c->interp_order != 3) return POND_EINVAL;
-    if (c->bc_x < 0 || c->bc_x > 2 || c->bc_y < 0 || c->bc_y > 2) return POND_EINVAL;
-    if (c->bc_y == POND_BC_WALL && c->ny == 1) return POND_EINVAL;   // quasi-1-D grids have no y walls
+    if (c->bc_x < 0 || c->bc_x > 3 || c->bc_y < 0 || c->bc_y > 3) return POND_EINVAL;
+    // quasi-1-D grids have no prescribed y sides
+    if ((c->bc_y == POND_BC_WALL || c->bc_y == POND_BC_INFLOW) && c->ny == 1) return POND_EINVAL;
     for (int w = 0; w < 4; ++w) {
-        const bool used = (w < 2 ? c->bc_x : c->bc_y) == POND_BC_WALL;
+        const bool used = side_prescribed(*c, w);
         const double* st = c->wall[w];
         if (used && !(st[2] > 0.0 && st[3] > 0.0 && std::isfinite(st[0]) && std::isfinite(st[1]) &&
                       std::isfinite(st[2]) && std::isfinite(st[3])))
@@ -144,6 +162,42 @@ namespace {
 double* mac_ptr(pond_sim* s, int k) { return reinterpret_cast<double*>(s->ws + s->lay.mac[k]); }
 void* neq_ptr(pond_sim* s, int k) { return s->ws + s->lay.neq[k]; }
 DevStatus* status_ptr(pond_sim* s) { return reinterpret_cast<DevStatus*>(s->ws + s->lay.status); }
+double* prof_ptr(pond_sim* s, int w) { return reinterpret_cast<double*>(s->ws + s->lay.prof[w]); }
+
+// The profiles a simulation's kernels read: every prescribed side streams from its profile in
+// the workspace (filled with the side's uniform state at creation); null for the other sides.
+void side_profiles(pond_sim* s, const double* prof[4])
+{
+    for (int w = 0; w < 4; ++w) prof[w] = s->lay.prof[w] ? prof_ptr(s, w) : nullptr;
+}
+
+int cuda_status(cudaError_t e);
+
+// Copy states [n][4] (host or device) into side w's profile, or its uniform state when
+// state is null.  Host states are checked (T > 0, rho > 0, finite).
+int write_profile(pond_sim* s, int w, const double* state, int on_device)
+{
+    const int n = side_length(s->cfg, w);
+    const size_t nb = 4 * (size_t)n * sizeof(double);
+    cudaError_t e;
+    if (state && on_device) {
+        e = cudaMemcpyAsync(prof_ptr(s, w), state, nb, cudaMemcpyDeviceToDevice, s->stream);
+    } else {
+        std::vector<double> h(4 * (size_t)n);
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < 4; ++j) h[4 * (size_t)k + j] = state ? state[4 * (size_t)k + j] : s->cfg.wall[w][j];
+        for (int k = 0; k < n; ++k) {
+            const double* st = &h[4 * (size_t)k];
+            if (!(st[2] > 0.0 && st[3] > 0.0 && std::isfinite(st[0]) && std::isfinite(st[1]) &&
+                  std::isfinite(st[2]) && std::isfinite(st[3])))
+                return POND_EINVAL;
+        }
+        // pageable source: the copy has read it when the call returns
+        e = cudaMemcpyAsync(prof_ptr(s, w), h.data(), nb, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    }
+    return cuda_status(e);
+}
 
 AuxParams aux_params(pond_sim* s, int k)
 {
@@ -157,6 +211,7 @@ AuxParams aux_params(pond_sim* s, int k)
     a.split = s->cfg.split;
     a.nord = grad_order(s->cfg);
     std::memcpy(a.wall, s->cfg.wall, sizeof(a.wall));
+    side_profiles(s, a.prof);
     a.N = (long long)s->cfg.nx * s->cfg.ny;
     a.cv = 1.0 / (s->cfg.gamma - 1.0);
     a.mac = mac_ptr(s, k);
@@ -213,8 +268,9 @@ int sync_status(pond_sim* s)
     return POND_OK;
 }
 
-// Parameters of one case for the step kernel (buffers filled by the caller).
-void fill_case(const pond_config& c, DevStatus* status, CaseDesc& d)
+// Parameters of one case for the step kernel (buffers filled by the caller); prof: the
+// sides' profiles (null: uniform states).
+void fill_case(const pond_config& c, DevStatus* status, CaseDesc& d, const double* const* prof = nullptr)
 {
     std::memset(&d, 0, sizeof(d));
     d.nx = c.nx;
@@ -233,6 +289,7 @@ void fill_case(const pond_config& c, DevStatus* status, CaseDesc& d)
     d.cur = 0;
     d.status = status;
     std::memcpy(d.wall, c.wall, sizeof(d.wall));
+    for (int w = 0; w < 4; ++w) d.prof[w] = prof ? prof[w] : nullptr;
 }
 
 // Launch shape of the step kernel: the tile (tile_x * tile_y nodes per CTA; 0 = default,
@@ -378,8 +435,20 @@ int pond_create(const pond_config* cfg, void* dev_workspace, size_t bytes, void*
         delete s;
         return cuda_status(e);
     }
+    for (int w = 0; w < 4; ++w) {   // prescribed sides start from their uniform states
+        if (!lay.prof[w]) continue;
+        rc = write_profile(s, w, nullptr, 0);
+        if (rc != POND_OK) { delete s; return rc; }
+    }
     *out = s;
     return POND_OK;
+}
+
+int pond_set_boundary_profile(pond_sim* s, int32_t side, const double* state, int on_device)
+{
+    if (!s || side < 0 || side > 3) return POND_EINVAL;
+    if (!s->lay.prof[side]) return POND_EINVAL;   // the side is not prescribed
+    return write_profile(s, side, state, on_device);
 }
 
 int pond_set_state(pond_sim* s, const double* rho, const double* ux, const double* uy, const double* T,
@@ -428,7 +497,9 @@ int pond_step(pond_sim* s, int32_t nsteps)
     p.lat = s->lat;
     p.box_w = s->box_w;
     p.box_h = s->box_h;
-    fill_case(c, status_ptr(s), p.one);
+    const double* prof[4];
+    side_profiles(s, prof);
+    fill_case(c, status_ptr(s), p.one, prof);
     Launch l;
     l.block = dim3(s->tx, s->ty, 1);
     l.grid = dim3((c.nx + s->tx - 1) / s->tx, (c.ny + s->ty - 1) / s->ty, 1);
@@ -682,7 +753,9 @@ extern "C" int pond_batch_create(pond_sim* const* sims, int32_t count, void* dev
             c.interp_order != s0->cfg.interp_order || s->one_d != s0->one_d || s->tx != s0->tx ||
             s->ty != s0->ty || s->box_w != s0->box_w || s->box_h != s0->box_h)
             return POND_EINVAL;
-        fill_case(c, status_ptr(s), cases[i]);
+        const double* prof[4];
+        side_profiles(s, prof);
+        fill_case(c, status_ptr(s), cases[i], prof);
         cases[i].mac[0] = mac_ptr(s, s->cur);
         cases[i].neq[0] = neq_ptr(s, s->cur);
         cases[i].mac[1] = mac_ptr(s, 1 - s->cur);
@@ -871,6 +944,10 @@ int time_shape(pond_sim* s, void* scratch, size_t bytes, int tile_x, int tile_y,
     cudaError_t e = cudaMemcpyAsync(mac_ptr(t, t->cur), mac_ptr(s, s->cur), mb, cudaMemcpyDeviceToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(neq_ptr(t, t->cur), neq_ptr(s, s->cur), nb, cudaMemcpyDeviceToDevice, s->stream);
+    for (int w = 0; w < 4 && e == cudaSuccess; ++w)   // and the prescribed sides' profiles
+        if (s->lay.prof[w])
+            e = cudaMemcpyAsync(prof_ptr(t, w), prof_ptr(s, w), 4 * (size_t)side_length(c, w) * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s->stream);
     if (e != cudaSuccess) {
         pond_destroy(t);
         return cuda_status(e);

@@ -17,7 +17,8 @@ struct AuxParams {
     void* neq;          // [nneq(N)][N] storage type
     const double* mac_prev;  // internal source: frames before the step
     DevStatus* status;
-    double wall[4][4];       // wall states (u_x, u_y, T, rho) for boundary type 2
+    double wall[4][4];       // prescribed side states (u_x, u_y, T, rho), boundary types 2 and 3
+    const double* prof[4];   // per side: null (uniform wall[side]) or [n][4] states along it
 };
 
 // Equilibrium state from rho, u, T (device arrays [N]): f_i = rho w_i, g_i = g_eq_i in the
@@ -171,19 +172,20 @@ template <class S>
 __device__ __forceinline__ void internal_source_node(long long n, int nx, int ny, int bc_x, int bc_y,
                                                      long long N, int nord, const double* mac,
                                                      const double* mac_prev, void* neq,
-                                                     const double (*wall)[4])
+                                                     const double (*wall)[4], const double* const* prof)
 {
     const int x = (int)(n % nx), y = (int)(n / nx);
     const double* ux1 = mac + N;
     const double* uy1 = mac + 2 * N;
-    // neighbour velocities: mapped nodes, or the wall's velocity beyond a wall
+    // neighbour velocities: mapped nodes, or the prescribed velocity beyond a prescribed side
     const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
     double vx[4], vy[4];
     for (int k = 0; k < 4; ++k) {
         const int w = wall_of(bc_x, bc_y, nx, ny, nb[k][0], nb[k][1]);
         if (w >= 0) {
-            vx[k] = wall[w][0];
-            vy[k] = wall[w][1];
+            const double* st = side_state(wall, prof, nx, ny, w, nb[k][0], nb[k][1]);
+            vx[k] = st[0];
+            vy[k] = st[1];
         } else {
             const long long m = (long long)bc_map(nb[k][1], ny, bc_y) * nx + bc_map(nb[k][0], nx, bc_x);
             vx[k] = ux1[m];
@@ -211,7 +213,8 @@ __global__ void internal_source_kernel(AuxParams p)
 {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    internal_source_node<S>(n, p.nx, p.ny, p.bc_x, p.bc_y, p.N, p.nord, p.mac, p.mac_prev, p.neq, p.wall);
+    internal_source_node<S>(n, p.nx, p.ny, p.bc_x, p.bc_y, p.N, p.nord, p.mac, p.mac_prev, p.neq, p.wall,
+                            p.prof);
 }
 
 // Batched form: block b works on nodes [256 (b - block_start[c]), ...) of case c (the last case
@@ -232,7 +235,7 @@ __global__ void internal_source_batch_kernel(const CaseDesc* cases, const int* b
     if (n >= c.N) return;
     const int in = c.cur ^ flip;          // the state before the step; the new one is in ^ 1
     internal_source_node<S>(n, c.nx, c.ny, c.bc_x, c.bc_y, c.N, c.nord, c.mac[in ^ 1], c.mac[in], c.neq[in ^ 1],
-                            c.wall);
+                            c.wall, c.prof);
 }
 
 }  // namespace pond

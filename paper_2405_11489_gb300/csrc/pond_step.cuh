@@ -52,7 +52,8 @@ struct CaseDesc {
     void* neq[2];               // [nneq(N)][N] storage type S
     int cur;                    // buffer holding the state when flip = 0
     DevStatus* status;
-    double wall[4][4];          // walls x-low, x-high, y-low, y-high: (u_x, u_y, T, rho)
+    double wall[4][4];          // prescribed sides x-low, x-high, y-low, y-high: (u_x, u_y, T, rho)
+    const double* prof[4];      // per side: null (uniform wall[side]) or [n][4] states along it
 };
 
 struct StepParams {
@@ -77,6 +78,7 @@ struct CaseRun {
     void* neq_out;
     DevStatus* status;
     double wall[4][4];
+    const double* prof[4];
 };
 
 // Resolves the block's case (warp 0 calls it).  In a batched launch every lane runs the same
@@ -116,19 +118,39 @@ __device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r, Ca
     r.mac_out = c->mac[in ^ 1];
     r.neq_out = c->neq[in ^ 1];
     r.status = c->status;
-    for (int w = 0; w < 4; ++w)
+    for (int w = 0; w < 4; ++w) {
         for (int k = 0; k < 4; ++k) r.wall[w][k] = c->wall[w][k];
+        r.prof[w] = c->prof[w];
+    }
 }
 
-// Walls (boundary type 2; the paper gives none): every position beyond a wall holds the
-// equilibrium at the wall's state (rho_w, u_w, T_w), so the wall lies half-way between the
-// last node and the first position beyond it.  Which wall (0 x-low, 1 x-high, 2 y-low,
-// 3 y-high) position (gx, gy) lies beyond, or -1; the y walls own the corners.
+// Prescribed sides (the paper gives no discretisation for walls, nor for the prescribed
+// inlet of the jet, Sec. III.C): every position beyond such a side holds the equilibrium at
+// the side's state (rho_w, u_w, T_w), so the side lies half-way between the last node and the
+// first position beyond it.  Walls (boundary type 2) prescribe both sides of the axis, inflow
+// (type 3) the low side, with outflow at the high side.  Which prescribed side (0 x-low,
+// 1 x-high, 2 y-low, 3 y-high) position (gx, gy) lies beyond, or -1; the y sides own the
+// corners.
 __device__ __forceinline__ int wall_of(int bc_x, int bc_y, int nx, int ny, int gx, int gy)
 {
-    if (bc_y == 2 && (gy < 0 || gy > ny - 1)) return gy < 0 ? 2 : 3;
-    if (bc_x == 2 && (gx < 0 || gx > nx - 1)) return gx < 0 ? 0 : 1;
+    if ((bc_y == 2 || bc_y == 3) && gy < 0) return 2;
+    if (bc_y == 2 && gy > ny - 1) return 3;
+    if ((bc_x == 2 || bc_x == 3) && gx < 0) return 0;
+    if (bc_x == 2 && gx > nx - 1) return 1;
     return -1;
+}
+
+// The state (u_x, u_y, T, rho) prescribed at position (gx, gy) beyond side w: the side's
+// profile entry at the position along the side (clamped to the grid), or its uniform state.
+__device__ __forceinline__ const double* side_state(const double (*wall)[4], const double* const* prof,
+                                                    int nx, int ny, int w, int gx, int gy)
+{
+    const double* pr = prof[w];
+    if (!pr) return wall[w];
+    const int n = w < 2 ? ny : nx;
+    int along = w < 2 ? gy : gx;
+    along = along < 0 ? 0 : (along > n - 1 ? n - 1 : along);
+    return pr + 4 * (long long)along;
 }
 
 // Tile reference state: the centre node's frame (FP64) and derived values in R.
@@ -299,15 +321,17 @@ __device__ __forceinline__ void source_dev(const CaseRun& p, const RefState<R>& 
                               p.mac_in[3 * Nn + nd], reinterpret_cast<const S*>(p.neq_in), nd, Df, Dg);
 }
 
-// The source at position (gx, gy): the node the boundary maps it to, or a wall's ghost.
+// The source at position (gx, gy): the node the boundary maps it to, or a prescribed side's
+// ghost.
 template <class S, class R, int N>
 __device__ __forceinline__ void source_at(const CaseRun& p, const RefState<R>& rf, int gx, int gy,
                                           R* Df, R* Dg)
 {
     const int w = wall_of(p.bc_x, p.bc_y, p.nx, p.ny, gx, gy);
     if (w >= 0) {
-        source_dev_state<S, R, N>(p, rf, p.wall[w][3], p.wall[w][0], p.wall[w][1], p.wall[w][2],
-                                  static_cast<const S*>(nullptr), 0, Df, Dg);
+        const double* st = side_state(p.wall, p.prof, p.nx, p.ny, w, gx, gy);
+        source_dev_state<S, R, N>(p, rf, st[3], st[0], st[1], st[2], static_cast<const S*>(nullptr), 0,
+                                  Df, Dg);
     } else {
         const int sx = bc_map(gx, p.nx, p.bc_x), sy = bc_map(gy, p.ny, p.bc_y);
         source_dev<S, R, N>(p, rf, (long long)sy * p.nx + sx, Df, Dg);

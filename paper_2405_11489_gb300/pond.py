@@ -25,12 +25,14 @@ POND_OK, POND_EINVAL, POND_ENOMEM, POND_ECUDA, POND_ENONPHYSICAL, POND_ENOCONV =
 POND_D2Q16, POND_D2Q25 = 16, 25
 POND_SPLIT_TOTAL, POND_SPLIT_INTERNAL, POND_SPLIT_NT = 0, 1, 2
 POND_FP64, POND_MIXED_FP32, POND_MIXED_FP16, POND_MIXED_BF16 = 0, 1, 2, 3
-POND_BC_PERIODIC, POND_BC_OUTFLOW, POND_BC_WALL = 0, 1, 2
+POND_BC_PERIODIC, POND_BC_OUTFLOW, POND_BC_WALL, POND_BC_INFLOW = 0, 1, 2, 3
 
 PRECISIONS = {"fp64": POND_FP64, "fp32": POND_MIXED_FP32, "fp16": POND_MIXED_FP16,
               "bf16": POND_MIXED_BF16}
 SPLITS = {"total": POND_SPLIT_TOTAL, "internal": POND_SPLIT_INTERNAL, "nt": POND_SPLIT_NT}
-BCS = {"periodic": POND_BC_PERIODIC, "outflow": POND_BC_OUTFLOW, "wall": POND_BC_WALL}
+BCS = {"periodic": POND_BC_PERIODIC, "outflow": POND_BC_OUTFLOW, "wall": POND_BC_WALL,
+       "inflow": POND_BC_INFLOW}
+SIDES = {"x_low": 0, "x_high": 1, "y_low": 2, "y_high": 3}
 
 # Symbols the header declares (checked by the ABI test).
 EXPORTS = ("pond_config_default", "pond_workspace_bytes", "pond_create", "pond_set_state",
@@ -39,7 +41,7 @@ EXPORTS = ("pond_config_default", "pond_workspace_bytes", "pond_create", "pond_s
            "pond_state_bytes", "pond_export_state", "pond_import_state", "pond_step_static",
            "pond_batch_workspace_bytes", "pond_batch_create", "pond_batch_step",
            "pond_batch_use_graph", "pond_batch_destroy", "pond_get_launch", "pond_set_launch",
-           "pond_autotune", "pond_autotune_clear")
+           "pond_autotune", "pond_autotune_clear", "pond_set_boundary_profile")
 POND_TUNE_APPLY, POND_TUNE_RETIME = 1, 2
 
 
@@ -114,6 +116,7 @@ def load_library(path: str = LIB_PATH):
         lib.pond_set_launch.argtypes = [vp, i32, i32, i32]
         lib.pond_autotune.argtypes = [vp, vp, sz, i32, i32, P(pond_tuning)]
         lib.pond_autotune_clear.argtypes = []
+        lib.pond_set_boundary_profile.argtypes = [vp, i32, vp, ctypes.c_int]
         lib.pond_strerror.argtypes = [ctypes.c_int]
         lib.pond_strerror.restype = ctypes.c_char_p
         lib.pond_version.restype = ctypes.c_char_p
@@ -260,6 +263,10 @@ def pond_autotune_clear() -> None:
     load_library().pond_autotune_clear()
 
 
+def pond_set_boundary_profile(h, side: int, state, on_device: int) -> int:
+    return load_library().pond_set_boundary_profile(h, side, state, on_device)
+
+
 def pond_sync(h) -> int:
     return load_library().pond_sync(h)
 
@@ -291,6 +298,8 @@ class Config:
     halo: int = 0
     grad_order: int = 0       # 0: the lattice's (3 on D2Q16, 4 on D2Q25)
     walls: tuple | None = None  # four (u_x, u_y, T, rho): x-low, x-high, y-low, y-high
+    # boundaries per axis: "periodic", "outflow", "wall" (both sides prescribed) or "inflow"
+    # (low side prescribed, high side outflow)
 
     def to_c(self) -> pond_config:
         tol = self.pc_tol if self.pc_tol is not None else (1e-12 if self.precision == "fp64" else 1e-6)
@@ -353,6 +362,30 @@ class Simulation:
             with torch.cuda.device(self.device):
                 rc = pond_set_state(self.handle, *[a.ctypes.data for a in arrs], 0)
         _check(rc, "pond_set_state")
+
+    def set_boundary_profile(self, side, state=None):
+        """Per-position states [n][4] (u_x, u_y, T, rho) of a prescribed side ("x_low",
+        "x_high", "y_low", "y_high" or 0..3; n = ny for the x sides, nx for the y sides):
+        numpy (checked and copied by the library) or a CUDA float64 tensor; None restores
+        the side's uniform state."""
+        torch = self.torch
+        w = SIDES[side] if isinstance(side, str) else int(side)
+        if not 0 <= w <= 3:
+            raise ValueError("side %r" % (side,))
+        n = self.cfg.ny if w < 2 else self.cfg.nx
+        if state is not None and tuple(state.shape) != (n, 4):
+            raise ValueError("profile of side %d: shape %s, expected (%d, 4)" % (w, tuple(state.shape), n))
+        with torch.cuda.device(self.device):
+            if state is None:
+                rc = pond_set_boundary_profile(self.handle, w, None, 0)
+            elif isinstance(state, torch.Tensor):
+                t = state.to(device=self.device, dtype=torch.float64).contiguous()
+                rc = pond_set_boundary_profile(self.handle, w, _dptr(t), 1)
+                self.stream.synchronize()          # the copy has read t
+            else:
+                a = np.ascontiguousarray(state, dtype=np.float64)
+                rc = pond_set_boundary_profile(self.handle, w, a.ctypes.data, 0)
+        _check(rc, "pond_set_boundary_profile")
 
     def set_populations(self, f, g, ux, uy, T):
         """Populations [Q][ny][nx] in the frames (ux, uy, T) [ny][nx] (numpy or tensors)."""

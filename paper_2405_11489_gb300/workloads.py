@@ -170,6 +170,42 @@ def riemann2d(n=1024, seed=0, gamma=1.4, max_disp=2.0, mu=1e-3, steps=500, width
                 meta={"seed": seed, "kappa": kappa, "states": states, "max_ma": ma, "width": width})
 
 
+def jet(nx=2000, ny=1000, diameter=100.0, ma=1.5, jet_state=(5.0, 0.005), ambient=(50.0, 0.0005),
+        gamma=1.4, mu=1e-3, width=2.0, steps=240):
+    """The jet of Sec. III.C: a semicircle of diameter `diameter` on the left side holds the
+    jet state (rho, T) = jet_state moving at Mach `ma` along x; the rest of the domain is at
+    rest at `ambient` (the paper: Ma 80, (5, 0.005) into (50, 0.0005), 2000 x 1000, D = 100).
+    The left side is an inflow side whose profile is the jet state inside the jet's diameter
+    and the ambient state outside; outflow elsewhere.  width > 0 blends jet and ambient over
+    a tanh profile of that many cells (density and pressure blended, T = p/rho).  The inlet
+    profile is meta["profile"] ([ny][4]: u_x, u_y, T, rho) and meta["walls"] the four side
+    states (the x-low one is the profile's first entry)."""
+    rho_j, T_j = jet_state
+    rho_a, T_a = ambient
+    u_j = ma * math.sqrt(gamma * T_j)
+    yc = np.arange(ny, dtype=float) - (ny - 1) / 2.0
+
+    def inside(r):
+        if width <= 0:
+            return (r <= diameter / 2.0).astype(float)
+        return 0.5 * (1.0 - np.tanh((r - diameter / 2.0) / width))
+
+    def state(s):
+        rho = rho_a + (rho_j - rho_a) * s
+        p = rho_a * T_a + (rho_j * T_j - rho_a * T_a) * s
+        return rho, u_j * s, p / rho
+
+    r_in, u_in, T_in = state(inside(np.abs(yc)))
+    prof = np.stack([u_in, np.zeros(ny), T_in, r_in], 1)
+    x = np.arange(nx, dtype=float)[None, :]
+    rho, ux, T = state(inside(np.sqrt((x + 0.5) ** 2 + yc[:, None] ** 2)))
+    walls = [tuple(prof[0])] * 4
+    return Case("jet", rho, ux, np.zeros((ny, nx)), T, gamma=gamma, mu=mu, bc_x="inflow",
+                bc_y="outflow", steps=steps,
+                meta={"ma": ma, "u_jet": u_j, "diameter": diameter, "profile": prof, "walls": walls,
+                      "jet_state": jet_state, "ambient": ambient, "width": width})
+
+
 def tube_batch(count=256, seed=1, nmin=200, nmax=4000, gamma=1.4, mu=1e-3, width=4.0):
     """Uneven quasi-1-D shock tubes: N ~ logU[nmin, nmax] cells (ny = 1), p_L/p_R ~ logU[2, 100],
     rho_L/rho_R ~ logU[1, 10] (right state rho = 0.125, p = 0.1 as in Sod).  Each tube's

@@ -68,3 +68,27 @@ def test_null_handles_are_rejected(lib):
     assert lib.pond_step(None, 1) == pond.POND_EINVAL
     assert lib.pond_sync(None) == pond.POND_EINVAL
     assert lib.pond_destroy(None) == pond.POND_EINVAL
+
+
+def test_prescribed_sides_are_validated_and_sized(lib):
+    from paper_2405_11489_gb300 import pond
+    n = ctypes.c_size_t(0)
+    base = pond.pond_config_default(40, 24)
+    b0 = pond.pond_workspace_bytes(base)
+    # inflow on x: the x-low side is prescribed and carries a profile of ny states
+    cfg = pond.pond_config_default(40, 24)
+    cfg.bc_x = pond.POND_BC_INFLOW
+    cfg.wall[0][2], cfg.wall[0][3] = 1.0, 1.0
+    assert pond.pond_workspace_bytes(cfg) >= b0 + 24 * 4 * 8
+    cfg.wall[0][2] = 0.0                                  # T <= 0 on a prescribed side
+    assert lib.pond_workspace_bytes(ctypes.byref(cfg), ctypes.byref(n)) == pond.POND_EINVAL
+    cfg.wall[0][2] = 1.0
+    cfg.wall[1][2] = 0.0                                  # x-high is outflow: not checked
+    assert lib.pond_workspace_bytes(ctypes.byref(cfg), ctypes.byref(n)) == pond.POND_OK
+    # no prescribed y sides on quasi-1-D grids
+    cfg1 = pond.pond_config_default(40, 1)
+    cfg1.bc_y = pond.POND_BC_INFLOW
+    assert lib.pond_workspace_bytes(ctypes.byref(cfg1), ctypes.byref(n)) == pond.POND_EINVAL
+    cfg1.bc_y = 4
+    assert lib.pond_workspace_bytes(ctypes.byref(cfg1), ctypes.byref(n)) == pond.POND_EINVAL
+    assert lib.pond_set_boundary_profile(None, 0, None, 0) == pond.POND_EINVAL

@@ -2,9 +2,10 @@
 
 FP64 mode in fixed-iteration predictor-corrector mode must match the oracle to a relative
 L-infinity error of 1e-12 per field (rel = max|gpu - oracle| / max|oracle|), on grids that
-span several tiles and leave ragged tails, with both boundary types, both lattices, both
-energy splits, both interpolation orders, the shared-memory and the global-gather (halo
-fallback) paths and degenerate grid shapes.
+span several tiles and leave ragged tails, with every boundary type (periodic, outflow,
+walls, inflow, per-position side profiles), both lattices, the three energy splits, both
+interpolation orders, the shared-memory and the global-gather (halo fallback) paths and
+degenerate grid shapes.
 """
 import math
 
@@ -109,6 +110,10 @@ CASES = [
     (28, 10, 16, "total", 3, ("periodic", "wall")),
     (24, 11, 25, "nt", 3, ("wall", "wall")),
     (30, 8, 16, "internal", 3, ("wall", "outflow")),
+    (33, 9, 16, "total", 3, ("inflow", "outflow")),
+    (26, 10, 25, "internal", 3, ("inflow", "inflow")),
+    (29, 8, 16, "nt", 2, ("periodic", "inflow")),
+    (300, 1, 16, "total", 3, ("inflow", "periodic")),
 ]
 
 
@@ -264,3 +269,78 @@ def test_couette_flow_on_the_gpu(pond):
         assert np.max(np.abs(theta - exact)) < 0.05, precision
         assert np.max(np.abs(ux[:, 0] / u0 - eta)) < 0.02, precision
         sim.close()
+
+
+def _profiles(rng, nx, ny, sides):
+    """Random per-position states (u_x, u_y, T, rho) along the given sides."""
+    out = [None] * 4
+    for w in sides:
+        n = ny if w < 2 else nx
+        out[w] = np.stack([0.3 + 0.1 * rng.standard_normal(n), 0.05 * rng.standard_normal(n),
+                           0.8 + 0.05 * rng.standard_normal(n), 1.0 + 0.05 * rng.standard_normal(n)], 1)
+    return out
+
+
+@pytest.mark.parametrize("split,lattice,bc,sides", [
+    ("total", 16, ("inflow", "wall"), (0, 2, 3)),
+    ("internal", 16, ("inflow", "inflow"), (0, 2)),
+    ("nt", 25, ("wall", "periodic"), (0, 1)),
+])
+def test_fp64_side_profiles_match_oracle(pond, orc, split, lattice, bc, sides):
+    """Per-position side states (pond_set_boundary_profile), changed between steps, and
+    restored to the uniform state, against the oracle with the same profiles."""
+    nx, ny = 35, 19
+    rng = np.random.default_rng(7)
+    ocfg, sim = make_pair(pond, orc, nx, ny, lattice, split, 3, bc, K=3)
+    st = random_state(orc, ocfg, seed=11)
+    sim.set_populations(st.f, st.g, st.ux, st.uy, st.T)
+    for phase in range(3):
+        prof = _profiles(rng, nx, ny, sides) if phase < 2 else [None] * 4
+        for w in sides:
+            sim.set_boundary_profile(w, prof[w])
+        pcfg = orc.make_config(nx, ny, lattice=lattice, split=split, bc_x=bc[0], bc_y=bc[1],
+                               mu=0.02, pc_fixed_iters=3, walls=WALLS, profiles=prof)
+        for _ in range(2):
+            st = orc.step(pcfg, st).state
+        sim.step(2)
+        compare(orc, pcfg, sim, st, FP64_TOL, "phase %d" % phase)
+    sim.close()
+
+
+def test_fp64_batched_members_keep_their_profiles(pond, orc):
+    """A batch of two inflow grids with different inlet profiles (one launch per step)."""
+    nx, ny = 30, 14
+    rng = np.random.default_rng(3)
+    sims, pairs = [], []
+    for k in range(2):
+        ocfg, sim = make_pair(pond, orc, nx, ny, 16, "total", 3, ("inflow", "outflow"), K=2)
+        prof = _profiles(rng, nx, ny, (0,))
+        sim.set_boundary_profile("x_low", prof[0])
+        pcfg = orc.make_config(nx, ny, bc_x="inflow", bc_y="outflow", mu=0.02, pc_fixed_iters=2,
+                               walls=WALLS, profiles=prof)
+        st = random_state(orc, ocfg, seed=20 + k)
+        sim.set_populations(st.f, st.g, st.ux, st.uy, st.T)
+        sims.append(sim)
+        pairs.append((pcfg, st))
+    batch = pond.Batch(sims)
+    batch.step(3)
+    for sim, (pcfg, st) in zip(sims, pairs):
+        for _ in range(3):
+            st = orc.step(pcfg, st).state
+        compare(orc, pcfg, sim, st, FP64_TOL, "batched")
+    batch.close()
+    for s in sims:
+        s.close()
+
+
+def test_profile_shape_and_side_are_checked(pond):
+    sim = pond.Simulation(pond.Config(nx=20, ny=10, bc_x="inflow", walls=tuple(WALLS)))
+    with pytest.raises(ValueError):
+        sim.set_boundary_profile("x_low", np.ones((20, 4)))      # x sides take ny states
+    with pytest.raises(pond.PondError):
+        sim.set_boundary_profile("x_high", np.ones((10, 4)))     # outflow side: not prescribed
+    bad = np.ones((10, 4))
+    bad[3, 2] = -1.0                                             # T <= 0
+    with pytest.raises(pond.PondError):
+        sim.set_boundary_profile("x_low", bad)
+    sim.close()

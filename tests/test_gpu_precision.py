@@ -75,6 +75,45 @@ def test_mixed_precision_l1_bounds(pond, orc, precision, lattice, split):
     sim.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_mixed_precision_jet_inflow_l1_bounds(pond, orc, precision):
+    """A jet entering through a profiled inlet (x-low inflow, tanh jet of Ma 1.5 over a
+    Ma 0.3 co-flow at equal pressure), outflow elsewhere, in the mixed modes: the stated
+    bounds hold."""
+    nx, ny, steps, gamma = 48, 40, 20, 1.4
+    yc = np.arange(ny) - (ny - 1) / 2.0
+    jet = 0.5 * (1.0 - np.tanh((np.abs(yc) - 6.0) / 2.0))
+    T_in = 0.8 * (1.0 + 0.1 * jet)
+    prof = np.stack([(0.3 + 1.2 * jet) * np.sqrt(gamma * T_in), np.zeros(ny), T_in, 0.8 / T_in], 1)
+    walls = [tuple(prof[0])] * 4
+    rho = np.full((ny, nx), 1.0)
+    ux = np.full((ny, nx), 0.3 * math.sqrt(gamma * 0.8))
+    uy = np.zeros((ny, nx))
+    T = np.full((ny, nx), 0.8)
+    ocfg = orc.make_config(nx, ny, bc_x="inflow", bc_y="outflow", mu=0.04, pc_fixed_iters=2,
+                           walls=walls, profiles=[prof, None, None, None])
+    st = orc.init_state(ocfg, rho, ux, uy, T)
+    for _ in range(steps):
+        st = orc.step(ocfg, st).state
+    o = orc.moments(ocfg, st)
+    sim = pond.Simulation(pond.Config(nx=nx, ny=ny, precision=precision, bc_x="inflow",
+                                      bc_y="outflow", mu=0.04, pc_fixed_iters=2, walls=tuple(walls)))
+    sim.set_boundary_profile("x_low", prof)
+    sim.set_state(rho, ux, uy, T)
+    sim.step(steps)
+    g = sim.moments()
+    brt, bu = BOUNDS[precision]
+    speed = max(np.abs(o[1]).max(), np.abs(o[2]).max(), math.sqrt(o[3].max()))
+    errs = {"rho": _l1(g[0], o[0], np.mean(np.abs(o[0]))), "T": _l1(g[3], o[3], np.mean(o[3])),
+            "ux": _l1(g[1], o[1], speed), "uy": _l1(g[2], o[2], speed)}
+    print(precision, "jet", errs)
+    assert errs["rho"] <= brt and errs["T"] <= brt, errs
+    assert errs["ux"] <= bu and errs["uy"] <= bu, errs
+    # the jet has entered: the centre row is faster than the co-flow
+    assert g[1][ny // 2, nx // 4] > 1.5 * g[1][2, nx // 4]
+    sim.close()
+
+
 def _sample_nodes(nx, ny, rng, n_random=48):
     pts = {(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1), (nx // 2, ny // 2),
            (nx // 2 - 1, ny // 2 - 1), (nx // 2, 0), (0, ny // 2), (nx - 1, ny // 2 + 1)}
@@ -85,9 +124,14 @@ def _sample_nodes(nx, ny, rng, n_random=48):
 
 
 def _sampled_step(pond, orc, case, precision, split, warm, tol_m, tol_f, seed, order=3):
+    walls = case.meta.get("walls")
+    prof = case.meta.get("profile")
     cfg = pond.Config(nx=case.nx, ny=case.ny, precision=precision, split=split, gamma=case.gamma,
-                      mu=case.mu, bc_x=case.bc_x, bc_y=case.bc_y, interp_order=order)
+                      mu=case.mu, bc_x=case.bc_x, bc_y=case.bc_y, interp_order=order,
+                      walls=tuple(walls) if walls else None)
     sim = pond.Simulation(cfg)
+    if prof is not None:
+        sim.set_boundary_profile("x_low", prof)
     sim.set_state(case.rho, case.ux, case.uy, case.T)
     sim.step(warm)
     f, g, fux, fuy, fT = sim.populations()
@@ -95,7 +139,8 @@ def _sampled_step(pond, orc, case, precision, split, warm, tol_m, tol_f, seed, o
     gf, gg, gux, guy, gT = sim.populations()
     ocfg = orc.make_config(case.nx, case.ny, split=split, gamma=case.gamma, mu=case.mu,
                            bc_x=case.bc_x, bc_y=case.bc_y, pc_tol=1e-13, pc_max_iter=40,
-                           interp_order=order)
+                           interp_order=order, walls=walls,
+                           profiles=[prof, None, None, None] if prof is not None else None)
     st = orc.State(f, g, fux, fuy, fT)
     xs, ys = _sample_nodes(case.nx, case.ny, np.random.default_rng(seed))
     of, og, (oux, ouy, oT), _ = orc.step_nodes(ocfg, st, xs, ys)
@@ -172,3 +217,10 @@ def test_sod_400x4_fp32_matches_exact_riemann(pond):
         assert np.mean(np.abs(rho[row] - re)) < 4e-3
         assert np.mean(np.abs(rho[row] * T[row] / 0.04 - pe)) < 4e-3
     sim.close()
+
+
+def test_jet_2000x1000_sampled_parity(pond, orc):
+    """The jet configuration of Sec. III.C at its resolution (2000 x 1000, D = 100, the paper's
+    jet and ambient states, profiled x-low inflow) at Mach 1.5, in mixed FP32."""
+    case = W.jet(ma=1.5)
+    _sampled_step(pond, orc, case, "fp32", "total", 3, 2e-6, 2e-5, seed=4)
