@@ -436,25 +436,34 @@ def e2e_rate(torch, pond, device, steps, warmup):
                     "pond_get_moments(host) x 4 grids; host wall clock"}
 
 
-def cpu_baseline(target_seconds=10.0):
+def cpu_baseline(target_seconds=10.0, single_seconds=6.0):
     """The FP64 oracle, as it stands, on the host cores: the Ma = 1 grid of the workload,
-    whole 256^2 field, as many time steps as fit in ~target_seconds (at least one)."""
+    whole 256^2 field, as many time steps as fit in ~target_seconds (at least one) with
+    OpenMP over every core; then the same on one thread (at least one step)."""
     import oracle
     oracle.build()
-    cores = os.cpu_count() or 1
+    cores = oracle.set_threads(os.cpu_count() or 1)
     cfg = oracle.make_config(NX, NY, gamma=GAMMA, mu=MU, pc_tol=1e-12)
-    st = oracle.init_state(cfg, *case_fields(1.0))
-    t0 = time.perf_counter()
-    n = 0
-    while True:
-        st = oracle.step(cfg, st).state
-        n += 1
-        if time.perf_counter() - t0 > target_seconds:
-            break
-    t = time.perf_counter() - t0
-    return {"value": NX * NY * n / t / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+
+    def rate(seconds):
+        st = oracle.init_state(cfg, *case_fields(1.0))
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            st = oracle.step(cfg, st).state
+            n += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        return NX * NY * n / (time.perf_counter() - t0) / 1e6, n
+
+    v, n = rate(target_seconds)
+    oracle.set_threads(1)
+    v1, n1 = rate(single_seconds)
+    oracle.set_threads(cores)
+    return {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": "FP64 oracle, %d time step(s) of the Ma = 1 256x256 grid (OpenMP, %d threads)"
-                      % (n, cores)}
+                      % (n, cores),
+            "single_thread": {"value": v1, "unit": "MLUPS", "steps": n1}}
 
 
 def run_reference(args, world, rank):

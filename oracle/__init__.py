@@ -103,6 +103,8 @@ def _lib_handle():
             lib = ctypes.CDLL(build())
             P = ctypes.POINTER
             lib.or_lattice_1d.argtypes = [ctypes.c_int, _D, _D]
+            lib.or_set_threads.argtypes = [ctypes.c_int]
+            lib.or_set_threads.restype = ctypes.c_int
             lib.or_grad_transform.argtypes = [ctypes.c_int, _D] + [ctypes.c_double] * 6 + [_D]
             lib.or_grad_coefficients.argtypes = [ctypes.c_int, _D] + [ctypes.c_double] * 6 + [_D]
             lib.or_grad_transform_n.argtypes = [ctypes.c_int, ctypes.c_int, _D] + [ctypes.c_double] * 6 + [_D]
@@ -122,6 +124,11 @@ def _lib_handle():
 def _p(a: np.ndarray):
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(_D)
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's node loops (n > 0 sets them); returns the count in effect."""
+    return _lib_handle().or_set_threads(n)
 
 
 def lattice_1d(q1: int):

@@ -50,6 +50,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_MAXQ1 5
 #define OR_MAXQ (OR_MAXQ1 * OR_MAXQ1)
@@ -80,6 +83,19 @@ static int grad_order_of(const or_config *cfg)
 /* ---------------------------------------------------------------------------------- */
 /* Table I: one-dimensional Gauss-Hermite quadratures with r T_L = 1.                  */
 /* ---------------------------------------------------------------------------------- */
+/* Threads of the node loops (OpenMP builds; 1 otherwise): n > 0 sets them; returns the count
+ * in effect.  Timing only: a node's arithmetic does not depend on the thread count. */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 int or_lattice_1d(int q1, double *c, double *w)
 {
     if (q1 == 4) {
