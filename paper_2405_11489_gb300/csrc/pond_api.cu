@@ -451,6 +451,19 @@ int pond_set_boundary_profile(pond_sim* s, int32_t side, const double* state, in
     return write_profile(s, side, state, on_device);
 }
 
+// Host check of primitive fields: rho > 0 and T > 0 finite, u finite.  Branch-free over the
+// nodes (x - x is 0 exactly for finite x and NaN otherwise), so the loop vectorises.
+static bool physical_fields(const double* rho, const double* ux, const double* uy, const double* T,
+                            long long N)
+{
+    const double inf = HUGE_VAL;
+    bool ok = true;
+    for (long long n = 0; n < N; ++n)
+        ok &= (rho[n] > 0.0) & (rho[n] < inf) & (T[n] > 0.0) & (T[n] < inf) &
+              (ux[n] - ux[n] == 0.0) & (uy[n] - uy[n] == 0.0);
+    return ok;
+}
+
 int pond_set_state(pond_sim* s, const double* rho, const double* ux, const double* uy, const double* T,
                    int on_device)
 {
@@ -460,10 +473,7 @@ int pond_set_state(pond_sim* s, const double* rho, const double* ux, const doubl
     if (rc != POND_OK) return rc;
     const double *drho = rho, *dux = ux, *duy = uy, *dT = T;
     if (!on_device) {
-        for (long long n = 0; n < N; ++n)
-            if (!(rho[n] > 0.0) || !(T[n] > 0.0) || !std::isfinite(rho[n]) || !std::isfinite(T[n]) ||
-                !std::isfinite(ux[n]) || !std::isfinite(uy[n]))
-                return POND_EINVAL;
+        if (!physical_fields(rho, ux, uy, T, N)) return POND_EINVAL;
         double* stage = mac_ptr(s, 1 - s->cur);   // the idle frame buffer stages the input
         const double* src[4] = {rho, ux, uy, T};
         for (int k = 0; k < 4; ++k) {

@@ -209,6 +209,14 @@ def test_nonphysical_state_is_reported(pond, orc):
     assert rc == pond.POND_ENONPHYSICAL and stats.first_bad_node >= 0
     with pytest.raises(pond.PondError):
         sim.set_state(np.ones((8, 12)), np.zeros((8, 12)), np.zeros((8, 12)), -np.ones((8, 12)))
+    # every kind of bad host field, at one node each
+    for field, value in ((0, 0.0), (0, np.inf), (0, np.nan), (1, np.nan), (1, np.inf), (2, -np.inf),
+                         (3, 0.0), (3, np.inf), (3, np.nan)):
+        f = [np.ones((8, 12)), np.zeros((8, 12)), np.zeros((8, 12)), np.ones((8, 12))]
+        f[field][5, 7] = value
+        with pytest.raises(pond.PondError):
+            sim.set_state(*f)
+    sim.set_state(np.ones((8, 12)), np.full((8, 12), -3.0), np.zeros((8, 12)), np.ones((8, 12)))
     sim.close()
 
 
