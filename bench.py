@@ -9,7 +9,7 @@ batch (pond_batch: one kernel launch per time step).  Synthetic, seeded inputs.
 
 Metric: MLUPS = node updates per second / 1e6 over the whole job (all ranks).  The line
 also carries the plain-FP64 GPU step on the same workload, the L1 error of the mixed path
-against the FP64 path, the FP32-pipe roofline of the step kernel, the end-to-end rate
+against the FP64 path, the ALU roofline (FP32 and FP64 pipes) of the step kernel, the end-to-end rate
 through the C-ABI with host buffers, and the FP64 oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -42,15 +42,33 @@ MU = 0.05
 METRIC = "PonD-DDF MLUPS, mixed-prec vs plain FP64 at stated L1 err; serving p50/p99 latency"
 WORKLOAD = ("periodic 256x256 shear wave (u_y = 0.05 sin 2pi x/L) + Gaussian thermal pulse "
             "(dT/T = 1e-3, width 16), background Ma 0.5/1/1.5/2 (4 grids), D2Q16 total split")
-# FP32-pipe peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (max SM clock).
+# Pipe peaks from unit counts at the maximum SM clock (2.070 GHz): FP32 152 SMs x 128 lanes x
+# 2 flop; FP64 152 SMs x 2 FMA per clock x 2 flop (= the part's nominal 1.25 TFLOP/s).
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
-# Algorithmic FP32 work of one node update (D2Q16): per predictor-corrector iteration and
-# population, a 16-tap interpolation of 20 Hermite coefficients plus the frame move,
-# reconstruction and moment sums (~800 flop); plus ~1000 flop per update for staging and
-# collision.  K = measured mean iterations.
+FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1e3
+# Algorithmic work of one node update (D2Q16), K = measured mean iterations:
+#  FP32: per predictor-corrector iteration and population, a 16-tap interpolation of 20
+#        Hermite coefficients plus the frame move, reconstruction and moment sums (~800 flop);
+#        plus ~1000 flop per update for staging and collision: 800 Q K + 1000;
+#  FP64: the conserved-moment sums (~130) and the frame update (~20) per iteration, plus ~50
+#        per update (temperature recovery, final frame): 150 K + 50.
+# The step's roofline time is F32/P32 + F64/P64 (the two pipes' work in sequence); `achieved`
+# is expressed in FP32-equivalent flop (FP64 flop weighted by P32/P64) per second against P32,
+# so that achieved / peak = roofline time / measured time.
 FLOP_PER_POP_ITER = 800.0
 FLOP_PER_UPDATE = 1000.0
+F64_PER_ITER = 150.0
+F64_PER_UPDATE = 50.0
+
+
+def roofline_terms(nodes, K, seconds):
+    """FP32 and FP64 algorithmic flop of `nodes` updates at mean iterations K, and the
+    roofline fraction (F32/P32 + F64/P64) / seconds."""
+    f32 = nodes * (FLOP_PER_POP_ITER * 16 * K + FLOP_PER_UPDATE)
+    f64 = nodes * (F64_PER_ITER * K + F64_PER_UPDATE)
+    t_roof = f32 / (FP32_PEAK_TFLOPS * 1e12) + f64 / (FP64_PEAK_TFLOPS * 1e12)
+    return f32, f64, t_roof / seconds
 
 
 def case_fields(ma):
@@ -564,7 +582,8 @@ def main():
     nodes_per_step = len(MACHS) * NX * NY
     value = whole_job_mlups(world, nodes_per_step, step_ms)
     launch_ms = sum(per_launch) / len(per_launch)
-    flops_per_launch = nodes_per_step * (FLOP_PER_POP_ITER * 16 * K + FLOP_PER_UPDATE)
+    f32_launch, f64_launch, frac = roofline_terms(nodes_per_step, K, launch_ms * 1e-3)
+    flops_per_launch = f32_launch + f64_launch * FP32_PEAK_TFLOPS / FP64_PEAK_TFLOPS
     achieved = flops_per_launch / (launch_ms * 1e-3) / 1e12
     if rank != 0:
         if world > 1:
@@ -579,6 +598,7 @@ def main():
     # plain FP64 GPU step on the same workload (fewer steps: it is ~two orders slower)
     sims64, batch64, tune64 = make_sims(pond, "fp64", device, stream, tune=True)
     per64 = time_steps(torch, batch64, stream, max(2, args.steps // 10), 1, flush)
+    K64 = mean_iters(sims64)
     batch64.close()
     for s in sims64:
         s.close()
@@ -608,6 +628,10 @@ def main():
         "autotune": tuning,
         "fp64": {"value": nodes_per_step / (fp64_ms * 1e-3) / 1e6, "unit": "MLUPS",
                  "ms_per_step": fp64_ms, "speedup_mixed_over_fp64": fp64_ms / step_ms,
+                 "pc_iters_mean": K64,
+                 # every flop on the FP64 pipe: (F32 + F64) / P64 over the measured time
+                 "roofline_frac": sum(roofline_terms(nodes_per_step, K64, 1.0)[:2])
+                                  / (FP64_PEAK_TFLOPS * 1e12) / (fp64_ms * 1e-3),
                  "launch_shape": "tile %dx%d, halo %d (autotuned)" % (tune64["tile_x"], tune64["tile_y"],
                                                                     tune64["halo"])},
         "l1_err_mixed_vs_fp64": err,
@@ -617,8 +641,13 @@ def main():
         "serving": serving,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "flop_basis": "FP32-equivalent: F32 + F64 x P32/P64; frac = (F32/P32 + F64/P64) / t",
+                     "f32_flop_per_launch": f32_launch, "f64_flop_per_launch": f64_launch,
+                     "p64_tflops": FP64_PEAK_TFLOPS,
+                     "fp32_pipe_frac": f32_launch / (launch_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
                      "kernel": "step_kernel<float,float,4,4,false,256> (batched over the 4 grids)",
-                     "peak_basis": "FP32 pipe: 152 SM x 128 lanes x 2 flop x 2.07 GHz (unit counts)",
+                     "peak_basis": "unit counts at 2.07 GHz: FP32 152 SM x 128 lanes x 2 flop; "
+                                   "FP64 152 SM x 2 FMA x 2 flop",
                      "flops_per_launch": flops_per_launch, "launch_ms": launch_ms},
         "cpu_baseline": cpu,
         "e2e": e2e,
