@@ -49,6 +49,7 @@ class Completion:
     nodes: int
     status: str
     fields: tuple = field(default=None, repr=False)
+    what: str = ""              # request type, grid, split and precision
 
 
 def percentile(values, q):
@@ -127,9 +128,11 @@ class Server:
                     fields, status = self.be.finish(a.sim)
                     self.used -= a.bytes
                     self.active.remove(a)
-                    self.done.append(Completion(a.req.rid, a.req.arrival, a.admitted_at, now,
-                                                a.req.steps, nodes, status,
-                                                fields if self.keep_fields else None))
+                    r = a.req
+                    what = "%s %dx%d %s %s" % (getattr(r.case, "name", "case"), r.case.nx, r.case.ny,
+                                               getattr(r, "split", ""), getattr(r, "precision", ""))
+                    self.done.append(Completion(r.rid, r.arrival, a.admitted_at, now, r.steps, nodes,
+                                                status, fields if self.keep_fields else None, what))
         return bool(ready)
 
     # -- the loop --------------------------------------------------------------------------
@@ -167,7 +170,11 @@ class Server:
                 "aggregate_mlups": self.node_updates / wall / 1e6 if wall > 0 else None,
                 "wall_s": wall, "ticks": self.ticks, "peak_workspace_bytes": self.peak_used,
                 "budget_bytes": self.budget,
-                "statuses": sorted({c.status for c in served})}
+                "statuses": sorted({c.status for c in served}),
+                "status_counts": {st: sum(1 for c in served if c.status == st)
+                                  for st in sorted({c.status for c in served})},
+                # requests whose state turned non-physical (first 20): id, type, grid, split, precision
+                "nonphysical": [(c.rid, c.what) for c in served if c.status.startswith("non-physical")][:20]}
 
 
 class PondBackend:
