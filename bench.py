@@ -174,7 +174,7 @@ def make_sims(pond, precision, device, stream, tune=False):
         sims.append(s)
     tuning = None
     if tune:
-        tuning = sims[0].autotune(steps=3, apply=True)
+        tuning = sims[0].autotune(steps=8, apply=True)
         for s in sims[1:]:
             s.set_launch(tuning["tile_x"], tuning["tile_y"], tuning["halo"])
     batch = pond.Batch(sims, stream=stream)

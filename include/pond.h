@@ -231,8 +231,8 @@ int pond_batch_destroy(pond_batch *batch);
  *    2-D grids (256x1 on quasi-1-D ones) times halos 4, 5, 6, 8 -- by running
  *    1 + steps time steps of a copy of sim's current state in dev_scratch (caller-owned
  *    device memory of pond_workspace_bytes(cfg) bytes, 256-byte aligned) on sim's stream,
- *    and return the fastest in *out (candidates = shapes timed, ms_per_step its time per
- *    step).  sim's own state and statistics are untouched; kernel-side statuses of the
+ *    time the three fastest twice more (each keeps its best time), and return the fastest
+ *    in *out (candidates = shapes timed, ms_per_step its best time per step).  sim's own state and statistics are untouched; kernel-side statuses of the
  *    copy (POND_ENOCONV, POND_ENONPHYSICAL) do not rule a shape out.  Results are cached per class
  *    (precision, lattice, interpolation order, split, 1-D or 2-D, boundaries, and nx, ny
  *    rounded up to powers of two) for the life of the process: a later call for the same

@@ -1,6 +1,7 @@
 // C-ABI of libpond (declared in include/pond.h): configuration checks, workspace layout,
 // the time-step loop and host <-> device transfers.  No device memory is allocated here:
 // the caller provides the workspace.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1024,8 +1025,8 @@ extern "C" int pond_autotune(pond_sim* s, void* dev_scratch, size_t bytes, int32
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     int rc = cuda_status(e);
-    double best = 0.0;
-    int bx = 0, by = 0, bh = 0, tried = 0;
+    struct Trial { double ms; int tx, ty, halo; };
+    std::vector<Trial> trials;
     const int ntiles = s->one_d ? 1 : 5;
     for (int ti = 0; ti < ntiles && rc == POND_OK; ++ti) {
         const int tx = s->one_d ? 0 : tiles2d[ti][0], ty = s->one_d ? 0 : tiles2d[ti][1];
@@ -1034,15 +1035,28 @@ extern "C" int pond_autotune(pond_sim* s, void* dev_scratch, size_t bytes, int32
             const int r = time_shape(s, dev_scratch, bytes, tx, ty, halos[hi], steps, e0, e1, &ms);
             if (r == POND_ECUDA) rc = r;           // a runtime failure ends the search
             if (r != POND_OK) continue;            // shape ruled out (shared memory, state)
-            ++tried;
-            if (tried == 1 || ms < best) {
-                best = ms;
-                bx = s->one_d ? kStepThreads : tx;
-                by = s->one_d ? 1 : ty;
-                bh = halos[hi];
-            }
+            trials.push_back(Trial{ms, tx, ty, halos[hi]});
         }
     }
+    // the candidates lie within a few per cent of each other: time the three fastest twice
+    // more and keep each one's best, so that one noisy trial does not decide
+    std::sort(trials.begin(), trials.end(), [](const Trial& a, const Trial& b) { return a.ms < b.ms; });
+    const size_t finalists = std::min<size_t>(3, trials.size());
+    for (int rep = 0; rep < 2 && rc == POND_OK && finalists > 1; ++rep)
+        for (size_t k = 0; k < finalists && rc == POND_OK; ++k) {
+            double ms = 0.0;
+            const int r = time_shape(s, dev_scratch, bytes, trials[k].tx, trials[k].ty, trials[k].halo, steps,
+                                     e0, e1, &ms);
+            if (r == POND_ECUDA) rc = r;
+            if (r == POND_OK) trials[k].ms = std::min(trials[k].ms, ms);
+        }
+    std::sort(trials.begin(), trials.begin() + finalists,
+              [](const Trial& a, const Trial& b) { return a.ms < b.ms; });
+    const int tried = (int)trials.size();
+    const double best = tried ? trials[0].ms : 0.0;
+    const int bx = tried ? (s->one_d ? kStepThreads : trials[0].tx) : 0;
+    const int by = tried ? (s->one_d ? 1 : trials[0].ty) : 0;
+    const int bh = tried ? trials[0].halo : 0;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (rc != POND_OK) return rc;

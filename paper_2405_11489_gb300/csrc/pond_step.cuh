@@ -556,21 +556,22 @@ __device__ __forceinline__ RefState<R> tile_reference(const CaseRun& p, int TX, 
     rf.ux = p.mac_in[N + c];
     rf.uy = p.mac_in[2 * N + c];
     rf.T = p.mac_in[3 * N + c];
-    const double P = rf.rho * rf.T;
-    const double Etot = rf.rho * (p.cv * rf.T + 0.5 * (rf.ux * rf.ux + rf.uy * rf.uy));
-    // B_00 of g's equilibrium, and the energy per mass whose balance gives T
-    const double E = p.split == 0 ? Etot : (p.split == 1 ? p.cv * P : (p.cv - 1.0) * P);
-    const double e = p.split == 1 ? p.cv * rf.T : Etot / rf.rho;
     rf.rhoR = R(rf.rho);
     rf.uxR = R(rf.ux);
     rf.uyR = R(rf.uy);
     rf.TR = R(rf.T);
-    rf.ER = R(E);
-    rf.PR = R(P);
-    rf.eR = R(e);
-    rf.isT = R(1.0 / sqrt(rf.T));
-    rf.invT = R(1.0 / rf.T);
     rf.cvR = R(p.cv);
+    // B_00 of g's equilibrium, and the energy per mass whose balance gives T.  One thread
+    // computes these while the block waits, so the reduced precisions take them in R: at the
+    // FP64 rate of this part a double division or square root costs the block about a
+    // microsecond, and the values are rounded to R anyway.
+    const R P = rf.rhoR * rf.TR;
+    const R e_tot = rf.cvR * rf.TR + R(0.5) * (rf.uxR * rf.uxR + rf.uyR * rf.uyR);
+    rf.ER = p.split == 0 ? rf.rhoR * e_tot : (p.split == 1 ? rf.cvR * P : (rf.cvR - R(1)) * P);
+    rf.PR = P;
+    rf.eR = p.split == 1 ? rf.cvR * rf.TR : e_tot;
+    rf.isT = R(1) / sqrt_r<R>(rf.TR);
+    rf.invT = R(1) / rf.TR;
     return rf;
 }
 
