@@ -578,7 +578,8 @@ __device__ __forceinline__ RefState<R> tile_reference(const CaseRun& p, int TX, 
 // Interpolation footprint of the tile (all threads of the block call it; nodes may appear in
 // several threads): the box of source nodes that covers the stencils of every node's departure
 // points under its previous frame, plus a margin for the frame to move during the iterations.
-// Writes box = {x0, y0, width, height}, the size clipped to the staged capacity.
+// Writes box = {x0, y0, width, height} (each thread its own copy), the size clipped to the
+// staged capacity.
 template <bool ONE_D, int NW>
 __device__ __forceinline__ void footprint_box(const CaseRun& p, const StepParams& pp, int TX, int TY,
                                               bool active, double ux0, double uy0, double T0,
@@ -602,23 +603,22 @@ __device__ __forceinline__ void footprint_box(const CaseRun& p, const StepParams
         red[0][warp] = lx; red[1][warp] = hx; red[2][warp] = ly; red[3][warp] = hy;
     }
     __syncthreads();
-    if (tid == 0) {
-        for (int w = 1; w < NW; ++w) {
-            lx = fminf(lx, red[0][w]); hx = fmaxf(hx, red[1][w]);
-            ly = fminf(ly, red[2][w]); hy = fmaxf(hy, red[3][w]);
-        }
-        const float margin = 0.5f;   // room for the frame to move during the iterations
-        // taps of a departure offset `off` lie in [floor(off) - 1, floor(off) + 2]
-        int x_lo = (int)floorf(fmaxf(lx - margin, -1e6f)) - 1;
-        int x_hi = (TX - 1) + (int)floorf(fminf(hx + margin, 1e6f)) + 2;
-        int y_lo = (int)floorf(fmaxf(ly - margin, -1e6f)) - 1;
-        int y_hi = (TY - 1) + (int)floorf(fminf(hy + margin, 1e6f)) + 2;
-        box[0] = p.tile_x * TX + x_lo;
-        box[1] = ONE_D ? 0 : p.tile_y * TY + y_lo;
-        box[2] = min(x_hi - x_lo + 1, pp.box_w);
-        box[3] = ONE_D ? 1 : min(y_hi - y_lo + 1, pp.box_h);
+    // every thread combines the warps' extremes itself (broadcast reads; no second barrier)
+    lx = red[0][0]; hx = red[1][0]; ly = red[2][0]; hy = red[3][0];
+    for (int w = 1; w < NW; ++w) {
+        lx = fminf(lx, red[0][w]); hx = fmaxf(hx, red[1][w]);
+        ly = fminf(ly, red[2][w]); hy = fmaxf(hy, red[3][w]);
     }
-    __syncthreads();
+    const float margin = 0.5f;   // room for the frame to move during the iterations
+    // taps of a departure offset `off` lie in [floor(off) - 1, floor(off) + 2]
+    const int x_lo = (int)floorf(fmaxf(lx - margin, -1e6f)) - 1;
+    const int x_hi = (TX - 1) + (int)floorf(fminf(hx + margin, 1e6f)) + 2;
+    const int y_lo = (int)floorf(fmaxf(ly - margin, -1e6f)) - 1;
+    const int y_hi = (TY - 1) + (int)floorf(fminf(hy + margin, 1e6f)) + 2;
+    box[0] = p.tile_x * TX + x_lo;
+    box[1] = ONE_D ? 0 : p.tile_y * TY + y_lo;
+    box[2] = min(x_hi - x_lo + 1, pp.box_w);
+    box[3] = ONE_D ? 1 : min(y_hi - y_lo + 1, pp.box_h);
 }
 
 // Frame of the final moments lambda* and the maps of the collision (Sec. III.A, collision in the
@@ -732,7 +732,6 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
     __shared__ float red[4][TPB / 32];
-    __shared__ int box[4];
     __shared__ LatRow<R> lat[Q1];
     __shared__ RefState<R> srf;
     __shared__ CaseRun scase;
@@ -763,8 +762,9 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     __syncthreads();
     const RefState<R>& rf = srf;
     const R sTr = R(1) / rf.isT;
+    int box[4];
     footprint_box<ONE_D, TPB / 32>(p, pp, TX, TY, active, ux0, uy0, T0, red, box, tid);
-    const int ox = box[0], oy = box[1], bw = box[2], bh = box[3];
+    const int ox = box[0], oy = box[1], bw = box[2], bh = box[3];   // this thread's copy
     const int bn = bw * bh;
 
     // ---- staging: source deviations in the reference frame --------------------------------
@@ -782,16 +782,19 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     int k = 0;
     bool bad = false, nonconv = false;
     unsigned int fallbacks = 0;
-    double ubx = ux0, uby = uy0, Tb = T0;
     double unx = ux0, uny = uy0, Tn = T0;
     R drho = R(0), dubx = R(0), duby = R(0), durx = R(0), dury = R(0), dTr = R(0), dTb = R(0);
     R Af[NC], Ag[NC];         // deviation coefficients of the streamed populations in lambda_bar
 
     if (active) {
+        // frame of the iteration relative to the reference: FP64 differences once, then each
+        // corrector takes the new moments' deviations (u - u_r, T - T_r) already in R; the
+        // frame's change over the iterations is summed in R and added to the FP64 frame at
+        // the end, so the loop itself has no FP64 operation
+        R rbx = R(rf.ux - ux0), rby = R(rf.uy - uy0);              // u_r - u_bar
+        R rbT = R(rf.T - T0);                                      // T_r - T_bar
+        R sum_dux = R(0), sum_duy = R(0);                          // u - u_bar, summed
         while (true) {
-            // frame of this iteration relative to the reference (FP64 adds only)
-            const R rbx = R(rf.ux - ubx), rby = R(rf.uy - uby);   // u_r - u_bar
-            const R rbT = R(rf.T - Tb);                            // T_r - T_bar
             const R sT = sqrt_r<R>(rf.TR - rbT);                   // sqrt(T_bar)
             const R isT = R(1) / sT;
             const R iTb = isT * isT;
@@ -1015,11 +1018,13 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                 cvdT -= R(0.5) * (durx * (R(2) * rf.uxR + durx) + dury * (R(2) * rf.uyR + dury));
             dTr = cvdT * R(p.inv_cv);                                 // T - T_r
             dTb = dTr + rbT;                                          // T - T_bar
-            unx = ubx + (double)dubx;
-            uny = uby + (double)duby;
-            Tn = rf.T + (double)dTr;
+            sum_dux += dubx;
+            sum_duy += duby;
             ++k;
-            if (!(rhoR > R(0)) || !(Tn > 0.0) || isnan(unx) || isnan(uny)) { bad = true; break; }
+            if (!(rhoR > R(0)) || !(rf.TR + dTr > R(0)) || isnan(sum_dux) || isnan(sum_duy)) {
+                bad = true;
+                break;
+            }
             const float du = sqrtf((float)(dubx * dubx + duby * duby));
             const float change = fmaxf(du * (float)isT, fabsf((float)(dTb * iTb)));
             bool stop;
@@ -1028,8 +1033,12 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
             else if (k >= p.pc_max_iter) { stop = true; nonconv = true; }
             else stop = false;
             if (stop) break;
-            ubx = unx; uby = uny; Tb = Tn;                       // corrector
+            rbx = -durx; rby = -dury; rbT = -dTr;                // corrector: lambda_bar <- lambda
         }
+        unx = ux0 + (double)sum_dux;
+        uny = uy0 + (double)sum_duy;
+        Tn = rf.T + (double)dTr;
+        if (!(Tn > 0.0)) bad = true;
     }
 
     // ---- collision in the frame of the final moments and write-back ---------------------------
