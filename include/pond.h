@@ -27,7 +27,9 @@
  *  - Ownership: the caller owns every buffer it passes in (host or device), including the
  *    device workspace given to pond_create.  The library copies inputs, never keeps a
  *    pointer to a caller's input or output buffer beyond the call, and never frees caller
- *    memory.  pond_create allocates only the small host-side handle.
+ *    memory.  pond_create allocates only the small host-side handle; the first
+ *    synchronising call of a host thread allocates a 64-byte page-locked mirror of the
+ *    status block for that thread's reads (kept for the thread's life).
  *  - Streams: all device work of a simulation is enqueued on the CUDA stream given to
  *    pond_create (NULL = the legacy default stream).
  *  - Thread safety: one pond_sim per host thread, or external synchronisation.
@@ -127,9 +129,10 @@ int pond_create(const pond_config *cfg, void *dev_workspace, size_t bytes, void 
 
 /* Set the macroscopic state: equilibrium populations f_i = rho w_i, g_i = g_eq_i in each
  * node's own frame (Sec. III.A).  rho, ux, uy, T: [ny][nx] doubles, host pointers
- * (on_device = 0) or device pointers (on_device = 1).  Requires rho > 0, T > 0
- * (checked on the host for host input; device input is checked by the next step).
- * Resets statistics and the sticky status. */
+ * (on_device = 0) or device pointers (on_device = 1).  Requires rho > 0, T > 0 and finite
+ * values: host input is checked after its copy to the device and before it replaces the
+ * state (POND_EINVAL, state unchanged; the call synchronises the stream for this); device
+ * input is checked by the next step.  Resets statistics and the sticky status. */
 int pond_set_state(pond_sim *sim, const double *rho, const double *ux, const double *uy,
                    const double *T, int on_device);
 

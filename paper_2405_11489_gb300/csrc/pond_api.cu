@@ -248,21 +248,48 @@ int cuda_status(cudaError_t e)
     return POND_ECUDA;
 }
 
+// Zero the status block (first_bad = ~0: none), on the stream, without a host copy.
 int reset_status(pond_sim* s)
 {
-    DevStatus z;
-    std::memset(&z, 0, sizeof(z));
-    z.first_bad = ~0ull;
     s->steps = 0;
-    return cuda_status(cudaMemcpyAsync(status_ptr(s), &z, sizeof(z), cudaMemcpyHostToDevice, s->stream));
+    DevStatus* st = status_ptr(s);
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&st->first_bad, 0xff, sizeof(st->first_bad), s->stream);
+    return cuda_status(e);
+}
+
+// Page-locked mirror of a status block for the synchronising reads of this host thread
+// (a copy into pageable memory goes through a staging buffer and costs several times a
+// small pinned copy).  Allocated at the thread's first synchronising call and kept; null
+// if the allocation failed, and the reads then go to pageable memory.
+DevStatus* pinned_status_mirror()
+{
+    static thread_local DevStatus* mirror = nullptr;
+    static thread_local bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        if (cudaMallocHost(&p, sizeof(DevStatus)) == cudaSuccess) mirror = static_cast<DevStatus*>(p);
+        else cudaGetLastError();
+    }
+    return mirror;
+}
+
+// Copy the status block to s->host_status and synchronise the stream.
+cudaError_t read_status(pond_sim* s)
+{
+    DevStatus* m = pinned_status_mirror();
+    DevStatus* dst = m ? m : &s->host_status;
+    cudaError_t e = cudaMemcpyAsync(dst, status_ptr(s), sizeof(DevStatus), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess && m) std::memcpy(&s->host_status, m, sizeof(DevStatus));
+    return e;
 }
 
 // Synchronise and translate the sticky device status.
 int sync_status(pond_sim* s)
 {
-    cudaError_t e = cudaMemcpyAsync(&s->host_status, status_ptr(s), sizeof(DevStatus),
-                                    cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaError_t e = read_status(s);
     if (e != cudaSuccess) return cuda_status(e);
     if (s->host_status.flags & 1) return POND_ENONPHYSICAL;
     if (s->host_status.flags & 2) return POND_ENOCONV;
@@ -452,17 +479,20 @@ int pond_set_boundary_profile(pond_sim* s, int32_t side, const double* state, in
     return write_profile(s, side, state, on_device);
 }
 
-// Host check of primitive fields: rho > 0 and T > 0 finite, u finite.  Branch-free over the
-// nodes (x - x is 0 exactly for finite x and NaN otherwise), so the loop vectorises.
-static bool physical_fields(const double* rho, const double* ux, const double* uy, const double* T,
-                            long long N)
+// Status flag of a rejected host input (bit 2; bits 0 and 1 are the kernels' statuses).
+constexpr int kInputBad = 4;
+
+// Host input of pond_set_state, staged as [4][N] (rho, u_x, u_y, T): sets kInputBad when a
+// node has rho <= 0, T <= 0 or a value that is not finite.  One flag write per warp.
+__global__ void check_fields_kernel(const double* mac, long long N, DevStatus* st)
 {
-    const double inf = HUGE_VAL;
-    bool ok = true;
-    for (long long n = 0; n < N; ++n)
-        ok &= (rho[n] > 0.0) & (rho[n] < inf) & (T[n] > 0.0) & (T[n] < inf) &
-              (ux[n] - ux[n] == 0.0) & (uy[n] - uy[n] == 0.0);
-    return ok;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (n < N) {
+        const double r = mac[n], ux = mac[N + n], uy = mac[2 * N + n], T = mac[3 * N + n];
+        bad = !(r > 0.0) || !(T > 0.0) || !isfinite(r) || !isfinite(T) || !isfinite(ux) || !isfinite(uy);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->flags, kInputBad);
 }
 
 int pond_set_state(pond_sim* s, const double* rho, const double* ux, const double* uy, const double* T,
@@ -474,13 +504,22 @@ int pond_set_state(pond_sim* s, const double* rho, const double* ux, const doubl
     if (rc != POND_OK) return rc;
     const double *drho = rho, *dux = ux, *duy = uy, *dT = T;
     if (!on_device) {
-        if (!physical_fields(rho, ux, uy, T, N)) return POND_EINVAL;
         double* stage = mac_ptr(s, 1 - s->cur);   // the idle frame buffer stages the input
         const double* src[4] = {rho, ux, uy, T};
         for (int k = 0; k < 4; ++k) {
             cudaError_t e = cudaMemcpyAsync(stage + k * N, src[k], N * sizeof(double),
                                             cudaMemcpyHostToDevice, s->stream);
             if (e != cudaSuccess) return cuda_status(e);
+        }
+        // the check reads the copy where it landed: the host's single core would take far
+        // longer over the same bytes than the copy itself
+        check_fields_kernel<<<(unsigned int)((N + 255) / 256), 256, 0, s->stream>>>(stage, N, status_ptr(s));
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = read_status(s);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (s->host_status.flags & kInputBad) {
+            rc = reset_status(s);
+            return rc != POND_OK ? rc : POND_EINVAL;
         }
         drho = stage; dux = stage + N; duy = stage + 2 * N; dT = stage + 3 * N;
     }

@@ -286,7 +286,7 @@ struct DevStatus {
     unsigned long long fallbacks;
     unsigned long long first_bad;    // atomicMin; ~0ull when none
     unsigned int iters_max;
-    int flags;                        // bit 0 non-physical, bit 1 non-convergence
+    int flags;                        // bit 0 non-physical, bit 1 non-convergence, bit 2 rejected host input
     unsigned long long steps;
     unsigned long long pad[2];
 };
