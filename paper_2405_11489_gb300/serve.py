@@ -209,9 +209,19 @@ class PondBackend:
 
     def create(self, req):
         key = self.class_key(req)
-        sim = self.pond.Simulation(self.config(req), device=self.device, stream=self._stream(key))
+        stream = self._stream(key)
+        sim = self.pond.Simulation(self.config(req), device=self.device, stream=stream)
         c = req.case
-        sim.set_state(c.rho, c.ux, c.uy, c.T)
+        # the fields go to the device on the class's stream and pond_set_state takes device
+        # input, which does not synchronise: admitting a request never waits for the class's
+        # chunk in flight (host input would be checked first, and the check waits for the
+        # stream).  The generator's fields are physical; a bad value would show in the
+        # request's status after its first step.
+        torch = self.torch
+        with torch.cuda.stream(stream):
+            fields = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(self.device, non_blocking=True)
+                      for a in (c.rho, c.ux, c.uy, c.T)]
+            sim.set_state(*fields)
         return sim
 
     def advance(self, key, sims, n):
