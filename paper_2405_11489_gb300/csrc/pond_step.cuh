@@ -835,7 +835,9 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                     // FP32, N = 3: both distributions in one pass over the rows (each record is
                     // five 16-byte loads and the row overhead is shared); otherwise one pass each
                     constexpr int ND = (std::is_same<R, float>::value && NG == 3) ? 2 : 1;
-#pragma unroll
+                    // one pass each (ND = 1) share their code: unrolled, the two passes kept
+                    // both sets of row temporaries live and spilled on D2Q25 (702 -> 534 us)
+#pragma unroll 1
                     for (int d0 = 0; d0 < 2; d0 += ND) {
                         // x pass once per row of the union of the y stencils, folded into Z_q,
                         // then added to the b's whose y stencil contains the row
