@@ -174,6 +174,19 @@ void side_profiles(pond_sim* s, const double* prof[4])
 
 int cuda_status(cudaError_t e);
 
+// Blocks of the step kernel resident at once on the current device: one per SM (255
+// registers x 256 threads fill an SM's register file).  0 if the query fails.
+int resident_step_blocks()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms;
+}
+
 // Copy states [n][4] (host or device) into side w's profile, or its uniform state when
 // state is null.  Host states are checked (T > 0, rho > 0, finite).
 int write_profile(pond_sim* s, int w, const double* state, int on_device)
@@ -547,6 +560,7 @@ int pond_step(pond_sim* s, int32_t nsteps)
     p.lat = s->lat;
     p.box_w = s->box_w;
     p.box_h = s->box_h;
+    p.ahead = resident_step_blocks();
     const double* prof[4];
     side_profiles(s, prof);
     fill_case(c, status_ptr(s), p.one, prof);
@@ -716,6 +730,7 @@ cudaError_t batch_launch_step(pond_batch* b)
     p.lat = s0->lat;
     p.box_w = s0->box_w;
     p.box_h = s0->box_h;
+    p.ahead = resident_step_blocks();
     p.flip = b->flip;
     p.ncase = b->count;
     p.cases = b->d_cases;

@@ -61,6 +61,7 @@ struct StepParams {
     int box_w, box_h;           // staged box capacity (nodes)
     int flip;                   // the input state is buffer cur ^ flip, the output the other one
     int ncase;                  // 0: the single case `one`; > 0: `cases` (batched launch)
+    int ahead;                  // blocks resident at once (one wave); 0: no L2 prefetch
     CaseDesc one;
     const CaseDesc* cases;
     const int* tile_start;      // [ncase + 1]: first tile of each case, total at the end
@@ -724,6 +725,55 @@ __device__ __forceinline__ void report_stats(DevStatus* st, int tid, unsigned in
     }
 }
 
+// Warms L2 with the state that the block one wave later (pp.ahead launch positions on) will
+// stage: the rows of the box capacity around its tile, clamped to its grid, in every frame and
+// non-equilibrium plane.  A prefetch is a hint; every address lies inside the case's arrays.
+template <class S, int NG, bool ONE_D>
+__device__ __forceinline__ void prefetch_next_wave(const StepParams& pp, int TX, int TY, int tid, int nthreads)
+{
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x + pp.ahead;
+    const CaseDesc* c;
+    long long tile;
+    if (pp.ncase > 0) {
+        if (b >= pp.tile_start[pp.ncase]) return;
+        int lo = 0, hi = pp.ncase - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pp.tile_start[mid] <= b) lo = mid; else hi = mid - 1;
+        }
+        c = pp.cases + lo;
+        tile = b - pp.tile_start[lo];
+    } else {
+        if (b >= (long long)gridDim.x * gridDim.y) return;
+        c = &pp.one;
+        tile = b;
+    }
+    const int tiles_x = pp.ncase > 0 ? c->tiles_x : (int)gridDim.x;
+    const int tx = (int)(tile % tiles_x), ty = (int)(tile / tiles_x);
+    const int nx = c->nx, ny = c->ny;
+    const long long N = c->N;
+    const int in = c->cur ^ pp.flip;
+    const char* mac = reinterpret_cast<const char*>(c->mac[in]);
+    const char* neq = reinterpret_cast<const char*>(c->neq[in]);
+    const int x0 = max(0, tx * TX - (pp.box_w - TX) / 2), x1 = min(nx - 1, tx * TX + TX - 1 + (pp.box_w - TX) / 2);
+    const int y0 = ONE_D ? 0 : max(0, ty * TY - (pp.box_h - TY) / 2);
+    const int y1 = ONE_D ? 0 : min(ny - 1, ty * TY + TY - 1 + (pp.box_h - TY) / 2);
+    if (x0 > x1 || y0 > y1) return;
+    const int rows = y1 - y0 + 1;
+    const int planes = NMAC + nneq(NG);
+    for (int k = tid; k < rows * planes; k += nthreads) {
+        const int plane = k / rows;
+        const long long first = (long long)(y0 + k % rows) * nx + x0;
+        const bool is_mac = plane < NMAC;
+        const size_t esz = is_mac ? sizeof(double) : sizeof(S);
+        const char* row = is_mac ? mac + ((long long)plane * N + first) * sizeof(double)
+                                 : neq + ((long long)(plane - NMAC) * N + first) * sizeof(S);
+        const size_t bytes = (size_t)(x1 - x0 + 1) * esz;
+        for (size_t off = 0; off < bytes; off += 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
+    }
+}
+
 // Single-thread-per-node kernel: FP64 arithmetic (2-D and quasi-1-D) and the FP32 quasi-1-D
 // grids.  One CTA per tile of TPB nodes.
 template <class S, class R, int Q1, int P, bool ONE_D, int TPB>
@@ -777,6 +827,7 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
         store_rec<R, NG>(sm + (size_t)i * REC, D, D + NC);
     }
     __syncthreads();
+    if (pp.ahead > 0) prefetch_next_wave<S, NG, ONE_D>(pp, TX, TY, tid, TPB);
 
     // ---- predictor-corrector ---------------------------------------------------------------
     int k = 0;
