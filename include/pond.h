@@ -216,6 +216,21 @@ int pond_batch_workspace_bytes(int32_t count, size_t *bytes);
 int pond_batch_create(pond_sim *const *sims, int32_t count, void *dev_workspace, size_t bytes,
                       void *cuda_stream, pond_batch **out);
 int pond_batch_step(pond_batch *batch, int32_t nsteps);
+/* pond_set_state for every member at once: rho[i], ux[i], uy[i], T[i] are member i's
+ * [ny][nx] fields (count pointers each, host or device as on_device says).  The same checks
+ * and effects as pond_set_state on each member, on the batch's stream and ordered with the
+ * members' streams like pond_batch_step; host input is checked after its copy with one
+ * synchronisation for the whole batch, and if any member's input is rejected no member's
+ * state changes (POND_EINVAL). */
+int pond_batch_set_state(pond_batch *batch, const double *const *rho, const double *const *ux,
+                         const double *const *uy, const double *const *T, int on_device);
+/* pond_get_moments for every member at once (any of the four pointer arrays may be NULL, and
+ * any member's pointer in them): one synchronisation of the batch's stream for all members;
+ * returns the worst member status (POND_ENONPHYSICAL before POND_ENOCONV), each member's own
+ * status stays available through pond_get_stats.  pond_batch_create allocates a page-locked
+ * array of count status blocks for this read-back. */
+int pond_batch_get_moments(pond_batch *batch, double *const *rho, double *const *ux,
+                           double *const *uy, double *const *T, int on_device);
 int pond_batch_use_graph(pond_batch *batch, int32_t steps_per_graph);
 int pond_batch_destroy(pond_batch *batch);
 

@@ -709,6 +709,8 @@ struct pond_batch {
     std::vector<cudaStream_t> member_streams;   // distinct member streams other than `stream`
     std::vector<cudaEvent_t> member_events;     // one per member stream
     cudaEvent_t done;                           // recorded on `stream` after each batch call
+    DevStatus* h_status;                        // page-locked, one per member (null: pageable)
+    std::vector<DevStatus> h_status_pageable;
 };
 
 namespace {
@@ -854,6 +856,12 @@ extern "C" int pond_batch_create(pond_sim* const* sims, int32_t count, void* dev
     b->graph_flip = 0;
     b->graph = nullptr;
     b->done = nullptr;
+    b->h_status = nullptr;
+    {
+        void* hp = nullptr;   // the members' status blocks, read back in one synchronisation
+        if (cudaMallocHost(&hp, count * sizeof(DevStatus)) == cudaSuccess) b->h_status = static_cast<DevStatus*>(hp);
+        else { cudaGetLastError(); b->h_status_pageable.resize(count); }
+    }
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < count; ++i) {
         cudaStream_t ms = sims[i]->stream;
@@ -880,6 +888,7 @@ extern "C" int pond_batch_create(pond_sim* const* sims, int32_t count, void* dev
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         batch_destroy_events(b);
+        if (b->h_status) cudaFreeHost(b->h_status);
         delete b;
         return cuda_status(e);
     }
@@ -952,8 +961,116 @@ extern "C" int pond_batch_destroy(pond_batch* b)
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     batch_destroy_events(b);
+    if (b->h_status) cudaFreeHost(b->h_status);
     delete b;
     return cuda_status(e);
+}
+
+namespace {
+
+// Read every member's status block into its handle with one synchronisation of the batch's
+// stream; returns the worst sticky status (non-physical before non-convergence).
+int batch_read_status(pond_batch* b, bool* input_bad)
+{
+    DevStatus* h = b->h_status ? b->h_status : b->h_status_pageable.data();
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < b->count && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(h + i, status_ptr(b->sims[i]), sizeof(DevStatus), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = POND_OK;
+    if (input_bad) *input_bad = false;
+    for (int i = 0; i < b->count; ++i) {
+        b->sims[i]->host_status = h[i];
+        if (input_bad && (h[i].flags & kInputBad)) *input_bad = true;
+        if (h[i].flags & 1) rc = POND_ENONPHYSICAL;
+        else if ((h[i].flags & 2) && rc == POND_OK) rc = POND_ENOCONV;
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int pond_batch_set_state(pond_batch* b, const double* const* rho, const double* const* ux,
+                                    const double* const* uy, const double* const* T, int on_device)
+{
+    if (!b || !rho || !ux || !uy || !T) return POND_EINVAL;
+    for (int i = 0; i < b->count; ++i)
+        if (!rho[i] || !ux[i] || !uy[i] || !T[i]) return POND_EINVAL;
+    cudaError_t e = batch_wait_members(b);
+    if (e != cudaSuccess) return cuda_status(e);
+    std::vector<const double*> src(4 * (size_t)b->count);
+    for (int i = 0; i < b->count; ++i) {
+        pond_sim* s = b->sims[i];
+        const long long N = (long long)s->cfg.nx * s->cfg.ny;
+        s->steps = 0;
+        DevStatus* st = status_ptr(s);
+        e = cudaMemsetAsync(st, 0, sizeof(DevStatus), b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&st->first_bad, 0xff, sizeof(st->first_bad), b->stream);
+        const double* in[4] = {rho[i], ux[i], uy[i], T[i]};
+        if (!on_device) {   // stage in the idle frame buffer and check it there
+            double* stage = mac_ptr(s, 1 - s->cur);
+            for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+                e = cudaMemcpyAsync(stage + k * N, in[k], N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+            if (e == cudaSuccess) {
+                check_fields_kernel<<<(unsigned int)((N + 255) / 256), 256, 0, b->stream>>>(stage, N, st);
+                e = cudaGetLastError();
+            }
+            for (int k = 0; k < 4; ++k) src[4 * i + k] = stage + k * N;
+        } else {
+            for (int k = 0; k < 4; ++k) src[4 * i + k] = in[k];
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (!on_device) {   // one synchronisation for every member's check
+        bool bad = false;
+        const int rc = batch_read_status(b, &bad);
+        if (rc == POND_ECUDA) return rc;
+        if (bad) {
+            for (int i = 0; i < b->count; ++i) {
+                const int r = reset_status(b->sims[i]);
+                if (r != POND_OK) return r;
+            }
+            return POND_EINVAL;
+        }
+    }
+    for (int i = 0; i < b->count; ++i) {
+        pond_sim* s = b->sims[i];
+        AuxParams a = aux_params(s, s->cur);
+        e = POND_BY_PRECISION(s->cfg.precision, init, a, src[4 * i], src[4 * i + 1], src[4 * i + 2],
+                              src[4 * i + 3], b->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return cuda_status(batch_release_members(b));
+}
+
+extern "C" int pond_batch_get_moments(pond_batch* b, double* const* rho, double* const* ux, double* const* uy,
+                                      double* const* T, int on_device)
+{
+    if (!b) return POND_EINVAL;
+    cudaError_t e = batch_wait_members(b);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int i = 0; i < b->count; ++i) {
+        pond_sim* s = b->sims[i];
+        const long long N = (long long)s->cfg.nx * s->cfg.ny;
+        double* dst[4] = {rho ? rho[i] : nullptr, ux ? ux[i] : nullptr, uy ? uy[i] : nullptr, T ? T[i] : nullptr};
+        AuxParams a = aux_params(s, s->cur);
+        if (on_device) {
+            e = POND_BY_PRECISION(s->cfg.precision, moments, a, dst[0], dst[1], dst[2], dst[3], b->stream);
+        } else {
+            double* stage = mac_ptr(s, 1 - s->cur);
+            e = POND_BY_PRECISION(s->cfg.precision, moments, a, stage, stage + N, stage + 2 * N, stage + 3 * N,
+                                  b->stream);
+            for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+                if (dst[k])
+                    e = cudaMemcpyAsync(dst[k], stage + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    const int rc = batch_read_status(b, nullptr);
+    if (rc == POND_ECUDA) return rc;
+    e = batch_release_members(b);
+    return e != cudaSuccess ? cuda_status(e) : rc;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -41,7 +41,8 @@ EXPORTS = ("pond_config_default", "pond_workspace_bytes", "pond_create", "pond_s
            "pond_state_bytes", "pond_export_state", "pond_import_state", "pond_step_static",
            "pond_batch_workspace_bytes", "pond_batch_create", "pond_batch_step",
            "pond_batch_use_graph", "pond_batch_destroy", "pond_get_launch", "pond_set_launch",
-           "pond_autotune", "pond_autotune_clear", "pond_set_boundary_profile")
+           "pond_autotune", "pond_autotune_clear", "pond_set_boundary_profile",
+           "pond_batch_set_state", "pond_batch_get_moments")
 POND_TUNE_APPLY, POND_TUNE_RETIME = 1, 2
 
 
@@ -110,6 +111,8 @@ def load_library(path: str = LIB_PATH):
         lib.pond_batch_workspace_bytes.argtypes = [i32, P(sz)]
         lib.pond_batch_create.argtypes = [P(vp), i32, vp, sz, vp, P(vp)]
         lib.pond_batch_step.argtypes = [vp, i32]
+        lib.pond_batch_set_state.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), ctypes.c_int]
+        lib.pond_batch_get_moments.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), ctypes.c_int]
         lib.pond_batch_use_graph.argtypes = [vp, i32]
         lib.pond_batch_destroy.argtypes = [vp]
         lib.pond_get_launch.argtypes = [vp, P(pond_tuning)]
@@ -229,6 +232,23 @@ def pond_batch_create(handles, workspace_ptr: int, nbytes: int, stream_ptr: int)
                                             ctypes.c_void_p(stream_ptr), ctypes.byref(h)),
            "pond_batch_create")
     return h.value
+
+
+def _ptr_array(ptrs):
+    if ptrs is None:
+        return None
+    return (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(p) if p else None for p in ptrs])
+
+
+def pond_batch_set_state(h, rho, ux, uy, T, on_device: int) -> int:
+    """rho, ux, uy, T: sequences of member pointers (ints)."""
+    return load_library().pond_batch_set_state(h, _ptr_array(rho), _ptr_array(ux), _ptr_array(uy),
+                                               _ptr_array(T), on_device)
+
+
+def pond_batch_get_moments(h, rho, ux, uy, T, on_device: int) -> int:
+    return load_library().pond_batch_get_moments(h, _ptr_array(rho), _ptr_array(ux), _ptr_array(uy),
+                                                 _ptr_array(T), on_device)
 
 
 def pond_batch_step(h, nsteps: int) -> int:
@@ -533,6 +553,36 @@ class Batch:
     def step(self, n: int = 1):
         with self.torch.cuda.device(self.device):
             _check(pond_batch_step(self.handle, n), "pond_batch_step")
+
+    def set_state(self, fields):
+        """fields: one (rho, ux, uy, T) per member, numpy arrays (host input, checked) or CUDA
+        float64 tensors (device input), shaped [ny][nx] of that member."""
+        torch = self.torch
+        cols, keep = [[], [], [], []], []
+        on_device = isinstance(fields[0][0], torch.Tensor)
+        for sim, f in zip(self.sims, fields):
+            shape = (sim.cfg.ny, sim.cfg.nx)
+            for k, a in enumerate(f):
+                if on_device:
+                    a = a.to(device=self.device, dtype=torch.float64).contiguous().reshape(shape)
+                    cols[k].append(_dptr(a))
+                else:
+                    a = np.ascontiguousarray(np.broadcast_to(a, shape), dtype=np.float64)
+                    cols[k].append(a.ctypes.data)
+                keep.append(a)
+        with torch.cuda.device(self.device):
+            rc = pond_batch_set_state(self.handle, *cols, 1 if on_device else 0)
+        self._keep = keep
+        _check(rc, "pond_batch_set_state")
+
+    def moments(self, allow=(POND_OK, POND_ENOCONV)):
+        """Every member's (rho, ux, uy, T) as float64 numpy arrays, one synchronisation."""
+        outs = [[np.empty((s.cfg.ny, s.cfg.nx)) for _ in range(4)] for s in self.sims]
+        cols = [[o[k].ctypes.data for o in outs] for k in range(4)]
+        with self.torch.cuda.device(self.device):
+            rc = pond_batch_get_moments(self.handle, *cols, 0)
+        _check(rc, "pond_batch_get_moments", allow=allow)
+        return [tuple(o) for o in outs]
 
     def close(self):
         if getattr(self, "handle", None):

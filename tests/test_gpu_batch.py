@@ -81,3 +81,56 @@ def test_batch_rejects_mismatched_members(pond):
     c = pond.Simulation(pond.Config(nx=32, ny=1, precision="fp32"))
     with pytest.raises(pond.PondError):
         pond.Batch([a, c])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_set_state_and_moments_equal_the_per_member_calls(pond, precision):
+    """pond_batch_set_state / pond_batch_get_moments (one synchronisation for all members)
+    give the same states and fields, bit for bit, as pond_set_state / pond_get_moments per
+    member, with host and with device input, before and after batched steps."""
+    import torch
+    cases = _grid_cases()
+    ref = _tube_sims(pond, cases, precision=precision)
+    for s in ref:
+        s.step(3)
+    sims = _tube_sims(pond, cases, precision=precision)     # states to be replaced
+    for s in sims:
+        s.step(2)
+    batch = pond.Batch(sims)
+    batch.set_state([(c.rho, c.ux, c.uy, c.T) for c in cases])
+    for got, s in zip(batch.moments(), _tube_sims(pond, cases, precision=precision)):
+        for x, y in zip(got, s.moments()):
+            assert np.array_equal(x, y)
+    batch.step(3)
+    for got, s in zip(batch.moments(), ref):
+        for x, y in zip(got, s.moments()):
+            assert np.array_equal(x, y)
+        assert s.stats()[1].steps == 3
+    for s in sims:
+        assert s.stats()[1].steps == 3
+    # device input
+    dev = [tuple(torch.as_tensor(a, device="cuda") for a in (c.rho, c.ux, c.uy, c.T)) for c in cases]
+    batch.set_state(dev)
+    batch.step(3)
+    for got, s in zip(batch.moments(), ref):
+        for x, y in zip(got, s.moments()):
+            assert np.array_equal(x, y)
+    batch.close()
+
+
+def test_batch_set_state_rejects_bad_host_input_and_changes_no_member(pond):
+    cases = _grid_cases()
+    sims = _tube_sims(pond, cases)
+    batch = pond.Batch(sims)
+    batch.step(2)
+    before = [s.export_state() for s in sims]
+    fields = [(c.rho.copy(), c.ux.copy(), c.uy.copy(), c.T.copy()) for c in cases]
+    fields[1][3][2, 5] = -1.0                                # one negative temperature
+    with pytest.raises(pond.PondError):
+        batch.set_state(fields)
+    for s, (mac, neq) in zip(sims, before):
+        m2, n2 = s.export_state()
+        assert np.array_equal(mac.cpu().numpy(), m2.cpu().numpy())
+        assert np.array_equal(neq.cpu().numpy(), n2.cpu().numpy())
+        assert s.stats()[0] == pond.POND_OK
+    batch.close()
