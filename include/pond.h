@@ -227,8 +227,9 @@ int pond_batch_set_state(pond_batch *batch, const double *const *rho, const doub
 /* pond_get_moments for every member at once (any of the four pointer arrays may be NULL, and
  * any member's pointer in them): one synchronisation of the batch's stream for all members;
  * returns the worst member status (POND_ENONPHYSICAL before POND_ENOCONV), each member's own
- * status stays available through pond_get_stats.  pond_batch_create allocates a page-locked
- * array of count status blocks for this read-back. */
+ * status stays available through pond_get_stats.  The first batched read-back of a host
+ * thread allocates a page-locked array of status blocks for it (grown to the largest batch
+ * and kept for the thread's life). */
 int pond_batch_get_moments(pond_batch *batch, double *const *rho, double *const *ux,
                            double *const *uy, double *const *T, int on_device);
 int pond_batch_use_graph(pond_batch *batch, int32_t steps_per_graph);

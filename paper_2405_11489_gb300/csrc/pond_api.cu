@@ -709,8 +709,7 @@ struct pond_batch {
     std::vector<cudaStream_t> member_streams;   // distinct member streams other than `stream`
     std::vector<cudaEvent_t> member_events;     // one per member stream
     cudaEvent_t done;                           // recorded on `stream` after each batch call
-    DevStatus* h_status;                        // page-locked, one per member (null: pageable)
-    std::vector<DevStatus> h_status_pageable;
+    std::vector<DevStatus> h_status_pageable;   // status read-back when no page-locked buffer
 };
 
 namespace {
@@ -856,12 +855,6 @@ extern "C" int pond_batch_create(pond_sim* const* sims, int32_t count, void* dev
     b->graph_flip = 0;
     b->graph = nullptr;
     b->done = nullptr;
-    b->h_status = nullptr;
-    {
-        void* hp = nullptr;   // the members' status blocks, read back in one synchronisation
-        if (cudaMallocHost(&hp, count * sizeof(DevStatus)) == cudaSuccess) b->h_status = static_cast<DevStatus*>(hp);
-        else { cudaGetLastError(); b->h_status_pageable.resize(count); }
-    }
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < count; ++i) {
         cudaStream_t ms = sims[i]->stream;
@@ -888,7 +881,6 @@ extern "C" int pond_batch_create(pond_sim* const* sims, int32_t count, void* dev
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         batch_destroy_events(b);
-        if (b->h_status) cudaFreeHost(b->h_status);
         delete b;
         return cuda_status(e);
     }
@@ -961,7 +953,6 @@ extern "C" int pond_batch_destroy(pond_batch* b)
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     batch_destroy_events(b);
-    if (b->h_status) cudaFreeHost(b->h_status);
     delete b;
     return cuda_status(e);
 }
@@ -970,9 +961,32 @@ namespace {
 
 // Read every member's status block into its handle with one synchronisation of the batch's
 // stream; returns the worst sticky status (non-physical before non-convergence).
+// Page-locked status blocks for the batch read-backs of this host thread, grown to the
+// largest batch seen and kept (allocating or freeing page-locked memory synchronises the
+// device, so a batch that is rebuilt often must not do it); null if the allocation fails.
+DevStatus* pinned_status_array(int count)
+{
+    static thread_local DevStatus* buf = nullptr;
+    static thread_local int cap = 0;
+    if (count <= cap) return buf;
+    void* p = nullptr;
+    if (cudaMallocHost(&p, (size_t)count * sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (buf) cudaFreeHost(buf);
+    buf = static_cast<DevStatus*>(p);
+    cap = count;
+    return buf;
+}
+
 int batch_read_status(pond_batch* b, bool* input_bad)
 {
-    DevStatus* h = b->h_status ? b->h_status : b->h_status_pageable.data();
+    DevStatus* h = pinned_status_array(b->count);
+    if (!h) {
+        b->h_status_pageable.resize(b->count);
+        h = b->h_status_pageable.data();
+    }
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < b->count && e == cudaSuccess; ++i)
         e = cudaMemcpyAsync(h + i, status_ptr(b->sims[i]), sizeof(DevStatus), cudaMemcpyDeviceToHost, b->stream);
