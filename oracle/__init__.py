@@ -245,9 +245,11 @@ def step_nodes(cfg: Config, st: State, xs, ys):
     fr = np.zeros((3, count))
     it = np.zeros(count, dtype=np.int32)
     I32 = ctypes.POINTER(ctypes.c_int32)
-    _lib_handle().or_step_nodes(ctypes.byref(cfg), _p(st.f), _p(st.g), _p(st.ux), _p(st.uy),
-                                _p(st.T), count, xs.ctypes.data_as(I32), ys.ctypes.data_as(I32),
-                                _p(fo), _p(go), _p(fr), it.ctypes.data_as(I32))
+    rc = _lib_handle().or_step_nodes(ctypes.byref(cfg), _p(st.f), _p(st.g), _p(st.ux), _p(st.uy),
+                                     _p(st.T), count, xs.ctypes.data_as(I32), ys.ctypes.data_as(I32),
+                                     _p(fo), _p(go), _p(fr), it.ctypes.data_as(I32))
+    if rc == -1:
+        raise ValueError("step_nodes: a node lies outside the %d x %d grid" % (cfg.nx, cfg.ny))
     return fo, go, (fr[0], fr[1], fr[2]), it
 
 

@@ -724,6 +724,8 @@ int or_step_nodes(const or_config *cfg, const double *f, const double *g, const 
                   const double *fuy, const double *fT, int count, const int32_t *xs,
                   const int32_t *ys, double *fo, double *go, double *frame, int32_t *iters)
 {
+    for (int k = 0; k < count; ++k)          /* nodes outside the grid are an error */
+        if (xs[k] < 0 || xs[k] >= cfg->nx || ys[k] < 0 || ys[k] >= cfg->ny) return -1;
     or_lattice L;
     make_lattice(cfg->q1, &L);
     or_src S = {cfg, &L, f, g, fux, fuy, fT};
