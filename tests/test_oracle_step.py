@@ -34,7 +34,7 @@ def _totals(orc, cfg, st):
 @pytest.mark.parametrize("split", ["total", "internal"])
 def test_uniform_supersonic_flow_stays_uniform(orc, lattice, split):
     """A uniform state at Ma = 3 is a fixed point of the whole step, converging in one
-    predictor-corrector iteration (the benchmark spec pin; Sec. III.A)."""
+    predictor-corrector iteration (Sec. III.A: the shifted lattice moves with the flow)."""
     gamma, T = 1.4, 0.6
     u = 3.0 * math.sqrt(gamma * T)
     cfg = orc.make_config(7, 5, lattice=lattice, split=split, gamma=gamma, mu=0.01)
