@@ -288,6 +288,8 @@ def config_rates(torch, pond, device, steps=6):
                                        / out["riemann_1024_internal_fp32"]["mlups"])
     dec = W.shear_wave(n=NX, ma=1.0, amp=0.05, gamma=GAMMA, mu=MU)
     out["decay_256_d2q16_fp32"] = rate(dec, 4 * steps)
+    out["decay_256_d2q16_fp16_storage"] = rate(dec, 4 * steps, precision="fp16")
+    out["decay_256_d2q16_bf16_storage"] = rate(dec, 4 * steps, precision="bf16")
     out["decay_256_d2q25_fp32"] = rate(dec, 4 * steps, lattice=25)
     out["d2q25_over_d2q16_time"] = (out["decay_256_d2q16_fp32"]["mlups"]
                                     / out["decay_256_d2q25_fp32"]["mlups"])
@@ -318,11 +320,11 @@ def mean_iters(sims):
 
 
 def l1_error(pond, device, stream, nsteps=200):
-    """Per-field relative L1 error of the mixed path against the FP64 path (which matches
-    the oracle to 1e-12 in the parity tests) on the Ma = 1 grid after nsteps."""
-    out = {}
+    """Per-field relative L1 error of the mixed paths (FP32 storage, and FP16 / BF16 storage
+    with FP32 arithmetic) against the FP64 path (which matches the oracle to 1e-12 in the
+    parity tests) on the Ma = 1 grid after nsteps."""
     res = {}
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "fp16", "bf16", "fp64"):
         s = pond.Simulation(pond.Config(nx=NX, ny=NY, precision=prec, gamma=GAMMA, mu=MU),
                             device=device, stream=stream)
         s.set_state(*case_fields(1.0))
@@ -330,13 +332,18 @@ def l1_error(pond, device, stream, nsteps=200):
         res[prec] = s.moments()
         s.close()
     names = ("rho", "ux", "uy", "T")
-    for n, a, b in zip(names, res["fp32"], res["fp64"]):
-        out[n] = float(np.mean(np.abs(a - b)) / np.mean(np.abs(b)))
-    # the perturbations themselves: error relative to the signal (deviation from the mean)
-    for n, a, b in zip(names, res["fp32"], res["fp64"]):
-        dev = np.mean(np.abs(b - b.mean()))
-        out[n + "_vs_signal"] = float(np.mean(np.abs(a - b)) / dev) if dev > 0 else None
-    return {"steps": nsteps, "rel_l1": out}
+
+    def errors(prec):
+        out = {}
+        for n, a, b in zip(names, res[prec], res["fp64"]):
+            out[n] = float(np.mean(np.abs(a - b)) / np.mean(np.abs(b)))
+        # the perturbations themselves: error relative to the signal (deviation from the mean)
+        for n, a, b in zip(names, res[prec], res["fp64"]):
+            dev = np.mean(np.abs(b - b.mean()))
+            out[n + "_vs_signal"] = float(np.mean(np.abs(a - b)) / dev) if dev > 0 else None
+        return out
+    return {"steps": nsteps, "rel_l1": errors("fp32"), "rel_l1_fp16_storage": errors("fp16"),
+            "rel_l1_bf16_storage": errors("bf16")}
 
 
 def decay_physics(torch, pond, device, steps=2000):
