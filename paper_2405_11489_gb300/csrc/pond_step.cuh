@@ -920,14 +920,23 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                                 for (int e = 0; e < ND; ++e) z_contract<R, NG>(phi, X[e], Z[e]);
 #pragma unroll
                                 for (int b = 0; b < Q1; ++b) {
-                                    // without a branch: a row outside b's stencil adds with weight 0
-                                    // (more FMAs, but the branch resolution cost more: 268 -> 262 us)
                                     const int j = r - jy[b];
-                                    const R w = ((unsigned)j < (unsigned)P) ? pick<R>(wy[b], j, P) : R(0);
+                                    if constexpr (std::is_same<R, float>::value) {
+                                        // FP32: no branch, a row outside b's stencil adds with weight
+                                        // 0 (more FMAs, but resolving the branch cost more: 268 ->
+                                        // 262 us); FP64 is bound by its pipe and keeps the branch
+                                        const R w = ((unsigned)j < (unsigned)P) ? pick<R>(wy[b], j, P) : R(0);
 #pragma unroll
-                                    for (int e = 0; e < ND; ++e)
+                                        for (int e = 0; e < ND; ++e)
 #pragma unroll
-                                        for (int q = 0; q <= NG; ++q) acc[e][b][q] += w * Z[e][q];
+                                            for (int q = 0; q <= NG; ++q) acc[e][b][q] += w * Z[e][q];
+                                    } else if ((unsigned)j < (unsigned)P) {
+                                        const R w = pick<R>(wy[b], j, P);
+#pragma unroll
+                                        for (int e = 0; e < ND; ++e)
+#pragma unroll
+                                            for (int q = 0; q <= NG; ++q) acc[e][b][q] += w * Z[e][q];
+                                    }
                                 }
                             }
                         } else {
