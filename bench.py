@@ -529,6 +529,47 @@ def run_reference(args, world, rank):
     return 0
 
 
+def profile_case(torch, pond, device, stream, flush, args):
+    """Batched steps of another configuration for a profiler: the four 256^2 decay grids on
+    D2Q25 (mixed FP32) or in plain FP64, or the 256 uneven tubes (3-point stencil, mixed
+    FP32), each with the launch shape the autotuner picks; prints one JSON line."""
+    if args.profile_case == "tubes":
+        cases = W.tube_batch(count=256, seed=1)
+        sims = []
+        for c in cases:
+            s = pond.Simulation(pond.Config(nx=c.nx, ny=c.ny, precision="fp32", gamma=c.gamma,
+                                            mu=c.mu, bc_x=c.bc_x, bc_y=c.bc_y, interp_order=2),
+                                device=device, stream=stream)
+            s.set_state(c.rho, c.ux, c.uy, c.T)
+            sims.append(s)
+        big = max(range(len(cases)), key=lambda i: cases[i].nx)
+        tuning = sims[big].autotune(steps=3, apply=True)
+        for s in sims:
+            s.set_launch(0, 0, tuning["halo"])
+        nodes = sum(c.nx * c.ny for c in cases)
+    else:
+        prec, lattice = ("fp32", 25) if args.profile_case == "d2q25" else ("fp64", 16)
+        sims = []
+        for ma in MACHS:
+            s = pond.Simulation(pond.Config(nx=NX, ny=NY, precision=prec, lattice=lattice, gamma=GAMMA,
+                                            mu=MU), device=device, stream=stream)
+            s.set_state(*case_fields(ma))
+            sims.append(s)
+        tuning = sims[0].autotune(steps=3, apply=True)
+        for s in sims[1:]:
+            s.set_launch(tuning["tile_x"], tuning["tile_y"], tuning["halo"])
+        nodes = len(MACHS) * NX * NY
+    batch = pond.Batch(sims, stream=stream)
+    per = time_steps(torch, batch, stream, args.steps, args.warmup, flush)
+    ms = sum(per) / len(per)
+    print(json.dumps({"case": args.profile_case, "mlups": nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                      "pc_iters_mean": mean_iters(sims), "launch_shape": tuning}))
+    batch.close()
+    for s in sims:
+        s.close()
+    return 0
+
+
 def profiled_traffic(key):
     """DRAM bytes (read + write) per launch of the timed kernel from the committed ncu record,
     or None when the record is missing or the kernel sources have changed since the capture."""
@@ -554,6 +595,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the Poisson serving run (the full stream is 10 000: "
                          "python -m paper_2405_11489_gb300.serve)")
+    ap.add_argument("--profile-case", choices=["d2q25", "fp64", "tubes"], default=None,
+                    help="time one other configuration's batched steps (inside the NVTX range "
+                         "timed_steps, for profiler runs) and print its rate")
     ap.add_argument("--quick", action="store_true",
                     help="timed mixed-precision steps only (for profiler runs)")
     args = ap.parse_args()
@@ -575,6 +619,8 @@ def main():
         dist.init_process_group("nccl", device_id=device)
 
     flush = l2_flusher(torch, device)
+    if args.profile_case:
+        return profile_case(torch, pond, device, stream, flush, args)
     sims, batch, tuning = make_sims(pond, "fp32", device, stream, tune=True)
     if world > 1:
         dist.barrier()
