@@ -280,6 +280,47 @@ struct CompSum {
 };
 
 // Sticky device status block (zeroed by pond_set_state*).
+// A double as a sum of two floats, hi + lo, formed with integer operations only (this part's
+// FP64 pipe runs at 1/64 of the FP32 rate): hi holds the top 24 significant bits, truncated,
+// lo the remaining 29 bits rounded to a float, so hi + lo is within 2^-48 of x.  Magnitudes
+// below 2^-126 give (0, 0) and magnitudes beyond the float range an infinite hi.  The
+// difference of two such pairs, (x.hi - r.hi) + (x.lo - r.lo), is x - r to FP32 rounding of
+// the result plus 2^-47 max(|x|, |r|).
+struct FloatPair {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FloatPair split_double(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ffull);                  // biased exponent
+    FloatPair r;
+    if (e < 1023 - 126) {                                        // zero, subnormal or below 2^-126
+        r.hi = __int_as_float((int)sign);
+        r.lo = 0.0f;
+        return r;
+    }
+    if (e > 1023 + 127) {                                        // beyond the float range
+        r.hi = __int_as_float((int)(sign | 0x7f800000u));
+        r.lo = 0.0f;
+        return r;
+    }
+    const unsigned long long m = b & 0x000fffffffffffffull;     // 52 fraction bits
+    r.hi = __int_as_float((int)(sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(m >> 29)));
+    // the low 29 bits are worth m_lo 2^(e - 1075)
+    const float m_lo = __uint2float_rn((unsigned int)(m & 0x1fffffffull));
+    const int k = e - 1075;
+    const float scale = k >= -126 ? __int_as_float((k + 127) << 23) : 0.0f;
+    r.lo = __int_as_float(__float_as_int(m_lo * scale) | (int)sign);
+    return r;
+}
+
+__device__ __forceinline__ float pair_diff(const FloatPair& x, const FloatPair& r)
+{
+    return (x.hi - r.hi) + (x.lo - r.lo);
+}
+
 struct DevStatus {
     unsigned long long iters_total;
     unsigned long long nonconv;

@@ -158,6 +158,7 @@ __device__ __forceinline__ const double* side_state(const double (*wall)[4], con
 template <class R>
 struct RefState {
     double rho, ux, uy, T;
+    FloatPair rho2, ux2, uy2, T2;   // the same as float pairs (deviations of the mixed modes)
     R rhoR, uxR, uyR, TR;
     R ER;       // B_00^eq of the reference node: E_r (total), U_r (internal), U'_r (non-translational)
     R PR;       // p_r = rho_r T_r
@@ -260,11 +261,20 @@ __device__ __forceinline__ void source_dev_state(const CaseRun& p, const RefStat
 {
     constexpr int NC = ncoef(N);
     const long long Nn = p.N;
-    // the only FP64 operations: differences of the primitive variables from the reference
-    const R drho = R(rho - rf.rho);
-    const R dux = R(ux - rf.ux);
-    const R duy = R(uy - rf.uy);
-    const R dT = R(T - rf.T);
+    // differences of the primitive variables from the reference: FP64 in the FP64 mode, from
+    // float pairs (integer splitting, no FP64 operation) in the mixed modes
+    R drho, dux, duy, dT;
+    if constexpr (std::is_same<R, double>::value) {
+        drho = rho - rf.rho;
+        dux = ux - rf.ux;
+        duy = uy - rf.uy;
+        dT = T - rf.T;
+    } else {
+        drho = pair_diff(split_double(rho), rf.rho2);
+        dux = pair_diff(split_double(ux), rf.ux2);
+        duy = pair_diff(split_double(uy), rf.uy2);
+        dT = pair_diff(split_double(T), rf.T2);
+    }
     const R rhoS = rf.rhoR + drho, uxS = rf.uxR + dux, uyS = rf.uyR + duy, TS = rf.TR + dT;
     const R dx = dux * rf.isT, dy = duy * rf.isT;
     const R sig = dT * rf.invT;                       // T/T_r - 1
@@ -557,6 +567,10 @@ __device__ __forceinline__ RefState<R> tile_reference(const CaseRun& p, int TX, 
     rf.ux = p.mac_in[N + c];
     rf.uy = p.mac_in[2 * N + c];
     rf.T = p.mac_in[3 * N + c];
+    rf.rho2 = split_double(rf.rho);
+    rf.ux2 = split_double(rf.ux);
+    rf.uy2 = split_double(rf.uy);
+    rf.T2 = split_double(rf.T);
     rf.rhoR = R(rf.rho);
     rf.uxR = R(rf.ux);
     rf.uyR = R(rf.uy);
@@ -838,12 +852,21 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
     R Af[NC], Ag[NC];         // deviation coefficients of the streamed populations in lambda_bar
 
     if (active) {
-        // frame of the iteration relative to the reference: FP64 differences once, then each
+        // frame of the iteration relative to the reference: the differences once (FP64, or
+        // from float pairs in the mixed modes), then each
         // corrector takes the new moments' deviations (u - u_r, T - T_r) already in R; the
         // frame's change over the iterations is summed in R and added to the FP64 frame at
         // the end, so the loop itself has no FP64 operation
-        R rbx = R(rf.ux - ux0), rby = R(rf.uy - uy0);              // u_r - u_bar
-        R rbT = R(rf.T - T0);                                      // T_r - T_bar
+        R rbx, rby, rbT;                                           // u_r - u_bar, T_r - T_bar
+        if constexpr (std::is_same<R, double>::value) {
+            rbx = rf.ux - ux0;
+            rby = rf.uy - uy0;
+            rbT = rf.T - T0;
+        } else {
+            rbx = pair_diff(rf.ux2, split_double(ux0));
+            rby = pair_diff(rf.uy2, split_double(uy0));
+            rbT = pair_diff(rf.T2, split_double(T0));
+        }
         R sum_dux = R(0), sum_duy = R(0);                          // u - u_bar, summed
         while (true) {
             const R sT = sqrt_r<R>(rf.TR - rbT);                   // sqrt(T_bar)
