@@ -788,14 +788,10 @@ __device__ __forceinline__ void prefetch_next_wave(const StepParams& pp, int TX,
     }
 }
 
-// The step kernel: one thread per node, one CTA per tile of TPB nodes, every precision, 2-D
-// and quasi-1-D.  Mixed-precision quasi-1-D grids run two blocks per SM (128 registers: a
-// little spilling, but twice the warps for a kernel whose short per-node work leaves it
-// latency-bound: tube batch 2129 -> 2158 MLUPS); everything else one block at up to 255
-// registers.
+// Single-thread-per-node kernel: FP64 arithmetic (2-D and quasi-1-D) and the FP32 quasi-1-D
+// grids.  One CTA per tile of TPB nodes.
 template <class S, class R, int Q1, int P, bool ONE_D, int TPB>
-__global__ void __launch_bounds__(TPB, (ONE_D && std::is_same<R, float>::value) ? 2 : 1)
-step_kernel(const StepParams pp)
+__global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
