@@ -160,8 +160,9 @@ int pond_set_boundary_profile(pond_sim *sim, int32_t side, const double *state, 
 int pond_step(pond_sim *sim, int32_t nsteps);
 
 /* Moments of the current populations: rho, ux, uy, T [ny][nx] (any pointer may be NULL).
- * Host (on_device = 0) or device pointers.  Synchronises the stream and returns the
- * sticky status. */
+ * Host (on_device = 0) or device pointers; page-locked host buffers (cudaHostAlloc,
+ * cudaHostRegister) are written by the kernel in place, other host memory through a staging
+ * copy.  Synchronises the stream and returns the sticky status. */
 int pond_get_moments(pond_sim *sim, double *rho, double *ux, double *uy, double *T,
                      int on_device);
 
@@ -227,9 +228,10 @@ int pond_batch_set_state(pond_batch *batch, const double *const *rho, const doub
 /* pond_get_moments for every member at once (any of the four pointer arrays may be NULL, and
  * any member's pointer in them): one synchronisation of the batch's stream for all members;
  * returns the worst member status (POND_ENONPHYSICAL before POND_ENOCONV), each member's own
- * status stays available through pond_get_stats.  The first batched read-back of a host
- * thread allocates a page-locked array of status blocks for it (grown to the largest batch
- * and kept for the thread's life). */
+ * status stays available through pond_get_stats.  Page-locked host buffers are written in
+ * place, as by pond_get_moments.  The first batched read-back of a host thread allocates a
+ * page-locked array of status blocks for it (grown to the largest batch and kept for the
+ * thread's life). */
 int pond_batch_get_moments(pond_batch *batch, double *const *rho, double *const *ux,
                            double *const *uy, double *const *T, int on_device);
 int pond_batch_use_graph(pond_batch *batch, int32_t steps_per_graph);

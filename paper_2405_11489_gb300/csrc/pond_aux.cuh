@@ -21,14 +21,15 @@ struct AuxParams {
     const double* prof[4];   // per side: null (uniform wall[side]) or [n][4] states along it
 };
 
-// Equilibrium state from rho, u, T (device arrays [N]): f_i = rho w_i, g_i = g_eq_i in the
-// node's own frame (Sec. III.A) -> all non-equilibrium coefficients zero.
+// Equilibrium state from rho, u, T (device-accessible arrays [N]): f_i = rho w_i, g_i = g_eq_i
+// in the node's own frame (Sec. III.A) -> all non-equilibrium coefficients zero.
 template <class S>
 __global__ void init_kernel(AuxParams p, const double* rho, const double* ux, const double* uy,
                             const double* T)
 {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
+    if (p.status->flags & kInputBad) return;   // the input check before rejected it: state unchanged
     double r = rho[n], vx = ux[n], vy = uy[n], t = T[n];
     if (!(r > 0.0) || !(t > 0.0) || isnan(vx) || isnan(vy) || isinf(vx) || isinf(vy) || isinf(r) || isinf(t)) {
         atomicOr(&p.status->flags, 1);

@@ -321,6 +321,10 @@ __device__ __forceinline__ float pair_diff(const FloatPair& x, const FloatPair& 
     return (x.hi - r.hi) + (x.lo - r.lo);
 }
 
+// Status flag of a rejected host input (bits 0 and 1 are the kernels' statuses, non-physical
+// and non-convergence).
+constexpr int kInputBad = 4;
+
 struct DevStatus {
     unsigned long long iters_total;
     unsigned long long nonconv;

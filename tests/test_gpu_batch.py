@@ -134,3 +134,46 @@ def test_batch_set_state_rejects_bad_host_input_and_changes_no_member(pond):
         assert np.array_equal(neq.cpu().numpy(), n2.cpu().numpy())
         assert s.stats()[0] == pond.POND_OK
     batch.close()
+
+
+def test_page_locked_host_buffers_are_used_in_place(pond):
+    """Page-locked host buffers: the moments are written by the kernel in place (no staging
+    copy); set_state / moments give the same results, bit for bit, as with pageable memory,
+    single and batched, and a bad page-locked input is rejected without changing the state."""
+    import torch
+    cases = _grid_cases()
+    pinned = [tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (c.rho, c.ux, c.uy, c.T))
+              for c in cases]
+    a = _tube_sims(pond, cases)                       # pageable numpy input
+    b = []
+    for c, f in zip(cases, pinned):
+        s = pond.Simulation(pond.Config(nx=c.nx, ny=c.ny, precision="fp32", gamma=c.gamma, mu=c.mu,
+                                        bc_x=c.bc_x, bc_y=c.bc_y))
+        rc = pond.pond_set_state(s.handle, *[t.data_ptr() for t in f], 0)
+        assert rc == 0
+        b.append(s)
+    for x, y in zip(a, b):
+        x.step(3)
+        y.step(3)
+        outs = [torch.empty(x.cfg.ny, x.cfg.nx, dtype=torch.float64).pin_memory() for _ in range(4)]
+        assert pond.pond_get_moments(y.handle, *[o.data_ptr() for o in outs], 0) == 0
+        for u, v in zip(x.moments(), outs):
+            assert np.array_equal(u, v.numpy())
+    # batched, page-locked in and out
+    batch = pond.Batch(b)
+    cols = [[f[k].data_ptr() for f in pinned] for k in range(4)]
+    assert pond.pond_batch_set_state(batch.handle, *cols, 0) == 0
+    batch.step(3)
+    outs = [[torch.empty(s.cfg.ny, s.cfg.nx, dtype=torch.float64).pin_memory() for _ in range(4)] for s in b]
+    assert pond.pond_batch_get_moments(batch.handle, *[[o[k].data_ptr() for o in outs] for k in range(4)], 0) == 0
+    for x, o in zip(a, outs):
+        for u, v in zip(x.moments(), o):
+            assert np.array_equal(u, v.numpy())
+    # a bad page-locked input is rejected and changes nothing
+    before = b[0].export_state()
+    bad = [t.clone().pin_memory() for t in pinned[0]]
+    bad[3][1, 2] = float("nan")
+    assert pond.pond_set_state(b[0].handle, *[t.data_ptr() for t in bad], 0) == pond.POND_EINVAL
+    after = b[0].export_state()
+    assert torch.equal(before[0], after[0]) and torch.equal(before[1], after[1])
+    batch.close()
