@@ -662,7 +662,7 @@ def main():
     tubes = tube_batch_rates(torch, pond, device)
     others = config_rates(torch, pond, device)
     from paper_2405_11489_gb300.serve import serve_benchmark
-    serving = serve_benchmark(args.serve_requests, rate=50.0, seed=2, load=0.7, chunk=16,
+    serving = serve_benchmark(args.serve_requests, rate=50.0, seed=2, load=0.7, chunk=32,
                               device=device)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     traffic = profiled_traffic("step_kernel_fp32_batched_4x256x256")

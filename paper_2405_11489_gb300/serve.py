@@ -266,7 +266,7 @@ def main(argv=None):
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--load", type=float, default=0.7, help="target offered load / capacity")
-    ap.add_argument("--chunk", type=int, default=16)
+    ap.add_argument("--chunk", type=int, default=32)
     ap.add_argument("--budget-gb", type=float, default=0.0, help="0: 80 percent of free HBM")
     args = ap.parse_args(argv)
     result = serve_benchmark(args.requests, args.rate, args.seed, args.load, args.chunk,
@@ -275,7 +275,7 @@ def main(argv=None):
     return 0
 
 
-def serve_benchmark(n_requests, rate=50.0, seed=2, load=0.7, chunk=16, budget_gb=0.0,
+def serve_benchmark(n_requests, rate=50.0, seed=2, load=0.7, chunk=32, budget_gb=0.0,
                     device="cuda:0"):
     """Poisson serving run: calibrate the capacity on a sample of the mix, scale the step
     counts so that the offered work is `load` x capacity at the given rate, serve."""
