@@ -84,8 +84,9 @@ typedef struct {
     double pc_tol;             /* predictor-corrector tolerance on max(|du|/sqrt(T), |dT|/T) */
     int32_t pc_max_iter;       /* iteration cap (1..64) */
     int32_t pc_fixed_iters;    /* > 0: exactly this many iterations, no tolerance test */
-    int32_t tile_x, tile_y;    /* 0 = automatic (32 x 8; 256 x 1 when ny = 1); otherwise the
-                                  tile in nodes, tile_x * tile_y = 256 */
+    int32_t tile_x, tile_y;    /* 0 = automatic (32 x 8; 128 x 1 when ny = 1); otherwise the
+                                  tile in nodes, tile_x * tile_y = 256 (128 x 1 when
+                                  ny = 1) */
     int32_t halo;              /* 0 = automatic (5); the staged box is the tile plus
                                   2 * halo + 2 nodes per axis; stencils outside it are read
                                   from global memory (slower, same result) */
@@ -240,16 +241,18 @@ int pond_batch_destroy(pond_batch *batch);
 /* Launch shapes and autotuning.  (No counterpart in the paper: the paper gives no
  * implementation; this tunes the staging of its interpolation stencils, Sec. III.A.2.)
  *
- * The step kernel runs one CTA per tile of 256 nodes and stages, per tile, the source nodes
+ * The step kernel runs one CTA per tile of 256 nodes (128 on quasi-1-D grids, two CTAs per
+ * SM) and stages, per tile, the source nodes
  * of its interpolation stencils in shared memory; the staged box holds the tile plus
  * 2 * halo + 2 nodes per axis, and stencils that leave it are gathered from global memory.
  * The shape (tile_x, tile_y, halo) changes speed only, never results beyond rounding (the
  * tile's centre node is the reference of the FP32 deviation arithmetic).
  *  - pond_get_launch: the current shape of sim (candidates = 0, ms_per_step = 0).
  *  - pond_set_launch: set sim's shape (0 = default, as in pond_config); POND_EINVAL if
- *    tile_x * tile_y != 256, tile_x is odd, or the box does not fit shared memory.
+ *    tile_x * tile_y != 256 (on quasi-1-D grids: the tile is not 128 x 1), tile_x is odd,
+ *    or the box does not fit shared memory.
  *  - pond_autotune: time every candidate shape -- tiles 32x8, 16x16, 64x4, 128x2, 8x32 on
- *    2-D grids (256x1 on quasi-1-D ones) times halos 4, 5, 6, 8 -- by running
+ *    2-D grids (128x1 on quasi-1-D ones) times halos 4, 5, 6, 8 -- by running
  *    1 + steps time steps of a copy of sim's current state in dev_scratch (caller-owned
  *    device memory of pond_workspace_bytes(cfg) bytes, 256-byte aligned) on sim's stream,
  *    time the three fastest twice more (each keeps its best time), and return the fastest

@@ -136,7 +136,7 @@ int check_config(const pond_config* c)
     if (c->tile_x < 0 || c->tile_y < 0 || c->halo < 0 || c->halo > 64) return POND_EINVAL;
     if (c->tile_x || c->tile_y) {
         int t = c->tile_x * c->tile_y;
-        if (c->tile_x < 1 || c->tile_y < 1 || t != kStepThreads) return POND_EINVAL;
+        if (c->tile_x < 1 || c->tile_y < 1 || t != step_threads(c->ny == 1)) return POND_EINVAL;
         if (c->ny == 1 && c->tile_y != 1) return POND_EINVAL;
     }
     return POND_OK;
@@ -174,9 +174,10 @@ void side_profiles(pond_sim* s, const double* prof[4])
 
 int cuda_status(cudaError_t e);
 
-// Blocks of the step kernel resident at once on the current device: one per SM (255
-// registers x 256 threads fill an SM's register file).  0 if the query fails.
-int resident_step_blocks()
+// Blocks of the step kernel resident at once on the current device: 256 threads per SM (255
+// registers a thread fill an SM's register file), i.e. one CTA per SM on 2-D grids and two on
+// quasi-1-D ones.  0 if the query fails.
+int resident_step_blocks(bool one_d)
 {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -184,7 +185,7 @@ int resident_step_blocks()
         cudaGetLastError();
         return 0;
     }
-    return sms;
+    return sms * (kStepThreads2D / step_threads(one_d));
 }
 
 // Copy states [n][4] (host or device) into side w's profile, or its uniform state when
@@ -334,7 +335,7 @@ void fill_case(const pond_config& c, DevStatus* status, CaseDesc& d, const doubl
 }
 
 // Launch shape of the step kernel: the tile (tile_x * tile_y nodes per CTA; 0 = default,
-// 32 x 8 on 2-D grids, 256 x 1 on quasi-1-D ones) and the staged box, the tile plus
+// 32 x 8 on 2-D grids, 128 x 1 on quasi-1-D ones) and the staged box, the tile plus
 // 2 halo + 2 cells per axis (halo 0 = default 5).
 struct Shape {
     int tx, ty, box_w, box_h, halo;
@@ -347,14 +348,14 @@ int make_shape(const pond_config& c, int tile_x, int tile_y, int halo, Shape* sh
     if (tile_x < 0 || tile_y < 0 || halo < 0 || halo > 64) return POND_EINVAL;
     sh->one_d = (c.ny == 1);
     if (sh->one_d) {
-        if ((tile_x && tile_x != kStepThreads) || (tile_y && tile_y != 1)) return POND_EINVAL;
-        sh->tx = kStepThreads;
+        if ((tile_x && tile_x != kStepThreads1D) || (tile_y && tile_y != 1)) return POND_EINVAL;
+        sh->tx = kStepThreads1D;
         sh->ty = 1;
     } else {
         if ((tile_x != 0) != (tile_y != 0)) return POND_EINVAL;
         sh->tx = tile_x ? tile_x : 32;
-        sh->ty = tile_y ? tile_y : kStepThreads / 32;
-        if (sh->tx * sh->ty != kStepThreads || sh->tx % 2) return POND_EINVAL;
+        sh->ty = tile_y ? tile_y : kStepThreads2D / 32;
+        if (sh->tx * sh->ty != kStepThreads2D || sh->tx % 2) return POND_EINVAL;
     }
     sh->halo = halo ? halo : 5;
     const int extent = 2 * sh->halo + 2;
@@ -362,7 +363,7 @@ int make_shape(const pond_config& c, int tile_x, int tile_y, int halo, Shape* sh
     sh->box_h = sh->one_d ? 1 : sh->ty + extent;
     const int q1 = c.lattice == POND_D2Q16 ? 4 : 5;
     sh->smem = step_smem_bytes(c.precision == POND_FP64 ? 8 : 4, q1, sh->one_d, sh->box_w, sh->box_h,
-                               kStepThreads);
+                               step_threads(sh->one_d));
     int dev = 0, smem_optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -588,7 +589,7 @@ int pond_step(pond_sim* s, int32_t nsteps)
     p.lat = s->lat;
     p.box_w = s->box_w;
     p.box_h = s->box_h;
-    p.ahead = resident_step_blocks();
+    p.ahead = resident_step_blocks(s->one_d);
     const double* prof[4];
     side_profiles(s, prof);
     fill_case(c, status_ptr(s), p.one, prof);
@@ -768,7 +769,7 @@ cudaError_t batch_launch_step(pond_batch* b)
     p.lat = s0->lat;
     p.box_w = s0->box_w;
     p.box_h = s0->box_h;
-    p.ahead = resident_step_blocks();
+    p.ahead = resident_step_blocks(s0->one_d);
     p.flip = b->flip;
     p.ncase = b->count;
     p.cases = b->d_cases;
@@ -1284,7 +1285,7 @@ extern "C" int pond_autotune(pond_sim* s, void* dev_scratch, size_t bytes, int32
               [](const Trial& a, const Trial& b) { return a.ms < b.ms; });
     const int tried = (int)trials.size();
     const double best = tried ? trials[0].ms : 0.0;
-    const int bx = tried ? (s->one_d ? kStepThreads : trials[0].tx) : 0;
+    const int bx = tried ? (s->one_d ? kStepThreads1D : trials[0].tx) : 0;
     const int by = tried ? (s->one_d ? 1 : trials[0].ty) : 0;
     const int bh = tried ? trials[0].halo : 0;
     if (e0) cudaEventDestroy(e0);

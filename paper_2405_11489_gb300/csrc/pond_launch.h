@@ -11,8 +11,14 @@ struct StepParams;
 struct AuxParams;
 struct CaseDesc;
 
-// Threads per CTA of the step kernel (tile_x * tile_y).
-constexpr int kStepThreads = 256;
+// Threads per CTA of the step kernel (tile_x * tile_y).  The kernel holds about 255
+// registers a thread, so an SM keeps 256 of its threads: one CTA of 256 on 2-D grids, two of
+// 128 on quasi-1-D grids, where one CTA's staging then overlaps the other's stencil work and
+// the last tile of a short tube leaves fewer lanes idle (256 uneven tubes: 2250 -> 2560 MLUPS;
+// on 2-D grids 128-node tiles stage 39 % more halo and ran 1-2 % slower).
+constexpr int kStepThreads2D = 256;
+constexpr int kStepThreads1D = 128;
+constexpr int step_threads(bool one_d) { return one_d ? kStepThreads1D : kStepThreads2D; }
 
 struct Launch {
     dim3 grid, block;

@@ -11,9 +11,9 @@ namespace pond {
 cudaError_t POND_CAT(step, POND_TAG)(const StepParams& p, int order, const Launch& l)
 {
     if (order == 3)
-        step_kernel<POND_S, POND_R, POND_Q1, 4, POND_ONED, kStepThreads><<<l.grid, l.block, l.smem, l.stream>>>(p);
+        step_kernel<POND_S, POND_R, POND_Q1, 4, POND_ONED, step_threads(POND_ONED)><<<l.grid, l.block, l.smem, l.stream>>>(p);
     else
-        step_kernel<POND_S, POND_R, POND_Q1, 3, POND_ONED, kStepThreads><<<l.grid, l.block, l.smem, l.stream>>>(p);
+        step_kernel<POND_S, POND_R, POND_Q1, 3, POND_ONED, step_threads(POND_ONED)><<<l.grid, l.block, l.smem, l.stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -32,9 +32,9 @@ static cudaError_t set_smem_limit(K kernel, size_t optin, size_t* static_bytes)
 cudaError_t POND_CAT(smem, POND_TAG)(int order, size_t optin, size_t* static_bytes)
 {
     if (order == 3)
-        return set_smem_limit(step_kernel<POND_S, POND_R, POND_Q1, 4, POND_ONED, kStepThreads>, optin,
+        return set_smem_limit(step_kernel<POND_S, POND_R, POND_Q1, 4, POND_ONED, step_threads(POND_ONED)>, optin,
                               static_bytes);
-    return set_smem_limit(step_kernel<POND_S, POND_R, POND_Q1, 3, POND_ONED, kStepThreads>, optin,
+    return set_smem_limit(step_kernel<POND_S, POND_R, POND_Q1, 3, POND_ONED, step_threads(POND_ONED)>, optin,
                           static_bytes);
 }
 

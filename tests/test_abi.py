@@ -63,6 +63,18 @@ def test_invalid_configs_are_rejected(lib, field, value):
     assert lib.pond_create(ctypes.byref(cfg), ctypes.c_void_p(256), 1 << 20, None, ctypes.byref(h)) == pond.POND_EINVAL
 
 
+@pytest.mark.parametrize("ny,tile,ok", [(1, (128, 1), True), (1, (256, 1), False), (1, (64, 2), False),
+                                         (16, (32, 8), True), (16, (128, 2), True), (16, (128, 1), False)])
+def test_tiles_hold_the_kernels_threads(lib, ny, tile, ok):
+    """A tile holds one CTA's threads: 256 nodes on 2-D grids, 128 x 1 on quasi-1-D ones."""
+    from paper_2405_11489_gb300 import pond
+    cfg = pond.pond_config_default(400, ny)
+    cfg.tile_x, cfg.tile_y = tile
+    n = ctypes.c_size_t(0)
+    rc = lib.pond_workspace_bytes(ctypes.byref(cfg), ctypes.byref(n))
+    assert rc == (pond.POND_OK if ok else pond.POND_EINVAL)
+
+
 def test_null_handles_are_rejected(lib):
     from paper_2405_11489_gb300 import pond
     assert lib.pond_step(None, 1) == pond.POND_EINVAL

@@ -62,7 +62,7 @@ def test_quasi_1d_grids_keep_the_row_tile(pond):
     case = W.tube_batch(count=1, seed=3, nmin=600, nmax=600)[0]
     s = _sim(pond, case, "fp32", interp_order=2)
     t = s.autotune(steps=2)
-    assert (t["tile_x"], t["tile_y"]) == (256, 1) and t["candidates"] >= 1
+    assert (t["tile_x"], t["tile_y"]) == (128, 1) and t["candidates"] >= 1
     s.close()
 
 
@@ -74,6 +74,20 @@ def test_autotune_times_states_whose_nodes_do_not_converge(pond):
     assert s.stats()[0] == pond.POND_ENOCONV
     t = s.autotune(steps=1)
     assert t["candidates"] >= 5
+    s.close()
+
+
+def test_quasi_1d_grids_take_only_the_row_tile(pond):
+    case = W.tube_batch(count=1, seed=3, nmin=500, nmax=500)[0]
+    s = _sim(pond, case, "fp32")
+    s.set_launch(128, 1, 6)
+    assert s.launch() == {"tile_x": 128, "tile_y": 1, "halo": 6}
+    for shape in ((256, 1, 5), (64, 2, 5)):
+        with pytest.raises(pond.PondError):
+            s.set_launch(*shape)
+    assert s.launch() == {"tile_x": 128, "tile_y": 1, "halo": 6}
+    s.step(3)
+    assert s.stats()[1].steps == 3
     s.close()
 
 
