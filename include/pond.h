@@ -163,7 +163,9 @@ int pond_step(pond_sim *sim, int32_t nsteps);
 /* Moments of the current populations: rho, ux, uy, T [ny][nx] (any pointer may be NULL).
  * Host (on_device = 0) or device pointers; page-locked host buffers (cudaHostAlloc,
  * cudaHostRegister) are written by the kernel in place, other host memory through a staging
- * copy.  Synchronises the stream and returns the sticky status. */
+ * copy.  Synchronises the stream and returns the sticky status.  In FP64 the moments are
+ * summed in FP64 (Sec. II); in the mixed modes the contributions of the stored FP32 (or
+ * FP16/BF16) non-equilibrium coefficients are formed in FP32 and added to the FP64 frame. */
 int pond_get_moments(pond_sim *sim, double *rho, double *ux, double *uy, double *T,
                      int on_device);
 
@@ -221,16 +223,21 @@ int pond_batch_step(pond_batch *batch, int32_t nsteps);
 /* pond_set_state for every member at once: rho[i], ux[i], uy[i], T[i] are member i's
  * [ny][nx] fields (count pointers each, host or device as on_device says).  The same checks
  * and effects as pond_set_state on each member, on the batch's stream and ordered with the
- * members' streams like pond_batch_step; host input is checked after its copy with one
+ * members' streams like pond_batch_step; host input is checked on the device with one
  * synchronisation for the whole batch, and if any member's input is rejected no member's
- * state changes (POND_EINVAL). */
+ * state changes (POND_EINVAL).  When every member's four host arrays are page-locked they are
+ * read in place by one kernel per 64 members, which checks and stages them; other host
+ * memory is copied first.  The status blocks are cleared, and the equilibria set, by one
+ * launch each per 64 members. */
 int pond_batch_set_state(pond_batch *batch, const double *const *rho, const double *const *ux,
                          const double *const *uy, const double *const *T, int on_device);
 /* pond_get_moments for every member at once (any of the four pointer arrays may be NULL, and
  * any member's pointer in them): one synchronisation of the batch's stream for all members;
  * returns the worst member status (POND_ENONPHYSICAL before POND_ENOCONV), each member's own
- * status stays available through pond_get_stats.  Page-locked host buffers are written in
- * place, as by pond_get_moments.  The first batched read-back of a host thread allocates a
+ * status stays available through pond_get_stats.  Device buffers, and page-locked host
+ * buffers when every given buffer is page-locked, are written in place by one kernel per 64
+ * members; otherwise each member's moments pass through a staging copy.  The first batched
+ * read-back of a host thread allocates a
  * page-locked array of status blocks for it (grown to the largest batch and kept for the
  * thread's life). */
 int pond_batch_get_moments(pond_batch *batch, double *const *rho, double *const *ux,

@@ -495,16 +495,65 @@ int pond_set_boundary_profile(pond_sim* s, int32_t side, const double* state, in
 
 // Host input of pond_set_state, staged on the device: sets kInputBad when a node has rho <= 0, T <= 0 or a value that is not finite.  One flag
 // write per warp.
+__device__ __forceinline__ bool bad_fields(double r, double ux, double uy, double t)
+{
+    return !(r > 0.0) || !(t > 0.0) || !isfinite(r) || !isfinite(t) || !isfinite(ux) || !isfinite(uy);
+}
+
 __global__ void check_fields_kernel(const double* rho, const double* vx, const double* vy, const double* T,
                                     long long N, DevStatus* st)
 {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool bad = false;
-    if (n < N) {
-        const double r = rho[n], ux = vx[n], uy = vy[n], t = T[n];
-        bad = !(r > 0.0) || !(t > 0.0) || !isfinite(r) || !isfinite(t) || !isfinite(ux) || !isfinite(uy);
-    }
+    const bool bad = n < N && bad_fields(rho[n], vx[n], vy[n], T[n]);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->flags, kInputBad);
+}
+
+// Batched form over members [c0, c1) of a batch (blocks from block_start[c0] = block0 on; a block
+// lies within one member): the fields of member c are fld.f[c - c0].
+__global__ void check_fields_batch_kernel(const CaseDesc* cases, const int* block_start, int c0, int c1,
+                                          int block0, MemberFields fld)
+{
+    const int b = block0 + (int)blockIdx.x;
+    const int c = member_of_block(block_start, c0, c1, b);
+    const CaseDesc& d = cases[c];
+    const long long n = (long long)(b - block_start[c]) * blockDim.x + threadIdx.x;
+    const double* const* in = fld.f[c - c0];
+    const bool bad = n < d.N && bad_fields(in[0][n], in[1][n], in[2][n], in[3][n]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&d.status->flags, kInputBad);
+}
+
+// Page-locked host input of members [c0, c1) (fld.f[c - c0]: device addresses of the host
+// arrays) read in place, checked like check_fields_batch_kernel and written into the member's
+// idle state buffer (cur ^ flip ^ 1), where the init kernel then reads it.
+__global__ void stage_check_batch_kernel(const CaseDesc* cases, const int* block_start, int c0, int c1,
+                                         int block0, int flip, MemberFields fld)
+{
+    const int b = block0 + (int)blockIdx.x;
+    const int c = member_of_block(block_start, c0, c1, b);
+    const CaseDesc& d = cases[c];
+    const long long n = (long long)(b - block_start[c]) * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (n < d.N) {
+        const double* const* in = fld.f[c - c0];
+        const double r = in[0][n], ux = in[1][n], uy = in[2][n], t = in[3][n];
+        double* stage = d.mac[d.cur ^ flip ^ 1];
+        stage[n] = r;
+        stage[d.N + n] = ux;
+        stage[2 * d.N + n] = uy;
+        stage[3 * d.N + n] = t;
+        bad = bad_fields(r, ux, uy, t);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&d.status->flags, kInputBad);
+}
+
+// The status blocks of a batch's members cleared as reset_status clears one (first_bad = ~0).
+__global__ void reset_status_batch_kernel(const CaseDesc* cases, int count)
+{
+    const int c = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= count) return;
+    DevStatus* st = cases[c].status;
+    *st = DevStatus{};
+    st->first_bad = ~0ull;
 }
 
 // The device address of page-locked host memory (kernels then read or write it directly,
@@ -739,6 +788,7 @@ struct pond_batch {
     CaseDesc* d_cases;
     int* d_tile_start;
     int* d_aux_start;
+    std::vector<int> h_aux_start;  // host copy of d_aux_start
     int count, total_tiles, total_aux_blocks;
     bool any_internal;
     int flip;                      // parity of the steps taken since creation
@@ -887,6 +937,7 @@ extern "C" int pond_batch_create(pond_sim* const* sims, int32_t count, void* dev
     b->count = count;
     b->total_tiles = tiles;
     b->total_aux_blocks = aux;
+    b->h_aux_start = aux_start;
     b->any_internal = any_internal;
     b->flip = 0;
     b->graph_steps = 0;
@@ -1043,6 +1094,25 @@ int batch_read_status(pond_batch* b, bool* input_bad)
 
 }  // namespace
 
+// Runs launch(c0, c1, block0, blocks, fields) over the batch's members in chunks of kAuxChunk;
+// fields.f[c - c0][k] = field(c, k).  One launch per chunk: the aux blocks of members [c0, c1)
+// are block0 .. block0 + blocks - 1 of the batch's aux block numbering.
+template <class F, class L>
+cudaError_t for_member_chunks(const pond_batch* b, F field, L launch)
+{
+    for (int c0 = 0; c0 < b->count; c0 += kAuxChunk) {
+        const int c1 = std::min(b->count, c0 + kAuxChunk);
+        MemberFields fld;
+        std::memset(&fld, 0, sizeof(fld));
+        for (int c = c0; c < c1; ++c)
+            for (int k = 0; k < 4; ++k) fld.f[c - c0][k] = field(c, k);
+        const int block0 = b->h_aux_start[c0];
+        cudaError_t e = launch(c0, c1, block0, b->h_aux_start[c1] - block0, fld);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 extern "C" int pond_batch_set_state(pond_batch* b, const double* const* rho, const double* const* ux,
                                     const double* const* uy, const double* const* T, int on_device)
 {
@@ -1051,32 +1121,52 @@ extern "C" int pond_batch_set_state(pond_batch* b, const double* const* rho, con
         if (!rho[i] || !ux[i] || !uy[i] || !T[i]) return POND_EINVAL;
     cudaError_t e = batch_wait_members(b);
     if (e != cudaSuccess) return cuda_status(e);
-    std::vector<const double*> src(4 * (size_t)b->count);
-    for (int i = 0; i < b->count; ++i) {
-        pond_sim* s = b->sims[i];
-        const long long N = (long long)s->cfg.nx * s->cfg.ny;
-        s->steps = 0;
-        DevStatus* st = status_ptr(s);
-        e = cudaMemsetAsync(st, 0, sizeof(DevStatus), b->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(&st->first_bad, 0xff, sizeof(st->first_bad), b->stream);
-        const double* in[4] = {rho[i], ux[i], uy[i], T[i]};
-        if (!on_device) {   // staged in the idle buffer and checked there
-            double* stage = mac_ptr(s, 1 - s->cur);
-            for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
-                e = cudaMemcpyAsync(stage + k * N, in[k], N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
-                src[4 * i + k] = stage + k * N;
-            }
-            if (e == cudaSuccess) {
-                check_fields_kernel<<<(unsigned int)((N + 255) / 256), 256, 0, b->stream>>>(
-                    src[4 * i], src[4 * i + 1], src[4 * i + 2], src[4 * i + 3], N, st);
-                e = cudaGetLastError();
-            }
+    const double* const* in[4] = {rho, ux, uy, T};
+    for (pond_sim* s : b->sims) s->steps = 0;
+    // every member's status block cleared by one launch, the input checked and the equilibria
+    // set by one launch per kAuxChunk members
+    reset_status_batch_kernel<<<(unsigned int)((b->count + 127) / 128), 128, 0, b->stream>>>(b->d_cases, b->count);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    auto staged = [b](int c, int k) {        // host input: staged in the member's idle buffer
+        pond_sim* s = b->sims[c];
+        return mac_ptr(s, 1 - s->cur) + k * (long long)s->cfg.nx * s->cfg.ny;
+    };
+    if (!on_device) {
+        // page-locked input: read in place by the staging kernel; other host memory: copied
+        std::vector<double*> view(4 * (size_t)b->count, nullptr);
+        bool page_locked = true;
+        for (int i = 0; i < b->count && page_locked; ++i) {
+            const double* src[4] = {in[0][i], in[1][i], in[2][i], in[3][i]};
+            const double* v[4];
+            page_locked = host_views(src, v);
+            for (int k = 0; k < 4; ++k) view[4 * (size_t)i + k] = const_cast<double*>(v[k]);
+        }
+        if (page_locked) {
+            e = for_member_chunks(
+                b, [&](int c, int k) { return view[4 * (size_t)c + k]; },
+                [b](int c0, int c1, int block0, int blocks, const MemberFields& fld) {
+                    stage_check_batch_kernel<<<blocks, 256, 0, b->stream>>>(b->d_cases, b->d_aux_start, c0, c1,
+                                                                            block0, b->flip, fld);
+                    return cudaGetLastError();
+                });
         } else {
-            for (int k = 0; k < 4; ++k) src[4 * i + k] = in[k];
+            for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+                pond_sim* s = b->sims[i];
+                const long long N = (long long)s->cfg.nx * s->cfg.ny;
+                for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+                    e = cudaMemcpyAsync(staged(i, k), in[k][i], N * sizeof(double), cudaMemcpyHostToDevice,
+                                        b->stream);
+            }
+            if (e == cudaSuccess)
+                e = for_member_chunks(b, staged, [b](int c0, int c1, int block0, int blocks, const MemberFields& fld) {
+                    check_fields_batch_kernel<<<blocks, 256, 0, b->stream>>>(b->d_cases, b->d_aux_start, c0, c1,
+                                                                             block0, fld);
+                    return cudaGetLastError();
+                });
         }
         if (e != cudaSuccess) return cuda_status(e);
-    }
-    if (!on_device) {   // one synchronisation for every member's check
+        // one synchronisation for every member's check
         bool bad = false;
         const int rc = batch_read_status(b, &bad);
         if (rc == POND_ECUDA) return rc;
@@ -1088,13 +1178,15 @@ extern "C" int pond_batch_set_state(pond_batch* b, const double* const* rho, con
             return POND_EINVAL;
         }
     }
-    for (int i = 0; i < b->count; ++i) {
-        pond_sim* s = b->sims[i];
-        AuxParams a = aux_params(s, s->cur);
-        e = POND_BY_PRECISION(s->cfg.precision, init, a, src[4 * i], src[4 * i + 1], src[4 * i + 2],
-                              src[4 * i + 3], b->stream);
-        if (e != cudaSuccess) return cuda_status(e);
-    }
+    const int precision = b->sims[0]->cfg.precision;
+    e = for_member_chunks(
+        b,
+        [&](int c, int k) { return on_device ? const_cast<double*>(in[k][c]) : staged(c, k); },
+        [b, precision](int c0, int c1, int block0, int blocks, const MemberFields& fld) {
+            return POND_BY_PRECISION(precision, init_batch, b->d_cases, b->d_aux_start, c0, c1, block0, blocks,
+                                     b->flip, fld, b->stream);
+        });
+    if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(batch_release_members(b));
 }
 
@@ -1104,16 +1196,39 @@ extern "C" int pond_batch_get_moments(pond_batch* b, double* const* rho, double*
     if (!b) return POND_EINVAL;
     cudaError_t e = batch_wait_members(b);
     if (e != cudaSuccess) return cuda_status(e);
-    for (int i = 0; i < b->count; ++i) {
+    double* const* out[4] = {rho, ux, uy, T};
+    // device or page-locked host outputs: written in place by one launch per kAuxChunk members
+    std::vector<double*> direct(4 * (size_t)b->count, nullptr);
+    bool all_direct = true;
+    for (int i = 0; i < b->count && all_direct; ++i) {
+        const double* dst[4];
+        for (int k = 0; k < 4; ++k) dst[k] = out[k] ? out[k][i] : nullptr;
+        const double* view[4];
+        if (on_device) {
+            for (int k = 0; k < 4; ++k) view[k] = dst[k];
+        } else {
+            all_direct = host_views(dst, view);
+        }
+        for (int k = 0; k < 4; ++k) direct[4 * (size_t)i + k] = const_cast<double*>(view[k]);
+    }
+    if (all_direct) {
+        const int precision = b->sims[0]->cfg.precision;
+        e = for_member_chunks(
+            b, [&](int c, int k) { return direct[4 * (size_t)c + k]; },
+            [b, precision](int c0, int c1, int block0, int blocks, const MemberFields& fld) {
+                return POND_BY_PRECISION(precision, moments_batch, b->d_cases, b->d_aux_start, c0, c1, block0,
+                                         blocks, b->flip, fld, b->stream);
+            });
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    for (int i = 0; i < b->count && !all_direct; ++i) {   // pageable host memory: staged copies
         pond_sim* s = b->sims[i];
         const long long N = (long long)s->cfg.nx * s->cfg.ny;
         double* dst[4] = {rho ? rho[i] : nullptr, ux ? ux[i] : nullptr, uy ? uy[i] : nullptr, T ? T[i] : nullptr};
         AuxParams a = aux_params(s, s->cur);
         const double* cdst[4] = {dst[0], dst[1], dst[2], dst[3]};
         const double* view[4];
-        if (on_device) {
-            e = POND_BY_PRECISION(s->cfg.precision, moments, a, dst[0], dst[1], dst[2], dst[3], b->stream);
-        } else if (host_views(cdst, view)) {   // page-locked host memory: written in place
+        if (host_views(cdst, view)) {   // page-locked host memory: written in place
             e = POND_BY_PRECISION(s->cfg.precision, moments, a, const_cast<double*>(view[0]),
                                   const_cast<double*>(view[1]), const_cast<double*>(view[2]),
                                   const_cast<double*>(view[3]), b->stream);

@@ -24,23 +24,29 @@ struct AuxParams {
 // Equilibrium state from rho, u, T (device-accessible arrays [N]): f_i = rho w_i, g_i = g_eq_i
 // in the node's own frame (Sec. III.A) -> all non-equilibrium coefficients zero.
 template <class S>
+__device__ __forceinline__ void init_node(double* mac, void* neq, long long N, int nord, DevStatus* status,
+                                          long long n, double r, double vx, double vy, double t)
+{
+    if (!(r > 0.0) || !(t > 0.0) || isnan(vx) || isnan(vy) || isinf(vx) || isinf(vy) || isinf(r) || isinf(t)) {
+        atomicOr(&status->flags, 1);
+        atomicMin(&status->first_bad, (unsigned long long)n);
+    }
+    mac[n] = r;
+    mac[N + n] = vx;
+    mac[2 * N + n] = vy;
+    mac[3 * N + n] = t;
+    S* q = reinterpret_cast<S*>(neq);
+    for (int m = 0; m < nneq(nord); ++m) sto_put<S, double>(q + (long long)m * N + n, 0.0);
+}
+
+template <class S>
 __global__ void init_kernel(AuxParams p, const double* rho, const double* ux, const double* uy,
                             const double* T)
 {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
     if (p.status->flags & kInputBad) return;   // the input check before rejected it: state unchanged
-    double r = rho[n], vx = ux[n], vy = uy[n], t = T[n];
-    if (!(r > 0.0) || !(t > 0.0) || isnan(vx) || isnan(vy) || isinf(vx) || isinf(vy) || isinf(r) || isinf(t)) {
-        atomicOr(&p.status->flags, 1);
-        atomicMin(&p.status->first_bad, (unsigned long long)n);
-    }
-    p.mac[n] = r;
-    p.mac[p.N + n] = vx;
-    p.mac[2 * p.N + n] = vy;
-    p.mac[3 * p.N + n] = t;
-    S* q = reinterpret_cast<S*>(p.neq);
-    for (int m = 0; m < nneq(p.nord); ++m) sto_put<S, double>(q + (long long)m * p.N + n, 0.0);
+    init_node<S>(p.mac, p.neq, p.N, p.nord, p.status, n, rho[n], ux[n], uy[n], T[n]);
 }
 
 // Populations f, g [Q][N] in frames (ux, uy, T) -> Hermite coefficients of order <= N.
@@ -87,19 +93,20 @@ __global__ void set_pops_kernel(AuxParams p, const double* f, const double* g, c
 
 // Full own-frame coefficients of node n (FP64).
 template <class S>
-__device__ __forceinline__ void node_coefficients(const AuxParams& p, long long n, double* A, double* B,
+__device__ __forceinline__ void node_coefficients(const double* mac, const void* neq, long long N, int nord,
+                                                  int split, double cv, long long n, double* A, double* B,
                                                   double& rho, double& ux, double& uy, double& T)
 {
-    const S* q = reinterpret_cast<const S*>(p.neq);
-    const int nc = ncoef(p.nord);
-    rho = p.mac[n];
-    ux = p.mac[p.N + n];
-    uy = p.mac[2 * p.N + n];
-    T = p.mac[3 * p.N + n];
+    const S* q = reinterpret_cast<const S*>(neq);
+    const int nc = ncoef(nord);
+    rho = mac[n];
+    ux = mac[N + n];
+    uy = mac[2 * N + n];
+    T = mac[3 * N + n];
     A[0] = rho;
-    for (int m = 1; m < nc; ++m) A[m] = sto_load<S>(q + (long long)(m - 1) * p.N + n);
-    for (int m = 0; m < nc; ++m) B[m] = sto_load<S>(q + (long long)(nc - 1 + m) * p.N + n);
-    GEq e = g_equilibrium(p.split, p.cv, rho, ux, uy, T, sqrt(T));
+    for (int m = 1; m < nc; ++m) A[m] = sto_load<S>(q + (long long)(m - 1) * N + n);
+    for (int m = 0; m < nc; ++m) B[m] = sto_load<S>(q + (long long)(nc - 1 + m) * N + n);
+    GEq e = g_equilibrium(split, cv, rho, ux, uy, T, sqrt(T));
     B[slot(0, 0)] += e.b00;
     B[slot(1, 0)] += e.b10;
     B[slot(0, 1)] += e.b01;
@@ -107,30 +114,81 @@ __device__ __forceinline__ void node_coefficients(const AuxParams& p, long long 
     B[slot(0, 2)] += e.b20;
 }
 
+template <class S>
+__device__ __forceinline__ void node_coefficients(const AuxParams& p, long long n, double* A, double* B,
+                                                  double& rho, double& ux, double& uy, double& T)
+{
+    node_coefficients<S>(p.mac, p.neq, p.N, p.nord, p.split, p.cv, n, A, B, rho, ux, uy, T);
+}
+
 // Moments of the populations (Sec. II): rho = A_00, rho u = rho u_frame + sqrt(T) (A_10, A_01),
 // total split E = B_00, T = (E/rho - |u|^2/2)/c_v; internal split T = B_00/(rho c_v);
 // non-translational split E = B_00 + sum |C|^2/2 f with
 // sum |C|^2/2 f = (T (A_20 + A_02 + 2 rho) + 2 sqrt(T) u_frame . (A_10, A_01) + |u_frame|^2 rho)/2.
+// Written to out[0..3][n] (rho, u_x, u_y, T); null arrays are skipped.
+//
+// Mixed modes (storage S narrower than double): the same moments written relative to the
+// stored frame (u_f, T_f), whose non-equilibrium coefficients are the only non-FP64 inputs:
+// with d = u - u_f = sqrt(T_f) (A_10, A_01) / rho and b = B_00 - B_00^eq,
+//   total split            T = T_f + (b / rho - u_f . d - |d|^2 / 2) / c_v,
+//   internal split         T = T_f + b / (rho c_v),
+//   non-translational      T = T_f + (b / rho + T_f (A_20 + A_02) / (2 rho) - |d|^2 / 2) / c_v
+// (B_00^eq = rho (c_v T_f + |u_f|^2/2), rho c_v T_f, rho (c_v - 1) T_f).  The corrections are
+// formed in FP32 and added to the FP64 frame once: FP64 is slow on this part, and the
+// coefficients carry FP32 (or narrower) precision in these modes anyway.
+template <class S>
+__device__ __forceinline__ void node_moments(const double* mac, const void* neq, long long N, int nord,
+                                             int split, double cv, long long n, double* const* out)
+{
+    double rho, vx, vy, t;
+    if constexpr (std::is_same<S, double>::value) {
+        double A[NCMAX], B[NCMAX], ux, uy, T;
+        node_coefficients<S>(mac, neq, N, nord, split, cv, n, A, B, rho, ux, uy, T);
+        double sT = sqrt(T);
+        vx = ux + sT * A[slot(1, 0)] / rho;
+        vy = uy + sT * A[slot(0, 1)] / rho;
+        double E = B[0];
+        if (split == 2)
+            E += 0.5 * (T * (A[slot(2, 0)] + A[slot(0, 2)] + 2.0 * rho) +
+                        2.0 * sT * (ux * A[slot(1, 0)] + uy * A[slot(0, 1)]) + (ux * ux + uy * uy) * rho);
+        t = (split == 1) ? B[0] / (rho * cv) : (E / rho - 0.5 * (vx * vx + vy * vy)) / cv;
+    } else {
+        const S* q = reinterpret_cast<const S*>(neq);
+        const int nc = ncoef(nord);
+        rho = mac[n];
+        const double ux = mac[N + n], uy = mac[2 * N + n], T = mac[3 * N + n];
+        const float a10 = sto_loadf<S>(q + (long long)(slot(1, 0) - 1) * N + n);
+        const float a01 = sto_loadf<S>(q + (long long)(slot(0, 1) - 1) * N + n);
+        const float b = sto_loadf<S>(q + (long long)(nc - 1) * N + n);
+        const float ir = 1.0f / (float)rho, Tf = (float)T, icv = 1.0f / (float)cv;
+        const float sT = sqrtf(Tf);
+        const float dx = sT * a10 * ir, dy = sT * a01 * ir;
+        float e = b * ir;
+        if (split == 0) {
+            e -= (float)ux * dx + (float)uy * dy + 0.5f * (dx * dx + dy * dy);
+        } else if (split == 2) {
+            const float a20 = sto_loadf<S>(q + (long long)(slot(2, 0) - 1) * N + n);
+            const float a02 = sto_loadf<S>(q + (long long)(slot(0, 2) - 1) * N + n);
+            e += 0.5f * Tf * (a20 + a02) * ir - 0.5f * (dx * dx + dy * dy);
+        }
+        vx = ux + (double)dx;
+        vy = uy + (double)dy;
+        t = T + (double)(e * icv);
+    }
+    if (out[0]) out[0][n] = rho;
+    if (out[1]) out[1][n] = vx;
+    if (out[2]) out[2][n] = vy;
+    if (out[3]) out[3][n] = t;
+}
+
 template <class S>
 __global__ void moments_kernel(AuxParams p, double* out_rho, double* out_ux, double* out_uy,
                                double* out_T)
 {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    double A[NCMAX], B[NCMAX], rho, ux, uy, T;
-    node_coefficients<S>(p, n, A, B, rho, ux, uy, T);
-    double sT = sqrt(T);
-    double vx = ux + sT * A[slot(1, 0)] / rho;
-    double vy = uy + sT * A[slot(0, 1)] / rho;
-    double E = B[0];
-    if (p.split == 2)
-        E += 0.5 * (T * (A[slot(2, 0)] + A[slot(0, 2)] + 2.0 * rho) +
-                    2.0 * sT * (ux * A[slot(1, 0)] + uy * A[slot(0, 1)]) + (ux * ux + uy * uy) * rho);
-    double t = (p.split == 1) ? B[0] / (rho * p.cv) : (E / rho - 0.5 * (vx * vx + vy * vy)) / p.cv;
-    if (out_rho) out_rho[n] = rho;
-    if (out_ux) out_ux[n] = vx;
-    if (out_uy) out_uy[n] = vy;
-    if (out_T) out_T[n] = t;
+    double* const out[4] = {out_rho, out_ux, out_uy, out_T};
+    node_moments<S>(p.mac, p.neq, p.N, p.nord, p.split, p.cv, n, out);
 }
 
 // Populations in each node's own frame: f_i = w_i sum A_pq He_p(c_a) He_q(c_b) / (p! q!).
@@ -218,18 +276,25 @@ __global__ void internal_source_kernel(AuxParams p)
                             p.prof);
 }
 
-// Batched form: block b works on nodes [256 (b - block_start[c]), ...) of case c (the last case
-// with block_start[c] <= b); cases of the total split return at once.
-template <class S>
-__global__ void internal_source_batch_kernel(const CaseDesc* cases, const int* block_start, int ncase,
-                                             int flip)
+// Batched auxiliary launches: block b works on nodes [256 (b - block_start[c]), ...) of member
+// c, the last of members [c0, c1) with block_start[c] <= b.
+__device__ __forceinline__ int member_of_block(const int* block_start, int c0, int c1, int b)
 {
-    int lo = 0, hi = ncase - 1;
-    const int b = (int)blockIdx.x;
+    int lo = c0, hi = c1 - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (block_start[mid] <= b) lo = mid; else hi = mid - 1;
     }
+    return lo;
+}
+
+// Batched internal source; members of the total split return at once.
+template <class S>
+__global__ void internal_source_batch_kernel(const CaseDesc* cases, const int* block_start, int ncase,
+                                             int flip)
+{
+    const int b = (int)blockIdx.x;
+    const int lo = member_of_block(block_start, 0, ncase, b);
     const CaseDesc& c = cases[lo];
     if (c.split != 1) return;
     const long long n = (long long)(b - block_start[lo]) * blockDim.x + threadIdx.x;
@@ -237,6 +302,37 @@ __global__ void internal_source_batch_kernel(const CaseDesc* cases, const int* b
     const int in = c.cur ^ flip;          // the state before the step; the new one is in ^ 1
     internal_source_node<S>(n, c.nx, c.ny, c.bc_x, c.bc_y, c.N, c.nord, c.mac[in ^ 1], c.mac[in], c.neq[in ^ 1],
                             c.wall, c.prof);
+}
+
+// Batched init and moments over members [c0, c1) of a batch (blocks from block_start[c0] = block0
+// on): each member's current state is buffer cur ^ flip; the fields of member c are
+// fld.f[c - c0].  Same per-node arithmetic as init_kernel and moments_kernel.
+template <class S>
+__global__ void init_batch_kernel(const CaseDesc* cases, const int* block_start, int c0, int c1, int block0,
+                                  int flip, MemberFields fld)
+{
+    const int b = block0 + (int)blockIdx.x;
+    const int c = member_of_block(block_start, c0, c1, b);
+    const CaseDesc& d = cases[c];
+    const long long n = (long long)(b - block_start[c]) * blockDim.x + threadIdx.x;
+    if (n >= d.N) return;
+    if (d.status->flags & kInputBad) return;   // the input check before rejected it: state unchanged
+    const int cur = d.cur ^ flip;
+    const double* const* in = fld.f[c - c0];
+    init_node<S>(d.mac[cur], d.neq[cur], d.N, d.nord, d.status, n, in[0][n], in[1][n], in[2][n], in[3][n]);
+}
+
+template <class S>
+__global__ void moments_batch_kernel(const CaseDesc* cases, const int* block_start, int c0, int c1, int block0,
+                                     int flip, MemberFields fld)
+{
+    const int b = block0 + (int)blockIdx.x;
+    const int c = member_of_block(block_start, c0, c1, b);
+    const CaseDesc& d = cases[c];
+    const long long n = (long long)(b - block_start[c]) * blockDim.x + threadIdx.x;
+    if (n >= d.N) return;
+    const int cur = d.cur ^ flip;
+    node_moments<S>(d.mac[cur], d.neq[cur], d.N, d.nord, d.split, d.cv, n, fld.f[c - c0]);
 }
 
 }  // namespace pond

@@ -51,4 +51,20 @@ cudaError_t POND_CAT(internal_source_batch, POND_PREC)(const CaseDesc* cases, co
     return cudaGetLastError();
 }
 
+cudaError_t POND_CAT(init_batch, POND_PREC)(const CaseDesc* cases, const int* block_start, int c0, int c1,
+                                            int block0, int blocks, int flip, const MemberFields& fld,
+                                            cudaStream_t s)
+{
+    init_batch_kernel<POND_S><<<blocks, 256, 0, s>>>(cases, block_start, c0, c1, block0, flip, fld);
+    return cudaGetLastError();
+}
+
+cudaError_t POND_CAT(moments_batch, POND_PREC)(const CaseDesc* cases, const int* block_start, int c0, int c1,
+                                               int block0, int blocks, int flip, const MemberFields& fld,
+                                               cudaStream_t s)
+{
+    moments_batch_kernel<POND_S><<<blocks, 256, 0, s>>>(cases, block_start, c0, c1, block0, flip, fld);
+    return cudaGetLastError();
+}
+
 }  // namespace pond

@@ -336,4 +336,11 @@ struct DevStatus {
     unsigned long long pad[2];
 };
 
+// Four [N] arrays (rho, u_x, u_y, T) for each member of a batched auxiliary launch over
+// members [c0, c0 + count), count <= kAuxChunk, passed by value as a kernel argument.
+constexpr int kAuxChunk = 64;
+struct MemberFields {
+    double* f[kAuxChunk][4];
+};
+
 }  // namespace pond

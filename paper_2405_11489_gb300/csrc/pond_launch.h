@@ -58,7 +58,13 @@ POND_DECLARE_STEP_ALL(bf16)
                                 double* uy, double* T, cudaStream_t s);                          \
     cudaError_t internal_source_##PREC(const AuxParams& p, cudaStream_t s);                        \
     cudaError_t internal_source_batch_##PREC(const CaseDesc* cases, const int* block_start,        \
-                                             int ncase, int flip, int blocks, cudaStream_t s);
+                                             int ncase, int flip, int blocks, cudaStream_t s);     \
+    cudaError_t init_batch_##PREC(const CaseDesc* cases, const int* block_start, int c0, int c1,   \
+                                  int block0, int blocks, int flip, const MemberFields& fld,       \
+                                  cudaStream_t s);                                                 \
+    cudaError_t moments_batch_##PREC(const CaseDesc* cases, const int* block_start, int c0, int c1, \
+                                     int block0, int blocks, int flip, const MemberFields& fld,    \
+                                     cudaStream_t s);
 
 POND_DECLARE_AUX(f64)
 POND_DECLARE_AUX(f32)

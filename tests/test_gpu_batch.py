@@ -177,3 +177,61 @@ def test_page_locked_host_buffers_are_used_in_place(pond):
     after = b[0].export_state()
     assert torch.equal(before[0], after[0]) and torch.equal(before[1], after[1])
     batch.close()
+
+
+@pytest.mark.parametrize("split", ["total", "internal"])
+def test_batch_state_calls_over_several_launch_chunks(pond, split):
+    """More members than one batched auxiliary launch takes (64): uneven tubes, host
+    (pageable and page-locked) and device fields, against the per-member calls bit for bit;
+    a bad value in a member of a later chunk is rejected and changes no member."""
+    import torch
+    cases = W.tube_batch(count=150, seed=5, nmin=40, nmax=700)
+    ref = _tube_sims(pond, cases, split=split)
+    for s in ref:
+        s.step(2)
+    sims = _tube_sims(pond, cases, split=split)
+    for s in sims:
+        s.step(1)                                          # states to be replaced
+    batch = pond.Batch(sims)
+    batch.set_state([(c.rho, c.ux, c.uy, c.T) for c in cases])
+    batch.step(2)
+    for got, s in zip(batch.moments(), ref):
+        for x, y in zip(got, s.moments()):
+            assert np.array_equal(x, y)
+    # page-locked in and out
+    pinned = [tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (c.rho, c.ux, c.uy, c.T))
+              for c in cases]
+    assert pond.pond_batch_set_state(batch.handle, *[[f[k].data_ptr() for f in pinned] for k in range(4)], 0) == 0
+    batch.step(2)
+    outs = [[torch.empty(c.ny, c.nx, dtype=torch.float64).pin_memory() for _ in range(4)] for c in cases]
+    rc = pond.pond_batch_get_moments(batch.handle, *[[o[k].data_ptr() for o in outs] for k in range(4)], 0)
+    assert rc in (pond.POND_OK, pond.POND_ENOCONV)
+    for o, s in zip(outs, ref):
+        for u, v in zip(s.moments(), o):
+            assert np.array_equal(u, v.numpy())
+    # device in and out
+    dev = [tuple(torch.as_tensor(a, device="cuda") for a in (c.rho, c.ux, c.uy, c.T)) for c in cases]
+    batch.set_state(dev)
+    batch.step(2)
+    douts = [[torch.empty(c.ny, c.nx, dtype=torch.float64, device="cuda") for _ in range(4)] for c in cases]
+    rc = pond.pond_batch_get_moments(batch.handle, *[[o[k].data_ptr() for o in douts] for k in range(4)], 1)
+    assert rc in (pond.POND_OK, pond.POND_ENOCONV)
+    for o, s in zip(douts, ref):
+        for u, v in zip(s.moments(), o):
+            assert np.array_equal(u, v.cpu().numpy())
+    # a bad value in member 130 (third chunk)
+    before = [s.export_state() for s in sims]
+    fields = [(c.rho.copy(), c.ux.copy(), c.uy.copy(), c.T.copy()) for c in cases]
+    fields[130][0][0, 3] = float("inf")
+    with pytest.raises(pond.PondError):
+        batch.set_state(fields)
+    # and the same through page-locked input (read in place by the staging kernel)
+    bad = [tuple(t.clone().pin_memory() for t in f) for f in pinned]
+    bad[130][3][0, 7] = -2.0
+    rc = pond.pond_batch_set_state(batch.handle, *[[f[k].data_ptr() for f in bad] for k in range(4)], 0)
+    assert rc == pond.POND_EINVAL
+    for s, (mac, neq) in zip(sims, before):
+        m2, n2 = s.export_state()
+        assert torch.equal(mac, m2) and torch.equal(neq, n2)
+        assert s.stats()[0] == pond.POND_OK
+    batch.close()
