@@ -924,10 +924,11 @@ __global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
                                 for (int q = 0; q <= NG; ++q) acc[e][b][q] = R(0);
                         if (rows_in && cols_in) {
                             const R* rowp = sm + ((size_t)(y + rmin - oy) * bw + tx0) * REC;
-                            // FP32: two rows per trip, so that one row's loads overlap the other's
-                            // FMAs (260 -> 257.5 us; three or four rows were slower); FP64 had
-                            // more spills with it
-                            constexpr int kRowUnroll = std::is_same<R, float>::value ? 2 : 1;
+                            // FP32, 4-point stencils: two rows per trip, so that one row's loads
+                            // overlap the other's FMAs (260 -> 257.5 us; three or four rows were
+                            // slower); FP64 had more spills with it, and 3-point stencils ran
+                            // 2 % slower
+                            constexpr int kRowUnroll = (std::is_same<R, float>::value && P == 4) ? 2 : 1;
 #pragma unroll kRowUnroll
                             for (int r = rmin; r <= rmax; ++r, rowp += (size_t)bw * REC) {
                                 R X[ND][NC];
