@@ -280,3 +280,41 @@ def test_jet_2000x1000_sampled_parity(pond, orc):
     jet and ambient states, profiled x-low inflow) at Mach 1.5, in mixed FP32."""
     case = W.jet(ma=1.5)
     _sampled_step(pond, orc, case, "fp32", "total", 3, 5e-5, 2e-4, seed=4)
+
+
+# Moments handed to the caller from populations far from their frame's equilibrium: the
+# mixed modes form the stored coefficients' contribution in FP32 and add it to the FP64
+# frame (the moment definitions of Sec. II rearranged relative to the frame), so the
+# corrections u - u_frame and T - T_frame are large here (5 % non-equilibrium parts).  On
+# these fields a wrong sign on a term of a rearrangement gives errors from 6e-4 (the |d|^2
+# term) to 3e-2 (u_frame . d, the A_20 + A_02 term), above the FP32 and FP16 bounds; the
+# bounds are the storage rounding of the coefficients.
+@pytest.mark.parametrize("split,lattice", [("total", 16), ("internal", 16), ("nt", 16), ("nt", 25),
+                                           ("total", 25)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6), ("fp16", 3e-4),
+                                           ("bf16", 3e-3)])
+def test_moments_of_non_equilibrium_populations(pond, orc, split, lattice, precision, tol):
+    nx, ny = 23, 9
+    rng = np.random.default_rng(lattice + len(split))
+    ocfg = orc.make_config(nx, ny, lattice=lattice, split=split, gamma=1.4, mu=0.02)
+    y, x = np.mgrid[0:ny, 0:nx]
+    rho = 1.0 + 0.1 * np.sin(2 * np.pi * x / nx) + 0.02 * rng.standard_normal((ny, nx))
+    ux = 0.9 + 0.2 * np.cos(2 * np.pi * y / ny)
+    uy = -0.4 + 0.1 * np.sin(2 * np.pi * (x + y) / nx)
+    T = 0.7 * (1 + 0.1 * np.cos(2 * np.pi * x / nx))
+    st = orc.init_state(ocfg, rho, ux, uy, T)
+    Q = ocfg.q1 * ocfg.q1
+    st.f = st.f * (1 + 0.05 * rng.standard_normal((Q, ny, nx)))
+    st.g = st.g * (1 + 0.05 * rng.standard_normal((Q, ny, nx)))
+    o_rho, o_ux, o_uy, o_T, _ = orc.moments(ocfg, st)
+    assert np.max(np.abs(o_ux - st.ux)) > 1e-3 and np.max(np.abs(o_T - st.T)) > 1e-3
+    sim = pond.Simulation(pond.Config(nx=nx, ny=ny, lattice=lattice, split=split, precision=precision,
+                                      gamma=1.4, mu=0.02))
+    sim.set_populations(st.f, st.g, st.ux, st.uy, st.T)
+    g_rho, g_ux, g_uy, g_T = sim.moments(allow=(pond.POND_OK,))
+    speed = max(np.max(np.abs(o_ux)), np.max(np.abs(o_uy)), np.sqrt(np.max(o_T)))
+    assert np.max(np.abs(g_rho - o_rho)) <= tol * np.max(o_rho)
+    assert np.max(np.abs(g_ux - o_ux)) <= tol * speed
+    assert np.max(np.abs(g_uy - o_uy)) <= tol * speed
+    assert np.max(np.abs(g_T - o_T)) <= tol * np.max(o_T)
+    sim.close()
