@@ -233,7 +233,9 @@ __device__ __forceinline__ void internal_source_node(long long n, int nx, int ny
                                                      const double* mac_prev, void* neq,
                                                      const double (*wall)[4], const double* const* prof)
 {
-    const int x = (int)(n % nx), y = (int)(n / nx);
+    // 32-bit division where the grid allows it (64-bit division is a long software sequence)
+    const int x = N <= 0x7fffffffll ? (int)n % nx : (int)(n % nx);
+    const int y = N <= 0x7fffffffll ? (int)n / nx : (int)(n / nx);
     const double* ux1 = mac + N;
     const double* uy1 = mac + 2 * N;
     // neighbour velocities: mapped nodes, or the prescribed velocity beyond a prescribed side
@@ -251,19 +253,37 @@ __device__ __forceinline__ void internal_source_node(long long n, int nx, int ny
             vy[k] = uy1[m];
         }
     }
-    double dxux = 0.5 * (vx[0] - vx[1]), dyux = 0.5 * (vx[2] - vx[3]);
-    double dxuy = 0.5 * (vy[0] - vy[1]), dyuy = 0.5 * (vy[2] - vy[3]);
-    double rho = mac[n], ux = ux1[n], uy = uy1[n], T = mac[3 * N + n];
-    double dtux = ux - mac_prev[N + n], dtuy = uy - mac_prev[2 * N + n];
-    double Dux = dtux + ux * dxux + uy * dyux;
-    double Duy = dtuy + ux * dxuy + uy * dyuy;
-    double rT = rho * T, rsT = rho * sqrt(T);
+    const double rho = mac[n], ux = ux1[n], uy = uy1[n], T = mac[3 * N + n];
     S* q = reinterpret_cast<S*>(neq);
-    double G[6] = {-rT * (dxux + dyuy), -rsT * Dux, -rsT * Duy, -2.0 * rT * dxux,
-                   -rT * (dyux + dxuy), -2.0 * rT * dyuy};
-    for (int m = 0; m < 6; ++m) {
-        S* a = q + (long long)(ncoef(nord) - 1 + m) * N + n;
-        sto_put<S, double>(a, sto_load<S>(a) + G[m]);
+    if constexpr (std::is_same<S, double>::value) {
+        double dxux = 0.5 * (vx[0] - vx[1]), dyux = 0.5 * (vx[2] - vx[3]);
+        double dxuy = 0.5 * (vy[0] - vy[1]), dyuy = 0.5 * (vy[2] - vy[3]);
+        double dtux = ux - mac_prev[N + n], dtuy = uy - mac_prev[2 * N + n];
+        double Dux = dtux + ux * dxux + uy * dyux;
+        double Duy = dtuy + ux * dxuy + uy * dyuy;
+        double rT = rho * T, rsT = rho * sqrt(T);
+        double G[6] = {-rT * (dxux + dyuy), -rsT * Dux, -rsT * Duy, -2.0 * rT * dxux,
+                       -rT * (dyux + dxuy), -2.0 * rT * dyuy};
+        for (int m = 0; m < 6; ++m) {
+            S* a = q + (long long)(ncoef(nord) - 1 + m) * N + n;
+            sto_put<S, double>(a, sto_load<S>(a) + G[m]);
+        }
+    } else {
+        // mixed modes: the velocity differences taken in FP64 (small against u), the source
+        // formed in FP32 like the coefficients it is added to (FP64 is slow on this part)
+        const float dxux = 0.5f * (float)(vx[0] - vx[1]), dyux = 0.5f * (float)(vx[2] - vx[3]);
+        const float dxuy = 0.5f * (float)(vy[0] - vy[1]), dyuy = 0.5f * (float)(vy[2] - vy[3]);
+        const float dtux = (float)(ux - mac_prev[N + n]), dtuy = (float)(uy - mac_prev[2 * N + n]);
+        const float uxf = (float)ux, uyf = (float)uy, rf = (float)rho, Tf = (float)T;
+        const float Dux = dtux + uxf * dxux + uyf * dyux;
+        const float Duy = dtuy + uxf * dxuy + uyf * dyuy;
+        const float rT = rf * Tf, rsT = rf * sqrtf(Tf);
+        const float G[6] = {-rT * (dxux + dyuy), -rsT * Dux, -rsT * Duy, -2.0f * rT * dxux,
+                            -rT * (dyux + dxuy), -2.0f * rT * dyuy};
+        for (int m = 0; m < 6; ++m) {
+            S* a = q + (long long)(ncoef(nord) - 1 + m) * N + n;
+            sto_put<S, float>(a, sto_loadf<S>(a) + G[m]);
+        }
     }
 }
 
