@@ -237,7 +237,7 @@ def pond_batch_create(handles, workspace_ptr: int, nbytes: int, stream_ptr: int)
 def _ptr_array(ptrs):
     if ptrs is None:
         return None
-    return (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(p) if p else None for p in ptrs])
+    return (ctypes.c_void_p * len(ptrs))(*[p or None for p in ptrs])
 
 
 def pond_batch_set_state(h, rho, ux, uy, T, on_device: int) -> int:
