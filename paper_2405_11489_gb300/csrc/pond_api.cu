@@ -595,7 +595,7 @@ int pond_set_state(pond_sim* s, const double* rho, const double* ux, const doubl
     // about 5 % of this call, for four batched 256^2 grids) and
     // checked there on the device (the host's single core would take far longer over the same
     // bytes than the copy); the initialisation skips a rejected input, and one synchronisation
-    // returns the verdict.
+    // returns the outcome.
     const double* in[4] = {rho, ux, uy, T};
     const double* src[4];
     double* stage = mac_ptr(s, 1 - s->cur);
