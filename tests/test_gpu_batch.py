@@ -235,3 +235,36 @@ def test_batch_state_calls_over_several_launch_chunks(pond, split):
         assert torch.equal(mac, m2) and torch.equal(neq, n2)
         assert s.stats()[0] == pond.POND_OK
     batch.close()
+
+
+@pytest.mark.parametrize("where", ["device", "page-locked"])
+def test_batched_moments_skip_absent_outputs(pond, where):
+    """pond_batch_get_moments with whole fields absent (NULL arrays) and single members'
+    buffers absent (NULL entries): the given buffers get the per-member values, bit for bit,
+    and the absent ones are skipped."""
+    import torch
+    cases = W.tube_batch(count=70, seed=8, nmin=40, nmax=300)     # two launch chunks
+    ref = _tube_sims(pond, cases)
+    sims = _tube_sims(pond, cases)
+    for s in ref:
+        s.step(2)
+    batch = pond.Batch(sims)
+    batch.step(2)
+    dev = where == "device"
+
+    def buf(c):
+        if dev:
+            return torch.full((c.ny, c.nx), -7.0, dtype=torch.float64, device="cuda")
+        return torch.full((c.ny, c.nx), -7.0, dtype=torch.float64).pin_memory()
+
+    T_out = [buf(c) for c in cases]
+    ux_out = [buf(c) if i % 3 else None for i, c in enumerate(cases)]   # every third member absent
+    rc = pond.pond_batch_get_moments(batch.handle, None, [o.data_ptr() if o is not None else 0 for o in ux_out],
+                                     None, [o.data_ptr() for o in T_out], 1 if dev else 0)
+    assert rc in (pond.POND_OK, pond.POND_ENOCONV)
+    for i, s in enumerate(ref):
+        rho, ux, uy, T = s.moments()
+        assert np.array_equal(T_out[i].cpu().numpy(), T)
+        if ux_out[i] is not None:
+            assert np.array_equal(ux_out[i].cpu().numpy(), ux)
+    batch.close()
