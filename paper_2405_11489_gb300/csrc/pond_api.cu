@@ -174,10 +174,9 @@ void side_profiles(pond_sim* s, const double* prof[4])
 
 int cuda_status(cudaError_t e);
 
-// Blocks of the step kernel resident at once on the current device: 256 threads per SM (255
-// registers a thread fill an SM's register file), i.e. one CTA per SM on 2-D grids and two on
-// quasi-1-D ones.  0 if the query fails.
-int resident_step_blocks(bool one_d)
+// Blocks of the step kernel resident at once on the current device (step_blocks_per_sm per
+// SM: the distance of the next-wave L2 prefetch).  0 if the query fails.
+int resident_step_blocks(const pond_config& c, bool one_d)
 {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -185,7 +184,7 @@ int resident_step_blocks(bool one_d)
         cudaGetLastError();
         return 0;
     }
-    return sms * (kStepThreads2D / step_threads(one_d));
+    return sms * step_blocks_per_sm(one_d, c.lattice == POND_D2Q25, c.precision == POND_FP64);
 }
 
 // Copy states [n][4] (host or device) into side w's profile, or its uniform state when
@@ -638,7 +637,7 @@ int pond_step(pond_sim* s, int32_t nsteps)
     p.lat = s->lat;
     p.box_w = s->box_w;
     p.box_h = s->box_h;
-    p.ahead = resident_step_blocks(s->one_d);
+    p.ahead = resident_step_blocks(s->cfg, s->one_d);
     const double* prof[4];
     side_profiles(s, prof);
     fill_case(c, status_ptr(s), p.one, prof);
@@ -819,7 +818,7 @@ cudaError_t batch_launch_step(pond_batch* b)
     p.lat = s0->lat;
     p.box_w = s0->box_w;
     p.box_h = s0->box_h;
-    p.ahead = resident_step_blocks(s0->one_d);
+    p.ahead = resident_step_blocks(s0->cfg, s0->one_d);
     p.flip = b->flip;
     p.ncase = b->count;
     p.cases = b->d_cases;

@@ -19,6 +19,14 @@ struct CaseDesc;
 constexpr int kStepThreads2D = 256;
 constexpr int kStepThreads1D = 128;
 constexpr int step_threads(bool one_d) { return one_d ? kStepThreads1D : kStepThreads2D; }
+// CTAs of the step kernel resident per SM, the launch bound it is compiled for: one on 2-D
+// grids and two on quasi-1-D grids (registers: about 255 a thread), three on quasi-1-D D2Q16
+// grids with FP32 arithmetic, whose kernel is held to 168 registers (90 B of spills; the 256
+// tubes 2410 -> 2820 MLUPS; four per SM spilled 400 B and ran at 2360).
+constexpr int step_blocks_per_sm(bool one_d, bool d2q25, bool fp64)
+{
+    return !one_d ? 1 : (!d2q25 && !fp64) ? 3 : 2;
+}
 
 struct Launch {
     dim3 grid, block;

@@ -37,6 +37,7 @@
 #pragma once
 
 #include "pond_device.cuh"
+#include "pond_launch.h"
 
 namespace pond {
 
@@ -789,9 +790,11 @@ __device__ __forceinline__ void prefetch_next_wave(const StepParams& pp, int TX,
 }
 
 // Single-thread-per-node kernel: FP64 arithmetic (2-D and quasi-1-D) and the FP32 quasi-1-D
-// grids.  One CTA per tile of TPB nodes.
+// grids.  One CTA per tile of TPB nodes; CTAs resident per SM as step_blocks_per_sm says
+// (the quasi-1-D D2Q16 kernel with FP32 arithmetic is held to three per SM).
 template <class S, class R, int Q1, int P, bool ONE_D, int TPB>
-__global__ void __launch_bounds__(TPB, 1) step_kernel(const StepParams pp)
+__global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::is_same<R, double>::value))
+    step_kernel(const StepParams pp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
