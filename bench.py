@@ -42,33 +42,49 @@ MU = 0.05
 METRIC = "PonD-DDF MLUPS, mixed-prec vs plain FP64 at stated L1 err; serving p50/p99 latency"
 WORKLOAD = ("periodic 256x256 shear wave (u_y = 0.05 sin 2pi x/L) + Gaussian thermal pulse "
             "(dT/T = 1e-3, width 16), background Ma 0.5/1/1.5/2 (4 grids), D2Q16 total split")
-# Pipe peaks from unit counts at the maximum SM clock (2.070 GHz): FP32 152 SMs x 128 lanes x
-# 2 flop; FP64 152 SMs x 2 FMA per clock x 2 flop (= the part's nominal 1.25 TFLOP/s).
-SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
-FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
-FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1e3
-# Algorithmic work of one node update (D2Q16), K = measured mean iterations:
-#  FP32: per predictor-corrector iteration and population, a 16-tap interpolation of 20
-#        Hermite coefficients plus the frame move, reconstruction and moment sums (~800 flop);
-#        plus ~1000 flop per update for staging and collision: 800 Q K + 1000;
+# Unit counts of the CUDA-core pipes, flop per SM per clock: FP32 128 lanes x FMA (2 flop);
+# FP64 2 FMA.  The peaks are these times the SM count read from the device and the SM clock
+# sampled (nvidia-smi) while the timed kernels run.
+FP32_FLOP_PER_SM_CLK = 128 * 2
+FP64_FLOP_PER_SM_CLK = 2 * 2
+FALLBACK_SM_MHZ = 2070.0        # the part's maximum SM clock, used only if sampling fails
+# Algorithmic work of one node update, K = measured mean predictor-corrector iterations,
+# for Q populations and P-point Lagrange stencils:
+#  FP32: per iteration and population, the interpolation of the 20 order-<=3 Hermite
+#        coefficients (f and g) over the stencil's taps (2 flop x 20 x P^2 in 2-D, x P along
+#        the single row of a quasi-1-D grid, whose y taps all read that row) plus ~160 flop
+#        for the frame move, the reconstruction and the moment sums; plus ~1000 flop per
+#        update for staging and collision.  Cubic 2-D D2Q16: 800 Q K + 1000.
 #  FP64: the conserved-moment sums (~130) and the frame update (~20) per iteration, plus ~50
 #        per update (temperature recovery, final frame): 150 K + 50.
-# The step's roofline time is F32/P32 + F64/P64 (the two pipes' work in sequence); `achieved`
-# is expressed in FP32-equivalent flop (FP64 flop weighted by P32/P64) per second against P32,
-# so that achieved / peak = roofline time / measured time.
-FLOP_PER_POP_ITER = 800.0
+# The mixed-precision kernels execute all of it on the FP32 pipe (their moment sums and frame
+# updates are FP32 deviations from FP64 reference values), so the roofline time of a node
+# update is (F32 + F64) / P32, and the fraction of the roofline is that over the measured
+# time.  The plain FP64 step executes all of it on the FP64 pipe: (F32 + F64) / P64.
+FLOP_PER_POP_ITER_OVERHEAD = 160.0
 FLOP_PER_UPDATE = 1000.0
 F64_PER_ITER = 150.0
 F64_PER_UPDATE = 50.0
 
 
-def roofline_terms(nodes, K, seconds):
-    """FP32 and FP64 algorithmic flop of `nodes` updates at mean iterations K, and the
-    roofline fraction (F32/P32 + F64/P64) / seconds."""
-    f32 = nodes * (FLOP_PER_POP_ITER * 16 * K + FLOP_PER_UPDATE)
+def pipe_peaks(sms, sm_mhz):
+    """FP32 and FP64 CUDA-core peaks (TFLOP/s) from the unit counts at sm_mhz."""
+    hz = sm_mhz * 1e6
+    return sms * FP32_FLOP_PER_SM_CLK * hz / 1e12, sms * FP64_FLOP_PER_SM_CLK * hz / 1e12
+
+
+def algorithmic_flops(nodes, K, q=16, taps=4, one_d=False):
+    """FP32 and FP64 algorithmic flop of `nodes` updates at mean iterations K."""
+    n_taps = taps if one_d else taps * taps
+    per_pop_iter = 2.0 * 20 * n_taps + FLOP_PER_POP_ITER_OVERHEAD
+    f32 = nodes * (per_pop_iter * q * K + FLOP_PER_UPDATE)
     f64 = nodes * (F64_PER_ITER * K + F64_PER_UPDATE)
-    t_roof = f32 / (FP32_PEAK_TFLOPS * 1e12) + f64 / (FP64_PEAK_TFLOPS * 1e12)
-    return f32, f64, t_roof / seconds
+    return f32, f64
+
+
+def roofline_fraction(f32, f64, seconds, peak_tflops):
+    """Roofline time of the work on one pipe, (F32 + F64) / peak, over the measured time."""
+    return (f32 + f64) / (peak_tflops * 1e12) / seconds
 
 
 def case_fields(ma):
@@ -247,6 +263,7 @@ def tube_batch_rates(torch, pond, device, steps=20):
     out["launches_per_step"] = {"per_case_loop": len(cases), "batched": 1}
     batch.close()
     out["statuses"] = sorted({pond.strerror(s.stats()[0]) for s in sims})
+    out["pc_iters_mean"] = mean_iters(sims)
     out["interp_order"] = 2
     for s in sims:
         s.close()
@@ -420,6 +437,31 @@ def decay_physics(torch, pond, device, steps=2000):
     return out
 
 
+def alu_peak(torch, pond, device, sms, seconds=0.3, launches=3):
+    """The FP32 and FP64 FMA rates of the device's CUDA-core pipes (pond_alu_peak: independent
+    FMA chains, 4 blocks of 256 threads per SM), each over `launches` launches of about
+    `seconds` each, with the SM clock sampled meanwhile; beside each, the unit-count peak at
+    the sampled clock and the measured fraction of it."""
+    out = {}
+    stream = torch.cuda.current_stream(device).cuda_stream
+    for name, fp64 in (("fp32", False), ("fp64", True)):
+        flop, ms = pond.pond_alu_peak(fp64, 64, stream)                  # warm-up, sizing
+        iters = max(64, int(64 * seconds * 1e3 / max(ms, 1e-3)))
+        rates = []
+        with ClockSampler(device.index or 0) as clk:
+            for _ in range(launches):
+                flop, ms = pond.pond_alu_peak(fp64, iters, stream)
+                rates.append(flop / (ms * 1e-3) / 1e12)
+        c = clk.summary()
+        mhz = c["sm_mhz"] or FALLBACK_SM_MHZ
+        unit = pipe_peaks(sms, mhz)[1 if fp64 else 0]
+        best = max(rates)
+        out[name] = {"tflops": best, "sm_mhz": c["sm_mhz"], "clock_reasons": c["reasons"],
+                     "unit_count_tflops_at_that_clock": unit, "fraction_of_unit_count": best / unit,
+                     "launch_ms": ms, "launches": launches}
+    return out
+
+
 def e2e_rate(torch, pond, device, steps, warmup):
     """MLUPS of the benchmark's workload (the four grids, one batched launch per time step)
     through the public C-ABI with host buffers: every step uploads the four grids' input
@@ -570,6 +612,26 @@ def profile_case(torch, pond, device, stream, flush, args):
     return 0
 
 
+def other_rooflines(tubes, others, p32, sm_mhz):
+    """ALU roofline fractions of the larger workloads: the 1024^2 Riemann problem (total split,
+    3-point stencils, 2-D) and the 256 tubes in one batched launch per step (3-point stencils,
+    quasi-1-D), each from its measured MLUPS and mean iterations, against the FP32 peak at the
+    headline's sampled SM clock."""
+    out = {}
+    rie = others["riemann_1024_total_fp32"]
+    cases = (("riemann_1024_total_fp32", rie["mlups"], rie["pc_iters_mean"], False),
+             ("tube_batch_256_batched", tubes["batched_launch_mlups"], tubes["pc_iters_mean"], True))
+    for name, mlups, K, one_d in cases:
+        f32, f64 = algorithmic_flops(1, K, taps=3, one_d=one_d)
+        t = 1.0 / (mlups * 1e6)                      # seconds per node update
+        out[name] = {"bound": "alu", "achieved": (f32 + f64) / t / 1e12, "peak": p32,
+                     "unit": "TFLOP/s", "frac": roofline_fraction(f32, f64, t, p32),
+                     "flop_per_update": f32 + f64, "pc_iters_mean": K, "mlups": mlups,
+                     "stencil": "3-point, %s" % ("quasi-1-D (x taps only)" if one_d else "2-D (3 x 3 taps)"),
+                     "sm_mhz": sm_mhz}
+    return out
+
+
 def profiled_traffic(key):
     """DRAM bytes (read + write) per launch of the timed kernel from the committed ncu record,
     or None when the record is missing or the kernel sources have changed since the capture."""
@@ -635,9 +697,14 @@ def main():
     nodes_per_step = len(MACHS) * NX * NY
     value = whole_job_mlups(world, nodes_per_step, step_ms)
     launch_ms = sum(per_launch) / len(per_launch)
-    f32_launch, f64_launch, frac = roofline_terms(nodes_per_step, K, launch_ms * 1e-3)
-    flops_per_launch = f32_launch + f64_launch * FP32_PEAK_TFLOPS / FP64_PEAK_TFLOPS
+    clocks = clk.summary()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    sm_mhz = clocks["sm_mhz"] or FALLBACK_SM_MHZ
+    p32, p64 = pipe_peaks(sms, sm_mhz)
+    f32_launch, f64_launch = algorithmic_flops(nodes_per_step, K)
+    flops_per_launch = f32_launch + f64_launch
     achieved = flops_per_launch / (launch_ms * 1e-3) / 1e12
+    frac = roofline_fraction(f32_launch, f64_launch, launch_ms * 1e-3, p32)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -646,7 +713,7 @@ def main():
     if args.quick:
         print(json.dumps({"metric": METRIC, "value": value, "unit": "MLUPS", "quick": True,
                           "ms_per_step": step_ms, "pc_iters_mean": K, "launch_ms": launch_ms,
-                          "achieved_tflops": achieved}))
+                          "achieved_tflops": achieved, "roofline_frac": frac, "clocks": clocks}))
         return 0
     # plain FP64 GPU step on the same workload (fewer steps: it is ~two orders slower)
     sims64, batch64, tune64 = make_sims(pond, "fp64", device, stream, tune=True)
@@ -664,6 +731,8 @@ def main():
     from paper_2405_11489_gb300.serve import serve_benchmark
     serving = serve_benchmark(args.serve_requests, rate=50.0, seed=2, load=0.7, chunk=32,
                               device=device)
+    alu = alu_peak(torch, pond, device, sms)
+    others_roofline = other_rooflines(tubes, others, p32, sm_mhz)
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     traffic = profiled_traffic("step_kernel_fp32_batched_4x256x256")
     line = {
@@ -683,8 +752,8 @@ def main():
                  "ms_per_step": fp64_ms, "speedup_mixed_over_fp64": fp64_ms / step_ms,
                  "pc_iters_mean": K64,
                  # every flop on the FP64 pipe: (F32 + F64) / P64 over the measured time
-                 "roofline_frac": sum(roofline_terms(nodes_per_step, K64, 1.0)[:2])
-                                  / (FP64_PEAK_TFLOPS * 1e12) / (fp64_ms * 1e-3),
+                 "roofline_frac": roofline_fraction(*algorithmic_flops(nodes_per_step, K64),
+                                                    fp64_ms * 1e-3, p64),
                  "launch_shape": "tile %dx%d, halo %d (autotuned)" % (tune64["tile_x"], tune64["tile_y"],
                                                                     tune64["halo"])},
         "l1_err_mixed_vs_fp64": err,
@@ -692,20 +761,25 @@ def main():
         "tube_batch": tubes,
         "other_configs": others,
         "serving": serving,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "flop_basis": "FP32-equivalent: F32 + F64 x P32/P64; frac = (F32/P32 + F64/P64) / t",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": p32, "unit": "TFLOP/s",
+                     "frac": frac, "traffic": traffic,
+                     "flop_basis": "algorithmic FP32 + FP64 flop per launch, all executed on the "
+                                   "FP32 pipe (the mixed kernel forms its moment sums and frame "
+                                   "updates as FP32 deviations); frac = (F32 + F64) / P32 / t",
                      "f32_flop_per_launch": f32_launch, "f64_flop_per_launch": f64_launch,
-                     "p64_tflops": FP64_PEAK_TFLOPS,
-                     "fp32_pipe_frac": f32_launch / (launch_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
                      "kernel": "step_kernel<float,float,4,4,false,256> (batched over the 4 grids)",
-                     "peak_basis": "unit counts at 2.07 GHz: FP32 152 SM x 128 lanes x 2 flop; "
-                                   "FP64 152 SM x 2 FMA x 2 flop",
-                     "flops_per_launch": flops_per_launch, "launch_ms": launch_ms},
+                     "peak_basis": "unit counts: %d SMs (device) x 128 FP32 lanes x 2 flop x %.0f MHz "
+                                   "(median SM clock sampled during the timed launches)" % (sms, sm_mhz),
+                     "sms": sms, "sm_mhz": sm_mhz,
+                     "measured_fma_tflops": alu["fp32"]["tflops"],
+                     "frac_of_measured_fma": achieved / alu["fp32"]["tflops"],
+                     "launch_ms": launch_ms},
+        "rooflines_other": others_roofline,
+        "alu_peak": alu,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": len(per_launch),
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     print(json.dumps(line))
     if world > 1:

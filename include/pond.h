@@ -303,17 +303,34 @@ void pond_autotune_clear(void);
  *    bytes (FP64/FP32/FP16/BF16), i.e. N <= 91 178 / 63 548 (FP64), 155 341 / 113 357
  *    (FP32), 239 669 / 186 408 (FP16/BF16) on D2Q16 / D2Q25; larger grids return
  *    POND_ENOMEM without touching the GPU.
- *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) and sets the step kernel's shared-memory limit; make that first
- *    call before any stream capture on that device.
+ *  - Set-up: the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) and the SM count, and the first call for each kernel variant
+ *    (precision, lattice, 1-D or 2-D, interpolation order, launch shape) sets the step
+ *    kernel's shared-memory limit; make those first calls before any stream capture on that
+ *    device.  Later calls query only the current device and context (cudaGetDevice and the
+ *    driver's context ID) and enqueue the status clear and the kernels.  If the current
+ *    context changes (after cudaDeviceReset, or another context made current), the next
+ *    call repeats the set-up.
  *  - Every call uses the same array and it keeps the last call's contents; the status
  *    block is cleared at the start of each call.  Calls that overlap on the GPU (other
  *    streams, other host threads) race on the array: serialise them.
  *  - stats: if non-NULL the call synchronises cuda_stream, fills *stats for this call and
- *    returns the sticky status; if NULL it returns once the work is enqueued. */
+ *    returns the sticky status; if NULL it returns once the work is enqueued, and the
+ *    kernel-side outcomes of this call (POND_ENONPHYSICAL, POND_ENOCONV) are not reported
+ *    at all: the next call clears the status block. */
 #define POND_STATIC_SCRATCH_BYTES (16u << 20)
 int pond_step_static(const pond_config *cfg, double *mac, void *neq, int32_t nsteps,
                      void *cuda_stream, pond_stats *stats);
+
+/* ALU peak measurement.  (No counterpart in the paper: the measured denominator of the step
+ * kernel's roofline, which is bound by the CUDA-core FP32 pipe, or the FP64 pipe in the
+ * FP64 mode.)  Runs one launch of independent FMA chains, 4 blocks of 256 threads per SM,
+ * each thread 8 chains of 16 * iters dependent FMAs, on cuda_stream (NULL = legacy default
+ * stream) on the current device, and waits for it.  fp64: 0 = FP32 FMAs, 1 = FP64 FMAs.
+ * On success *flop = the flops executed (2 per FMA) and *ms = their CUDA-event time; divide
+ * for the rate.  Allocates nothing.  Errors: POND_EINVAL (iters <= 0, fp64 not 0 or 1, a
+ * NULL output), POND_ECUDA. */
+int pond_alu_peak(int32_t fp64, int32_t iters, void *cuda_stream, double *flop, float *ms);
 
 /* Static description of a status code. */
 const char *pond_strerror(int status);

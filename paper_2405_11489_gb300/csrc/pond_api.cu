@@ -1433,21 +1433,99 @@ namespace {
 static __device__ __align__(256) unsigned char g_pond_static_scratch[POND_STATIC_SCRATCH_BYTES];
 
 constexpr int kStaticMaxDevices = 64;
-std::mutex g_static_mutex;
-void* g_static_address[kStaticMaxDevices];   // device address of the array, per device
 
-// Set-up, once per device with that device current: the array's name is a host-side
-// stand-in, so its device address must be looked up before a kernel can be given it.
-int static_scratch(int dev, void** out)
+// Driver calls that identify the current context (resolved once through the runtime, so the
+// library does not link the driver library itself).  A context's ID is never reused within a
+// process, so a changed ID means the context was reset or replaced.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+std::once_flag g_ctx_fns_once;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// ID of the context current on this thread; 0 if none is current yet.
+int current_context_id(unsigned long long* id)
+{
+    std::call_once(g_ctx_fns_once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    if (!g_ctx_get_current || !g_ctx_get_id) return POND_ECUDA;
+    void* ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0) return POND_ECUDA;
+    *id = 0;
+    if (ctx && g_ctx_get_id(ctx, id) != 0) return POND_ECUDA;
+    return POND_OK;
+}
+
+// Per-device set-up of the allocation-free path, valid for one context: the array's device
+// address (its name in host code is only a stand-in), the SM count, and the launch shapes
+// already prepared (preparing one sets the step kernel's shared-memory limit).
+struct StaticShape {
+    int precision, lattice, interp_order, tile_x, tile_y, halo, one_d;
+    Shape sh;
+};
+struct StaticDevice {
+    unsigned long long ctx = 0;
+    void* addr = nullptr;
+    int sms = 0;
+    std::vector<StaticShape> shapes;
+};
+std::mutex g_static_mutex;
+StaticDevice g_static[kStaticMaxDevices];
+
+// The device's set-up for the current context (device dev current), done on first use and
+// again whenever the current context has changed.
+int static_device(int dev, StaticDevice** out)
 {
     std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_address[dev]) {
+    StaticDevice& d = g_static[dev];
+    unsigned long long ctx = 0;
+    int rc = current_context_id(&ctx);
+    if (rc != POND_OK) return rc;
+    if (!d.addr || ctx == 0 || ctx != d.ctx) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_pond_static_scratch);
         if (e != cudaSuccess || !p) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
-        g_static_address[dev] = p;
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_status(e);
+        rc = current_context_id(&ctx);       // the look-up made the device's context current
+        if (rc != POND_OK) return rc;
+        d.ctx = ctx;
+        d.addr = p;
+        d.sms = sms;
+        d.shapes.clear();
     }
-    *out = g_static_address[dev];
+    *out = &d;
+    return POND_OK;
+}
+
+// The launch shape for cfg on device d, prepared on first use (make_shape sets the kernel's
+// shared-memory limit) and reused afterwards.
+int static_shape(StaticDevice* d, const pond_config& c, Shape* out)
+{
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    const int one_d = c.ny == 1;
+    for (const StaticShape& s : d->shapes)
+        if (s.precision == c.precision && s.lattice == c.lattice && s.interp_order == c.interp_order &&
+            s.tile_x == c.tile_x && s.tile_y == c.tile_y && s.halo == c.halo && s.one_d == one_d) {
+            *out = s.sh;
+            return POND_OK;
+        }
+    StaticShape s{c.precision, c.lattice, c.interp_order, c.tile_x, c.tile_y, c.halo, one_d, Shape()};
+    int rc = make_shape(c, c.tile_x, c.tile_y, c.halo, &s.sh);
+    if (rc != POND_OK) return rc;
+    d->shapes.push_back(s);
+    *out = s.sh;
     return POND_OK;
 }
 
@@ -1468,10 +1546,10 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 0 || dev >= kStaticMaxDevices) return POND_EINVAL;
-    void* base = nullptr;
-    rc = static_scratch(dev, &base);
+    StaticDevice* sd = nullptr;
+    rc = static_device(dev, &sd);
     if (rc != POND_OK) return rc;
-    char* scratch = reinterpret_cast<char*>(base);
+    char* scratch = reinterpret_cast<char*>(sd->addr);
     double* smac = reinterpret_cast<double*>(scratch);
     void* sneq = scratch + off_neq;
     DevStatus* st = reinterpret_cast<DevStatus*>(scratch + off_status);
@@ -1479,7 +1557,7 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
 
     // launch shape of the step kernel, as pond_create chooses it
     Shape sh;
-    rc = make_shape(*cfg, cfg->tile_x, cfg->tile_y, cfg->halo, &sh);
+    rc = static_shape(sd, *cfg, &sh);
     if (rc != POND_OK) return rc;
     const bool one_d = sh.one_d;
     const int tx = sh.tx, ty = sh.ty, box_w = sh.box_w, box_h = sh.box_h;
@@ -1497,6 +1575,8 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     p.lat = lat;
     p.box_w = box_w;
     p.box_h = box_h;
+    // the next-wave L2 prefetch distance, as pond_step sets it: the blocks resident at once
+    p.ahead = sd->sms * step_blocks_per_sm(one_d, cfg->lattice == POND_D2Q25, cfg->precision == POND_FP64);
     fill_case(*cfg, st, p.one);
     Launch l;
     l.block = dim3(tx, ty, 1);

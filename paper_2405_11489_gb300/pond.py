@@ -42,7 +42,7 @@ EXPORTS = ("pond_config_default", "pond_workspace_bytes", "pond_create", "pond_s
            "pond_batch_workspace_bytes", "pond_batch_create", "pond_batch_step",
            "pond_batch_use_graph", "pond_batch_destroy", "pond_get_launch", "pond_set_launch",
            "pond_autotune", "pond_autotune_clear", "pond_set_boundary_profile",
-           "pond_batch_set_state", "pond_batch_get_moments")
+           "pond_batch_set_state", "pond_batch_get_moments", "pond_alu_peak")
 POND_TUNE_APPLY, POND_TUNE_RETIME = 1, 2
 
 
@@ -120,6 +120,7 @@ def load_library(path: str = LIB_PATH):
         lib.pond_autotune.argtypes = [vp, vp, sz, i32, i32, P(pond_tuning)]
         lib.pond_autotune_clear.argtypes = []
         lib.pond_set_boundary_profile.argtypes = [vp, i32, vp, ctypes.c_int]
+        lib.pond_alu_peak.argtypes = [i32, i32, vp, P(ctypes.c_double), P(ctypes.c_float)]
         lib.pond_strerror.argtypes = [ctypes.c_int]
         lib.pond_strerror.restype = ctypes.c_char_p
         lib.pond_version.restype = ctypes.c_char_p
@@ -217,6 +218,17 @@ def pond_step_static(cfg: pond_config, mac_ptr: int, neq_ptr: int, nsteps: int, 
                                          ctypes.c_void_p(stream_ptr),
                                          ctypes.byref(st) if want_stats else None)
     return rc, st
+
+
+def pond_alu_peak(fp64: bool, iters: int, stream_ptr: int = 0):
+    """One launch of independent FMA chains on the current device (FP32, or FP64 with fp64);
+    returns (flop executed, milliseconds)."""
+    flop, ms = ctypes.c_double(0.0), ctypes.c_float(0.0)
+    rc = load_library().pond_alu_peak(1 if fp64 else 0, iters, ctypes.c_void_p(stream_ptr),
+                                      ctypes.byref(flop), ctypes.byref(ms))
+    if rc != POND_OK:
+        raise PondError(rc, "pond_alu_peak")
+    return flop.value, ms.value
 
 
 def pond_batch_workspace_bytes(count: int) -> int:

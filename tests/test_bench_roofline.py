@@ -1,6 +1,7 @@
-"""The bench's roofline bookkeeping on the CPU: the ALU peaks from unit counts, the roofline
-fraction (F32/P32 + F64/P64) / time of the algorithmic per-update counts, and the DRAM traffic
-record, which holds only while the step kernel's sources are the ones it was captured from."""
+"""The bench's roofline bookkeeping on the CPU: the ALU peaks from unit counts, the SM count
+and a clock, the algorithmic per-update counts, the roofline fraction (F32 + F64) / P / time
+with all the work charged to the pipe that executes it, and the DRAM traffic record, which
+holds only while the step kernel's sources are the ones it was captured from."""
 import json
 import os
 import sys
@@ -13,20 +14,34 @@ import bench  # noqa: E402
 
 def test_alu_peaks_from_unit_counts():
     # 152 SMs x 128 FP32 lanes x FMA (2 flop) x 2.07 GHz; 2 FP64 FMA per SM per clock
-    assert abs(bench.FP32_PEAK_TFLOPS - 80.54784) < 1e-9
-    assert abs(bench.FP64_PEAK_TFLOPS - 1.25856) < 1e-9
+    p32, p64 = bench.pipe_peaks(152, 2070.0)
+    assert abs(p32 - 80.54784) < 1e-9
+    assert abs(p64 - 1.25856) < 1e-9
+    # the peaks follow the SM count and the clock they are given
+    q32, q64 = bench.pipe_peaks(76, 1035.0)
+    assert abs(q32 - p32 / 4) < 1e-9 and abs(q64 - p64 / 4) < 1e-9
 
 
-def test_roofline_fraction_of_the_algorithmic_counts():
+def test_algorithmic_counts():
+    K = 2.0
+    f32, f64 = bench.algorithmic_flops(1, K)                    # cubic 2-D D2Q16
+    assert f32 == 800.0 * 16 * K + 1000.0 and f64 == 150.0 * K + 50.0
+    f32, _ = bench.algorithmic_flops(1, K, taps=3)              # 3-point 2-D: 9 taps
+    assert f32 == (2 * 20 * 9 + 160.0) * 16 * K + 1000.0
+    f32, _ = bench.algorithmic_flops(1, K, taps=3, one_d=True)  # quasi-1-D: x taps only
+    assert f32 == (2 * 20 * 3 + 160.0) * 16 * K + 1000.0
+    assert bench.algorithmic_flops(10, K)[0] == 10 * bench.algorithmic_flops(1, K)[0]
+
+
+def test_roofline_fraction_charges_every_flop_to_one_pipe():
     nodes, K = 262144, 2.0
-    f32_node = 800.0 * 16 * K + 1000.0           # per update: 16 populations x K iterations
-    f64_node = 150.0 * K + 50.0
-    t_roof = nodes * (f32_node / 80.54784e12 + f64_node / 1.25856e12)
-    f32, f64, frac = bench.roofline_terms(nodes, K, 2.0 * t_roof)
-    assert abs(f32 - nodes * f32_node) < 1e-3 and abs(f64 - nodes * f64_node) < 1e-3
-    assert abs(frac - 0.5) < 1e-12
-    # at the headline's measured 260 us per launch the fraction is about 0.61
-    assert 0.60 < bench.roofline_terms(nodes, K, 260e-6)[2] < 0.62
+    f32, f64 = bench.algorithmic_flops(nodes, K)
+    p32, _ = bench.pipe_peaks(152, 2070.0)
+    t_roof = (f32 + f64) / (p32 * 1e12)
+    assert abs(bench.roofline_fraction(f32, f64, 2.0 * t_roof, p32) - 0.5) < 1e-12
+    # at 258.7 us per launch (the last measured headline launch) the FP32-pipe fraction is
+    # about 0.34; the old two-pipe sum F32/P32 + F64/P64 gave 0.62 for the same launch
+    assert 0.33 < bench.roofline_fraction(f32, f64, 258.7e-6, p32) < 0.35
 
 
 def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):

@@ -75,8 +75,18 @@ def test_static_step_matches_pond_step_on_two_calls(P, precision, split, tol, la
 
 
 def test_static_step_rejects_grids_beyond_the_array(P):
-    c = P.Config(nx=512, ny=512, precision="fp32").to_c()     # 262 144 nodes > 155 341
-    rc, _ = P.pond_step_static(c, 256, 256, 1, 0)
+    """A grid larger than the array is refused before any launch; the caller's (real) buffers
+    are left as they were."""
+    import torch
+    cfg = P.Config(nx=512, ny=512, precision="fp32")             # 262 144 nodes > 155 341
+    c = cfg.to_c()
+    mb, nb = P.pond_state_bytes(c)
+    mac = torch.full((mb // 8,), 1.25, dtype=torch.float64, device="cuda")
+    neq = torch.full((nb // 4,), -0.5, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc, _ = P.pond_step_static(c, mac.data_ptr(), neq.data_ptr(), 1, stream)
     assert rc == P.POND_ENOMEM
+    torch.cuda.synchronize()
+    assert bool((mac == 1.25).all()) and bool((neq == -0.5).all())
     lib = P.load_library()
     assert lib.pond_step_static(ctypes.byref(c), None, None, 1, None, None) == P.POND_EINVAL
