@@ -33,8 +33,18 @@
  *     max(|du|/sqrt(T_bar), |dT|/T_bar), stop at tolerance or iteration cap, or after
  *     exactly K iterations in fixed mode;
  *   - collision in the frame of the final moments, after projecting into it;
- *   - internal-energy split source: f -> f_eq inside the source, backward time
- *     difference of u against the frame before the step, central space differences;
+ *   - internal-energy split source (Eq. int_g_evolution), integrated along the
+ *     characteristics by the trapezoidal rule, the same second-order rule that gives
+ *     omega = 1/(tau + 1/2): with g carried as g - (Omega + G)/2, the internal energy of a
+ *     node is U = sum g + (1/2) sum G and the collision adds (1 - omega/2) G.  Inside the
+ *     source f -> f_eq, so sum G = -p div u exactly; d_t u is the backward difference
+ *     against the frame before the step and grad u the central difference of the new
+ *     velocities.  U needs div u at the new time level, which is non-local: it is taken
+ *     from predictor velocities, the velocities of one streaming iteration of f in each
+ *     node's previous frame, so that T = sum g / (rho (c_v + div u_pred / 2)).  (With
+ *     div u of the previous step, the pdV work lags the compression by a step and sound
+ *     waves grow instead of decaying at the bulk viscosity of Sec. II.)  The temperature
+ *     of a node is its frame's;
  *   - non-translational split: E = sum g + sum |C|^2/2 f, g_eq = (U'/rho) f_eq;
  *   - walls (not in the paper): every position beyond a wall holds the equilibrium at the
  *     wall's state (rho_w, u_w, T_w), so the wall lies half-way between the last node and
@@ -298,6 +308,10 @@ static double geq_pop(const or_lattice *L, int i, int split, double rho, or_fram
 }
 
 /* Exported: equilibrium populations for fields rho, u, T (the state set by set_state). */
+static void node_source(const or_config *cfg, const or_lattice *L, double *g, int x, int y,
+                        const double *ux1, const double *uy1, double T1, double rho1, double dtux,
+                        double dtuy, double factor);
+
 int or_init(const or_config *cfg, const double *rho, const double *ux, const double *uy,
             const double *T, double *f, double *g, double *fux, double *fuy, double *fT)
 {
@@ -315,6 +329,15 @@ int or_init(const or_config *cfg, const double *rho, const double *ux, const dou
         fuy[n] = uy[n];
         fT[n] = T[n];
     }
+    /* internal split: g is carried as g - (Omega + G)/2 and the state is the post-collision
+     * one, g - (Omega + G)/2 + Omega + G (see internal_source); at equilibrium (Omega = 0)
+     * that is g_eq + G/2, with grad u of the initial fields and d_t u = 0 */
+    if (cfg->split == 1)
+        for (int y = 0; y < cfg->ny; ++y)
+            for (int x = 0; x < cfg->nx; ++x) {
+                size_t n = (size_t)y * cfg->nx + x;
+                node_source(cfg, &L, g, x, y, ux, uy, T[n], rho[n], 0.0, 0.0, 0.5);
+            }
     return 0;
 }
 
@@ -325,8 +348,10 @@ int or_init(const or_config *cfg, const double *rho, const double *ux, const dou
 /* ---------------------------------------------------------------------------------- */
 typedef struct { double rho, ux, uy, T, E; } or_moments;
 
-static or_moments moments_of(const or_lattice *L, const double *f, const double *g, int stride,
-                             or_frame fr, int split, double cv)
+/* div: div u of the node at the new time level (internal split only; 0 elsewhere), for
+ * U = sum g + (1/2) sum G = sum g - (1/2) rho T div u. */
+static or_moments moments_of_div(const or_lattice *L, const double *f, const double *g, int stride,
+                                 or_frame fr, int split, double cv, double div)
 {
     double sT = sqrt(fr.T);
     double rho = 0.0, jx = 0.0, jy = 0.0, G = 0.0, K2 = 0.0;
@@ -348,8 +373,8 @@ static or_moments moments_of(const or_lattice *L, const double *f, const double 
         m.E = G;
         m.T = (G / rho - 0.5 * u2) / cv;
     } else if (split == 1) {
-        m.E = G + 0.5 * rho * u2;
-        m.T = G / (rho * cv);
+        m.T = G / (rho * (cv + 0.5 * div));          /* rho c_v T = sum g - (1/2) rho T div u */
+        m.E = rho * cv * m.T + 0.5 * rho * u2;
     } else {
         m.E = G + K2;
         m.T = (m.E / rho - 0.5 * u2) / cv;
@@ -357,7 +382,14 @@ static or_moments moments_of(const or_lattice *L, const double *f, const double 
     return m;
 }
 
-/* Exported: rho, u, T of every node from its populations in its own frame. */
+static or_moments moments_of(const or_lattice *L, const double *f, const double *g, int stride,
+                             or_frame fr, int split, double cv)
+{
+    return moments_of_div(L, f, g, stride, fr, split, cv, 0.0);
+}
+
+/* Exported: rho, u, T of every node from its populations in its own frame (internal split:
+ * the temperature is the frame's, the one its last collision relaxed to). */
 int or_moments_field(const or_config *cfg, const double *f, const double *g, const double *fux,
                      const double *fuy, const double *fT, double *rho, double *ux, double *uy,
                      double *T, double *E)
@@ -369,6 +401,10 @@ int or_moments_field(const or_config *cfg, const double *f, const double *g, con
     for (size_t n = 0; n < N; ++n) {
         or_frame fr = {fux[n], fuy[n], fT[n]};
         or_moments m = moments_of(&L, f + n, g + n, (int)N, fr, cfg->split, cv);
+        if (cfg->split == 1) {
+            m.T = fT[n];
+            m.E = m.rho * cv * m.T + 0.5 * m.rho * (m.ux * m.ux + m.uy * m.uy);
+        }
         rho[n] = m.rho;
         ux[n] = m.ux;
         uy[n] = m.uy;
@@ -573,45 +609,94 @@ static int nonphysical(or_moments m)
 
 /* ---------------------------------------------------------------------------------- */
 /* Internal-energy split source (Eq. int_g_evolution, Appendix A G term):              */
-/*   G_i = -rho w_i (C_i - u) . (d_t u + C_i . grad u), added to g after collision.    */
+/*   G_i = -rho w_i (C_i - u) . (d_t u + C_i . grad u), f -> f_eq inside the source.   */
 /* ---------------------------------------------------------------------------------- */
+/* Velocity at position (gx, gy) of the fields ux, uy: the mapped node's, or the prescribed
+ * velocity beyond a prescribed side. */
+static void velocity_at(const or_config *cfg, const double *ux, const double *uy, int gx, int gy,
+                        double *vx, double *vy)
+{
+    int w = wall_of(cfg, gx, gy);
+    if (w >= 0) {
+        const double *st = side_state(cfg, w, gx, gy);
+        *vx = st[0];
+        *vy = st[1];
+    } else {
+        size_t m = (size_t)bc_map(gy, cfg->ny, cfg->bc_y) * cfg->nx + bc_map(gx, cfg->nx, cfg->bc_x);
+        *vx = ux[m];
+        *vy = uy[m];
+    }
+}
+
+/* Central differences of the velocity field at node (x, y): d_x u_x, d_y u_x, d_x u_y, d_y u_y. */
+static void velocity_gradient(const or_config *cfg, const double *ux, const double *uy, int x, int y,
+                              double grad[4])
+{
+    const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
+    double vx[4], vy[4];
+    for (int k = 0; k < 4; ++k) velocity_at(cfg, ux, uy, nb[k][0], nb[k][1], &vx[k], &vy[k]);
+    grad[0] = 0.5 * (vx[0] - vx[1]);
+    grad[1] = 0.5 * (vx[2] - vx[3]);
+    grad[2] = 0.5 * (vy[0] - vy[1]);
+    grad[3] = 0.5 * (vy[2] - vy[3]);
+}
+
+/* Adds factor * G to the populations g of node (x, y) (n = its index), G at velocity field
+ * ux1, uy1 (whose central differences give grad u), temperature T1, density rho1 and time
+ * derivative (dtux, dtuy). */
+static void node_source(const or_config *cfg, const or_lattice *L, double *g, int x, int y,
+                        const double *ux1, const double *uy1, double T1, double rho1, double dtux,
+                        double dtuy, double factor)
+{
+    size_t N = (size_t)cfg->nx * cfg->ny, n = (size_t)y * cfg->nx + x;
+    double gr[4];
+    velocity_gradient(cfg, ux1, uy1, x, y, gr);
+    double dxux = gr[0], dyux = gr[1], dxuy = gr[2], dyuy = gr[3];
+    double sT = sqrt(T1);
+    for (int i = 0; i < L->Q; ++i) {
+        double Cx = sT * L->cx[i] + ux1[n], Cy = sT * L->cy[i] + uy1[n];
+        double ax = dtux + Cx * dxux + Cy * dyux;     /* d_t u_x + C . grad u_x */
+        double ay = dtuy + Cx * dxuy + Cy * dyuy;
+        double Gi = -rho1 * L->w[i] * ((Cx - ux1[n]) * ax + (Cy - uy1[n]) * ay);
+        g[(size_t)i * N + n] += factor * Gi;
+    }
+}
+
+/* Adds (1 - omega/2) G to the post-collision g of every node (the trapezoidal rule along the
+ * characteristics), with u, T, rho of the new time level, d_t u = u^{n+1} - u^n (delta_t = 1). */
 static void internal_source(const or_config *cfg, const or_lattice *L, double *g, const double *ux1,
                             const double *uy1, const double *T1, const double *rho1,
                             const double *ux0, const double *uy0)
 {
     int nx = cfg->nx, ny = cfg->ny;
-    size_t N = (size_t)nx * ny;
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t n = (size_t)y * nx + x;
-            /* neighbour velocities: mapped nodes, or the prescribed velocity beyond a prescribed side */
-            const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
-            double vx[4], vy[4];
-            for (int k = 0; k < 4; ++k) {
-                int w = wall_of(cfg, nb[k][0], nb[k][1]);
-                if (w >= 0) {
-                    const double *st = side_state(cfg, w, nb[k][0], nb[k][1]);
-                    vx[k] = st[0];
-                    vy[k] = st[1];
-                } else {
-                    size_t m = (size_t)bc_map(nb[k][1], ny, cfg->bc_y) * nx + bc_map(nb[k][0], nx, cfg->bc_x);
-                    vx[k] = ux1[m];
-                    vy[k] = uy1[m];
-                }
-            }
-            double dxux = 0.5 * (vx[0] - vx[1]), dyux = 0.5 * (vx[2] - vx[3]);
-            double dxuy = 0.5 * (vy[0] - vy[1]), dyuy = 0.5 * (vy[2] - vy[3]);
-            double dtux = ux1[n] - ux0[n], dtuy = uy1[n] - uy0[n];   /* delta_t = 1 */
-            double sT = sqrt(T1[n]);
-            for (int i = 0; i < L->Q; ++i) {
-                double Cx = sT * L->cx[i] + ux1[n], Cy = sT * L->cy[i] + uy1[n];
-                double ax = dtux + Cx * dxux + Cy * dyux;     /* d_t u_x + C . grad u_x */
-                double ay = dtuy + Cx * dxuy + Cy * dyuy;
-                double Gi = -rho1[n] * L->w[i] * ((Cx - ux1[n]) * ax + (Cy - uy1[n]) * ay);
-                g[(size_t)i * N + n] += Gi * 1.0;              /* delta_t = 1 */
-            }
+            double tau = cfg->mu / (rho1[n] * T1[n]);
+            double omega = 1.0 / (tau + 0.5);
+            node_source(cfg, L, g, x, y, ux1, uy1, T1[n], rho1[n], ux1[n] - ux0[n], uy1[n] - uy0[n],
+                        1.0 - 0.5 * omega);
         }
+}
+
+/* Predictor velocity of the internal split at node (x, y): rho u of the populations f
+ * streamed once in the node's previous frame, over rho. */
+static void predictor_velocity(const or_src *S, or_memo *M, int x, int y, double *upx, double *upy)
+{
+    const or_lattice *L = S->L;
+    size_t n = (size_t)y * S->cfg->nx + x;
+    or_frame bar = {S->fux[n], S->fuy[n], S->fT[n]};
+    double P[OR_MAXQ], G[OR_MAXQ];
+    stream_node(S, M, x, y, bar, P, G);
+    double sT = sqrt(bar.T), rho = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < L->Q; ++i) {
+        rho += P[i];
+        jx += (sT * L->cx[i] + bar.ux) * P[i];
+        jy += (sT * L->cy[i] + bar.uy) * P[i];
+    }
+    *upx = jx / rho;
+    *upy = jy / rho;
 }
 
 /* ---------------------------------------------------------------------------------- */
@@ -623,9 +708,10 @@ static void internal_source(const or_config *cfg, const or_lattice *L, double *g
 /* ---------------------------------------------------------------------------------- */
 /* Predictor-corrector and collision at one node (x, y): streamed populations in successive
  * frames until the frame converges (or K iterations in fixed mode), then BGK in the frame of
- * the final moments.  Writes the node's post-collision populations fo_n, go_n and its moments.
- * Returns the iteration count; *badnode / *nonconv flag the outcomes. */
-static int step_node(const or_src *S, or_memo *M, int x, int y, double *fo_n, double *go_n,
+ * the final moments.  div: div u of the node at the new time level (internal split).  Writes
+ * the node's post-collision populations fo_n, go_n and its moments.  Returns the iteration
+ * count; *badnode / *nonconv flag the outcomes. */
+static int step_node(const or_src *S, or_memo *M, int x, int y, double div, double *fo_n, double *go_n,
                      or_moments *mout, int *badnode, int *nonconv)
 {
     const or_config *cfg = S->cfg;
@@ -640,7 +726,7 @@ static int step_node(const or_src *S, or_memo *M, int x, int y, double *fo_n, do
     *nonconv = 0;
     while (!stop) {
         stream_node(S, M, x, y, bar, P, G);
-        m = moments_of(L, P, G, 1, bar, cfg->split, cv);
+        m = moments_of_div(L, P, G, 1, bar, cfg->split, cv, div);
         ++k;
         if (nonphysical(m)) { *badnode = 1; break; }
         double du = sqrt((m.ux - bar.ux) * (m.ux - bar.ux) + (m.uy - bar.uy) * (m.uy - bar.uy));
@@ -680,6 +766,26 @@ int or_step(const or_config *cfg, const double *f, const double *g, const double
     int64_t nonconv = 0, bad = -1;
     double *rho1 = (double *)malloc(N * sizeof(double));
     if (!rho1) return -2;
+    /* internal split: predictor velocities of every node (div u at the new time level) */
+    double *upx = NULL, *upy = NULL;
+    if (cfg->split == 1) {
+        upx = (double *)malloc(N * sizeof(double));
+        upy = (double *)malloc(N * sizeof(double));
+        if (!upx || !upy) {
+            free(rho1);
+            free(upx);
+            free(upy);
+            return -2;
+        }
+#pragma omp parallel
+        {
+            or_memo *M = (or_memo *)malloc(sizeof(or_memo));
+#pragma omp for schedule(static)
+            for (int64_t n = 0; n < (int64_t)N; ++n)
+                predictor_velocity(&S, M, (int)(n % nx), (int)(n / nx), &upx[n], &upy[n]);
+            free(M);
+        }
+    }
 
 #pragma omp parallel reduction(+ : nonconv)
     {
@@ -690,7 +796,13 @@ int or_step(const or_config *cfg, const double *f, const double *g, const double
             int x = (int)(n % nx), y = (int)(n / nx);
             or_moments m;
             int badnode, nc;
-            int k = step_node(&S, M, x, y, fo_n, go_n, &m, &badnode, &nc);
+            double div = 0.0;
+            if (cfg->split == 1) {
+                double gr[4];
+                velocity_gradient(cfg, upx, upy, x, y, gr);
+                div = gr[0] + gr[3];
+            }
+            int k = step_node(&S, M, x, y, div, fo_n, go_n, &m, &badnode, &nc);
             nonconv += nc;
             if (iters) iters[n] = k;
             if (badnode) {
@@ -711,15 +823,18 @@ int or_step(const or_config *cfg, const double *f, const double *g, const double
     if (cfg->split == 1 && bad < 0)
         internal_source(cfg, &L, go, oux, ouy, oT, rho1, fux, fuy);
     free(rho1);
+    free(upx);
+    free(upy);
     if (first_bad) *first_bad = bad;
     if (bad >= 0) return -4;
     if (nonconv > 0) return -5;
     return 0;
 }
 
-/* Exported for the tests: one time step at the nodes listed in xs, ys only (total split, or
- * the internal split before its source pass), from the full state of the previous step:
- * fo, go [Q][count], frame [3][count] (ux, uy, T), iters [count]. */
+/* Exported for the tests: one time step at the nodes listed in xs, ys only (the internal
+ * split before its source pass, with the predictor velocities of the four neighbours), from
+ * the full state of the previous step: fo, go [Q][count], frame [3][count] (ux, uy, T),
+ * iters [count]. */
 int or_step_nodes(const or_config *cfg, const double *f, const double *g, const double *fux,
                   const double *fuy, const double *fT, int count, const int32_t *xs,
                   const int32_t *ys, double *fo, double *go, double *frame, int32_t *iters)
@@ -738,7 +853,26 @@ int or_step_nodes(const or_config *cfg, const double *f, const double *g, const 
         for (int j = 0; j < count; ++j) {
             or_moments m;
             int badnode, nc;
-            int k = step_node(&S, M, xs[j], ys[j], fo_n, go_n, &m, &badnode, &nc);
+            double div = 0.0;
+            if (cfg->split == 1) {
+                /* div u_pred by central differences; beyond a prescribed side its velocity */
+                const int x = xs[j], y = ys[j];
+                const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
+                double vx[4], vy[4];
+                for (int q = 0; q < 4; ++q) {
+                    int w = wall_of(cfg, nb[q][0], nb[q][1]);
+                    if (w >= 0) {
+                        const double *st = side_state(cfg, w, nb[q][0], nb[q][1]);
+                        vx[q] = st[0];
+                        vy[q] = st[1];
+                    } else {
+                        predictor_velocity(&S, M, bc_map(nb[q][0], cfg->nx, cfg->bc_x),
+                                           bc_map(nb[q][1], cfg->ny, cfg->bc_y), &vx[q], &vy[q]);
+                    }
+                }
+                div = 0.5 * (vx[0] - vx[1]) + 0.5 * (vy[2] - vy[3]);
+            }
+            int k = step_node(&S, M, xs[j], ys[j], div, fo_n, go_n, &m, &badnode, &nc);
             if (iters) iters[j] = k;
             if (badnode) rc = -4;
             for (int i = 0; i < L.Q; ++i) {

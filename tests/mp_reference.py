@@ -13,8 +13,11 @@ from the oracle (no shared code) and follows the paper with the same readings:
 - collision: project into the frame of the final moments, BGK with omega = 1/(tau + 1/2),
   tau = mu/(rho T), f_eq = rho w_i, g_eq of the total, internal or non-translational split
   (Sec. II; the last with E = sum g + sum |C|^2/2 f);
-- internal split: G_i = -rho w_i (C_i - u).(d_t u + C_i . grad u) after the collision, with
-  d_t u = u^{n+1} - u^n and central differences of u^{n+1}.
+- internal split: the source G_i = -rho w_i (C_i - u).(d_t u + C_i . grad u) by the
+  trapezoidal rule along the characteristics: T from U = sum g + (1/2) sum G =
+  sum g - (1/2) rho T div u, with div u from the predictor velocities (rho u of one streaming
+  of f in each node's previous frame, central differences), and (1 - omega/2) G added after
+  the collision, with d_t u = u^{n+1} - u^n and central differences of u^{n+1}.
 """
 import mpmath as mp
 
@@ -94,7 +97,7 @@ def g_eq(lat, i, split, rho, fr, cv):
     return ((cv - 1) * fr[2] + kin) * rho * lat.w[i]
 
 
-def moments(lat, P, G, fr, split, cv):
+def moments(lat, P, G, fr, split, cv, div=0):
     sT = mp.sqrt(fr[2])
     rho = sum(P)
     jx = sum((sT * lat.cx[i] + fr[0]) * P[i] for i in range(lat.Q))
@@ -103,7 +106,7 @@ def moments(lat, P, G, fr, split, cv):
     if split == "total":
         T = (sum(G) / rho - (ux * ux + uy * uy) / 2) / cv
     elif split == "internal":
-        T = sum(G) / (rho * cv)
+        T = sum(G) / (rho * (cv + div / 2))
     else:
         K2 = sum(((sT * lat.cx[i] + fr[0]) ** 2 + (sT * lat.cy[i] + fr[1]) ** 2) / 2 * P[i]
                  for i in range(lat.Q))
@@ -122,7 +125,55 @@ def init(lat, nx, ny, rho, ux, uy, T, split, gamma):
             st["f"].append([r * lat.w[i] for i in range(lat.Q)])
             st["g"].append([g_eq(lat, i, split, r, fr, cv) for i in range(lat.Q)])
             st["fr"].append(fr)
+    if split == "internal":
+        # post-collision state of g carried as g - (Omega + G)/2: at equilibrium g_eq + G/2
+        # (d_t u = 0 at the start)
+        add_source(lat, st, st["fr"], [(0, 0)] * (nx * ny), nx, ny, lambda n: mp.mpf(1) / 2)
     return st
+
+
+def stream(lat, st, nx, ny, x, y, bar):
+    """Populations f, g streamed to node (x, y) on the lattice of frame bar."""
+    cache = {}
+    sT = mp.sqrt(bar[2])
+    P, G = [], []
+    for i in range(lat.Q):
+        bx, wx = cubic(x - (sT * lat.cx[i] + bar[0]))
+        by, wy = cubic(y - (sT * lat.cy[i] + bar[1]))
+        fi = gi = mp.mpf(0)
+        for ky in range(4):
+            for kx in range(4):
+                s = ((by + ky) % ny) * nx + (bx + kx) % nx
+                if s not in cache:
+                    cache[s] = (coefficients(lat, st["f"][s], st["fr"][s], bar),
+                                coefficients(lat, st["g"][s], st["fr"][s], bar))
+                W = wx[kx] * wy[ky]
+                fi += W * population(lat, cache[s][0], i)
+                gi += W * population(lat, cache[s][1], i)
+        P.append(fi)
+        G.append(gi)
+    return P, G
+
+
+def divergence(lat, st, nx, ny):
+    """Internal split: div u at the new time level from the predictor velocities (rho u / rho
+    of f streamed once in each node's previous frame), central differences, periodic."""
+    up = []
+    for y in range(ny):
+        for x in range(nx):
+            bar = st["fr"][y * nx + x]
+            P, _ = stream(lat, st, nx, ny, x, y, bar)
+            sT = mp.sqrt(bar[2])
+            rho = sum(P)
+            up.append((sum((sT * lat.cx[i] + bar[0]) * P[i] for i in range(lat.Q)) / rho,
+                       sum((sT * lat.cy[i] + bar[1]) * P[i] for i in range(lat.Q)) / rho))
+    div = []
+    for y in range(ny):
+        for x in range(nx):
+            xp, xm = y * nx + (x + 1) % nx, y * nx + (x - 1) % nx
+            yp, ym = ((y + 1) % ny) * nx + x, ((y - 1) % ny) * nx + x
+            div.append((up[xp][0] - up[xm][0]) / 2 + (up[yp][1] - up[ym][1]) / 2)
+    return div
 
 
 def step(lat, st, nx, ny, split, gamma, mu, K):
@@ -130,29 +181,13 @@ def step(lat, st, nx, ny, split, gamma, mu, K):
     cv = 1 / (mp.mpf(gamma) - 1)
     mu = mp.mpf(mu)
     out = {"f": [], "g": [], "fr": []}
+    div = divergence(lat, st, nx, ny) if split == "internal" else None
     for y in range(ny):
         for x in range(nx):
             bar = st["fr"][y * nx + x]
             for k in range(K):
-                cache = {}
-                sT = mp.sqrt(bar[2])
-                P, G = [], []
-                for i in range(lat.Q):
-                    bx, wx = cubic(x - (sT * lat.cx[i] + bar[0]))
-                    by, wy = cubic(y - (sT * lat.cy[i] + bar[1]))
-                    fi = gi = mp.mpf(0)
-                    for ky in range(4):
-                        for kx in range(4):
-                            s = ((by + ky) % ny) * nx + (bx + kx) % nx
-                            if s not in cache:
-                                cache[s] = (coefficients(lat, st["f"][s], st["fr"][s], bar),
-                                            coefficients(lat, st["g"][s], st["fr"][s], bar))
-                            W = wx[kx] * wy[ky]
-                            fi += W * population(lat, cache[s][0], i)
-                            gi += W * population(lat, cache[s][1], i)
-                    P.append(fi)
-                    G.append(gi)
-                m = moments(lat, P, G, bar, split, cv)
+                P, G = stream(lat, st, nx, ny, x, y, bar)
+                m = moments(lat, P, G, bar, split, cv, div[y * nx + x] if div else 0)
                 if k < K - 1:
                     bar = (m[1], m[2], m[3])
             rho, star = m[0], (m[1], m[2], m[3])
@@ -168,13 +203,15 @@ def step(lat, st, nx, ny, split, gamma, mu, K):
             out["g"].append(go)
             out["fr"].append(star)
     if split == "internal":
-        internal_source(lat, st, out, nx, ny)
+        internal_source(lat, st, out, nx, ny, mu)
     return out
 
 
-def internal_source(lat, before, after, nx, ny):
-    ux = [fr[0] for fr in after["fr"]]
-    uy = [fr[1] for fr in after["fr"]]
+def add_source(lat, st, frames, dtu, nx, ny, factor):
+    """Adds factor(n) * G to st's g at every node n, G with the velocities and temperatures of
+    frames (central differences, periodic), rho of st's f and time derivatives dtu[n]."""
+    ux = [fr[0] for fr in frames]
+    uy = [fr[1] for fr in frames]
     for y in range(ny):
         for x in range(nx):
             n = y * nx + x
@@ -182,11 +219,23 @@ def internal_source(lat, before, after, nx, ny):
             yp, ym = ((y + 1) % ny) * nx + x, ((y - 1) % ny) * nx + x
             dxux, dyux = (ux[xp] - ux[xm]) / 2, (ux[yp] - ux[ym]) / 2
             dxuy, dyuy = (uy[xp] - uy[xm]) / 2, (uy[yp] - uy[ym]) / 2
-            dtux, dtuy = ux[n] - before["fr"][n][0], uy[n] - before["fr"][n][1]
-            rho = sum(after["f"][n])
-            sT = mp.sqrt(after["fr"][n][2])
+            dtux, dtuy = dtu[n]
+            rho = sum(st["f"][n])
+            sT = mp.sqrt(frames[n][2])
+            fac = factor(n)
             for i in range(lat.Q):
                 Cx, Cy = sT * lat.cx[i] + ux[n], sT * lat.cy[i] + uy[n]
                 ax = dtux + Cx * dxux + Cy * dyux
                 ay = dtuy + Cx * dxuy + Cy * dyuy
-                after["g"][n][i] += -rho * lat.w[i] * ((Cx - ux[n]) * ax + (Cy - uy[n]) * ay)
+                st["g"][n][i] += -fac * rho * lat.w[i] * ((Cx - ux[n]) * ax + (Cy - uy[n]) * ay)
+
+
+def internal_source(lat, before, after, nx, ny, mu):
+    """(1 - omega/2) G after the collision, d_t u = u^{n+1} - u^n."""
+    fr1, fr0 = after["fr"], before["fr"]
+    dtu = [(fr1[n][0] - fr0[n][0], fr1[n][1] - fr0[n][1]) for n in range(nx * ny)]
+
+    def factor(n):
+        omega = 1 / (mu / (sum(after["f"][n]) * fr1[n][2]) + mp.mpf(1) / 2)
+        return 1 - omega / 2
+    add_source(lat, after, fr1, dtu, nx, ny, factor)

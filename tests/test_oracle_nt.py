@@ -162,7 +162,8 @@ def test_d2q25_needs_order_4_at_high_mach(orc):
 
 
 @pytest.mark.parametrize("split,lattice,gamma", [("total", 16, 1.4), ("total", 16, 1.8),
-                                                 ("nt", 16, 1.4), ("nt", 25, 1.8)])
+                                                 ("nt", 16, 1.4), ("nt", 25, 1.8),
+                                                 ("internal", 16, 1.4), ("internal", 16, 1.8)])
 def test_sound_attenuation_gives_the_bulk_viscosity(orc, split, lattice, gamma):
     """A standing isentropic sound wave decays at Gamma = (k^2/2)[(2 - 2/D) nu + eta/rho +
     (gamma - 1) alpha] (linearised Navier-Stokes-Fourier), which with the bulk viscosity of
