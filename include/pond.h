@@ -13,7 +13,13 @@
  * this predictor-corrector until the frame converges; relax f and g to their equilibria
  * (BGK, tau = mu / p, Eq. kin_visc).  The energy split is the total-energy split (Eq. Es,
  * first line) by default, the internal-energy split (second line, with the source term of
- * Eq. int_g_evolution) as an option.
+ * Eq. int_g_evolution) as an option.  The internal split's source is integrated along the
+ * characteristics by the trapezoidal rule: the stored g is the post-collision g carried as
+ * g - (Omega + G)/2, a node's internal energy is U = sum g + (1/2) sum G = sum g -
+ * (1/2) rho T div u with div u at the new time level from a predictor pass (each node's f
+ * streamed once in its previous frame), and the collision adds (1 - omega/2) G; a step of
+ * that split is three launches (predictor, step, source).  Its reported temperature is the
+ * frame's.
  *
  * Units: lattice units (Sec. III), r = 1, dx = dt = 1, T_L = 1.
  *
@@ -117,8 +123,9 @@ typedef struct pond_sim pond_sim;
 int pond_config_default(pond_config *cfg, int32_t nx, int32_t ny);
 
 /* Bytes of device workspace a simulation with this configuration needs (two copies of the
- * state, see pond_state_bytes, a status block and the prescribed sides' profiles).  For
- * admission by free HBM. */
+ * state, see pond_state_bytes, a status block, the prescribed sides' profiles and, for the
+ * internal-energy split, its predictor velocities, 16 bytes per node).  For admission by
+ * free HBM. */
 int pond_workspace_bytes(const pond_config *cfg, size_t *bytes);
 
 /* Create a simulation on the current device.  dev_workspace: caller-owned device memory
@@ -201,8 +208,8 @@ int pond_destroy(pond_sim *sim);
 /* Batched stepping (many simulations, one kernel launch per time step).
  *
  * A batch advances count simulations together: every time step is one launch of the step
- * kernel over the tiles of all of them (plus one launch of the internal-split source pass if
- * any member uses that split), so uneven cases share the GPU without per-case launches or
+ * kernel over the tiles of all of them (plus one launch each of the internal split's predictor
+ * and source passes if any member uses that split), so uneven cases share the GPU without per-case launches or
  * tail effects.  The members must share precision, lattice, interpolation order, the 1-D
  * (ny = 1) or 2-D class and the tile configuration; grid size, boundaries, split, gamma, mu
  * and the predictor-corrector settings may differ.  dev_workspace (caller-owned device
@@ -301,8 +308,9 @@ void pond_autotune_clear(void);
  *  - Size limit: the state must fit that array, state bytes = align256(4*8*N) +
  *    align256(P*s*N) + 256 with N = nx*ny, P = 19 (D2Q16) or 29 (D2Q25) and s = 8/4/2/2
  *    bytes (FP64/FP32/FP16/BF16), i.e. N <= 91 178 / 63 548 (FP64), 155 341 / 113 357
- *    (FP32), 239 669 / 186 408 (FP16/BF16) on D2Q16 / D2Q25; larger grids return
- *    POND_ENOMEM without touching the GPU.
+ *    (FP32), 239 669 / 186 408 (FP16/BF16) on D2Q16 / D2Q25; the internal-energy split adds
+ *    align256(16*N) for its predictor velocities.  Larger grids return POND_ENOMEM without
+ *    touching the GPU.
  *  - Set-up: the first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) and the SM count, and the first call for each kernel variant
  *    (precision, lattice, 1-D or 2-D, interpolation order, launch shape) sets the step

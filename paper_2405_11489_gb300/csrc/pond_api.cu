@@ -70,6 +70,7 @@ Lattice make_lattice(int q1)
 
 struct Layout {
     size_t mac[2], neq[2], status, prof[4], total;   // prof[side] = 0: the side takes no profile
+    size_t upred;                                    // internal split: [2][N] predictor velocities; else 0
 };
 
 // Grad order of a configuration: the lattice's (3 on D2Q16, 4 on D2Q25).
@@ -101,6 +102,11 @@ Layout layout_of(const pond_config& c)
         if (!side_prescribed(c, w)) continue;
         l.prof[w] = off;
         off = align_up(off + 4 * (size_t)side_length(c, w) * sizeof(double));
+    }
+    l.upred = 0;
+    if (c.split == POND_SPLIT_INTERNAL) {
+        l.upred = off;
+        off = align_up(off + 2 * N * sizeof(double));
     }
     l.total = off;
     return l;
@@ -164,6 +170,7 @@ double* mac_ptr(pond_sim* s, int k) { return reinterpret_cast<double*>(s->ws + s
 void* neq_ptr(pond_sim* s, int k) { return s->ws + s->lay.neq[k]; }
 DevStatus* status_ptr(pond_sim* s) { return reinterpret_cast<DevStatus*>(s->ws + s->lay.status); }
 double* prof_ptr(pond_sim* s, int w) { return reinterpret_cast<double*>(s->ws + s->lay.prof[w]); }
+double* upred_ptr(pond_sim* s) { return s->lay.upred ? reinterpret_cast<double*>(s->ws + s->lay.upred) : nullptr; }
 
 // The profiles a simulation's kernels read: every prescribed side streams from its profile in
 // the workspace (filled with the side's uniform state at creation); null for the other sides.
@@ -228,6 +235,7 @@ AuxParams aux_params(pond_sim* s, int k)
     side_profiles(s, a.prof);
     a.N = (long long)s->cfg.nx * s->cfg.ny;
     a.cv = 1.0 / (s->cfg.gamma - 1.0);
+    a.mu = s->cfg.mu;
     a.mac = mac_ptr(s, k);
     a.neq = neq_ptr(s, k);
     a.mac_prev = mac_ptr(s, 1 - k);
@@ -641,17 +649,21 @@ int pond_step(pond_sim* s, int32_t nsteps)
     const double* prof[4];
     side_profiles(s, prof);
     fill_case(c, status_ptr(s), p.one, prof);
+    p.one.upred = upred_ptr(s);
     Launch l;
     l.block = dim3(s->tx, s->ty, 1);
     l.grid = dim3((c.nx + s->tx - 1) / s->tx, (c.ny + s->ty - 1) / s->ty, 1);
     l.smem = s->smem;
     l.stream = s->stream;
+    const StepFn step = kStep[c.precision][s->lat.q1 == 5][s->one_d];
     for (int k = 0; k < nsteps; ++k) {
         p.one.mac[0] = mac_ptr(s, s->cur);
         p.one.neq[0] = neq_ptr(s, s->cur);
         p.one.mac[1] = mac_ptr(s, 1 - s->cur);
         p.one.neq[1] = neq_ptr(s, 1 - s->cur);
-        cudaError_t e = kStep[c.precision][s->lat.q1 == 5][s->one_d](p, c.interp_order, l);
+        cudaError_t e = cudaSuccess;
+        if (c.split == POND_SPLIT_INTERNAL) e = step(p, c.interp_order, true, l);   // predictor velocities
+        if (e == cudaSuccess) e = step(p, c.interp_order, false, l);
         if (e != cudaSuccess) return cuda_status(e);
         if (c.split == POND_SPLIT_INTERNAL) {
             AuxParams a = aux_params(s, 1 - s->cur);   // new state; mac_prev = state before the step
@@ -829,7 +841,10 @@ cudaError_t batch_launch_step(pond_batch* b)
     l.smem = s0->smem;
     l.stream = b->stream;
     const pond_config& c = s0->cfg;
-    cudaError_t e = kStep[c.precision][s0->lat.q1 == 5][s0->one_d](p, c.interp_order, l);
+    const StepFn step = kStep[c.precision][s0->lat.q1 == 5][s0->one_d];
+    cudaError_t e = cudaSuccess;
+    if (b->any_internal) e = step(p, c.interp_order, true, l);   // predictor velocities (internal split)
+    if (e == cudaSuccess) e = step(p, c.interp_order, false, l);
     if (e == cudaSuccess && b->any_internal)
         e = POND_BY_PRECISION(c.precision, internal_source_batch, b->d_cases, b->d_aux_start, b->count,
                               b->flip, b->total_aux_blocks, b->stream);
@@ -909,6 +924,7 @@ extern "C" int pond_batch_create(pond_sim* const* sims, int32_t count, void* dev
         const double* prof[4];
         side_profiles(s, prof);
         fill_case(c, status_ptr(s), cases[i], prof);
+        cases[i].upred = upred_ptr(s);
         cases[i].mac[0] = mac_ptr(s, s->cur);
         cases[i].neq[0] = neq_ptr(s, s->cur);
         cases[i].mac[1] = mac_ptr(s, 1 - s->cur);
@@ -1540,7 +1556,11 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     size_t mb = 0, nb = 0;
     pond_state_bytes(cfg, &mb, &nb);
     const size_t off_neq = align_up(mb), off_status = off_neq + align_up(nb);
-    if (off_status + align_up(sizeof(DevStatus)) > (size_t)POND_STATIC_SCRATCH_BYTES) return POND_ENOMEM;
+    // internal split: the predictor velocities follow the status block
+    const size_t off_upred = off_status + align_up(sizeof(DevStatus));
+    const size_t need = off_upred + (cfg->split == POND_SPLIT_INTERNAL
+                                         ? align_up(2 * (size_t)cfg->nx * cfg->ny * sizeof(double)) : 0);
+    if (need > (size_t)POND_STATIC_SCRATCH_BYTES) return POND_ENOMEM;
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1578,6 +1598,7 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     // the next-wave L2 prefetch distance, as pond_step sets it: the blocks resident at once
     p.ahead = sd->sms * step_blocks_per_sm(one_d, cfg->lattice == POND_D2Q25, cfg->precision == POND_FP64);
     fill_case(*cfg, st, p.one);
+    p.one.upred = cfg->split == POND_SPLIT_INTERNAL ? reinterpret_cast<double*>(scratch + off_upred) : nullptr;
     Launch l;
     l.block = dim3(tx, ty, 1);
     l.grid = dim3((cfg->nx + tx - 1) / tx, (cfg->ny + ty - 1) / ty, 1);
@@ -1595,6 +1616,7 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     std::memcpy(a.wall, cfg->wall, sizeof(a.wall));
     a.N = N;
     a.cv = p.one.cv;
+    a.mu = cfg->mu;
     a.status = st;
     // ping-pong between the caller's buffers and the array
     for (int k = 0; k < nsteps; ++k) {
@@ -1603,7 +1625,10 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
         p.one.neq[0] = from_caller ? neq : sneq;
         p.one.mac[1] = from_caller ? smac : mac;
         p.one.neq[1] = from_caller ? sneq : neq;
-        e = kStep[cfg->precision][lat.q1 == 5][one_d](p, cfg->interp_order, l);
+        const StepFn step = kStep[cfg->precision][lat.q1 == 5][one_d];
+        e = cudaSuccess;
+        if (cfg->split == POND_SPLIT_INTERNAL) e = step(p, cfg->interp_order, true, l);   // predictor
+        if (e == cudaSuccess) e = step(p, cfg->interp_order, false, l);
         if (e != cudaSuccess) return cuda_status(e);
         if (cfg->split == POND_SPLIT_INTERNAL) {
             a.mac = p.one.mac[1];

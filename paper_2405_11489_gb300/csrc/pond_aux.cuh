@@ -13,6 +13,7 @@ struct AuxParams {
     int nord;           // Grad order N of the state (3 or 4)
     long long N;
     double cv;
+    double mu;          // dynamic viscosity (tau = mu / p)
     double* mac;        // [4][N] rho, u_x, u_y, T
     void* neq;          // [nneq(N)][N] storage type
     const double* mac_prev;  // internal source: frames before the step
@@ -40,6 +41,27 @@ __device__ __forceinline__ void init_node(double* mac, void* neq, long long N, i
 }
 
 template <class S>
+__device__ __forceinline__ void add_source_node(long long n, int x, int y, int nx, int ny, int bc_x, int bc_y,
+                                                long long N, int nord, const double* vux, const double* vuy,
+                                                const double (*wall)[4], const double* const* prof, double rho,
+                                                double ux, double uy, double T, double dtux_d, double dtuy_d,
+                                                double factor, void* neq);
+
+// Internal split: the stored state is the post-collision g carried as g - (Omega + G)/2 (the
+// trapezoidal rule of the source), which at equilibrium is g_eq + G/2, G with grad u of the
+// given velocity fields and d_t u = 0.
+template <class S>
+__device__ __forceinline__ void init_internal_source(long long n, int nx, int ny, int bc_x, int bc_y, long long N,
+                                                     int nord, const double* ux, const double* uy,
+                                                     const double (*wall)[4], const double* const* prof,
+                                                     double r, double t, void* neq)
+{
+    const int x = (int)(n % nx), y = (int)(n / nx);
+    add_source_node<S>(n, x, y, nx, ny, bc_x, bc_y, N, nord, ux, uy, wall, prof, r, ux[n], uy[n], t, 0.0, 0.0, 0.5,
+                       neq);
+}
+
+template <class S>
 __global__ void init_kernel(AuxParams p, const double* rho, const double* ux, const double* uy,
                             const double* T)
 {
@@ -47,6 +69,9 @@ __global__ void init_kernel(AuxParams p, const double* rho, const double* ux, co
     if (n >= p.N) return;
     if (p.status->flags & kInputBad) return;   // the input check before rejected it: state unchanged
     init_node<S>(p.mac, p.neq, p.N, p.nord, p.status, n, rho[n], ux[n], uy[n], T[n]);
+    if (p.split == 1)
+        init_internal_source<S>(n, p.nx, p.ny, p.bc_x, p.bc_y, p.N, p.nord, ux, uy, p.wall, p.prof, rho[n], T[n],
+                                p.neq);
 }
 
 // Populations f, g [Q][N] in frames (ux, uy, T) -> Hermite coefficients of order <= N.
@@ -122,7 +147,8 @@ __device__ __forceinline__ void node_coefficients(const AuxParams& p, long long 
 }
 
 // Moments of the populations (Sec. II): rho = A_00, rho u = rho u_frame + sqrt(T) (A_10, A_01),
-// total split E = B_00, T = (E/rho - |u|^2/2)/c_v; internal split T = B_00/(rho c_v);
+// total split E = B_00, T = (E/rho - |u|^2/2)/c_v; internal split: T of the frame, the
+// temperature of the last collision (its stored B_00 holds U + (1/2) sum G, see the source);
 // non-translational split E = B_00 + sum |C|^2/2 f with
 // sum |C|^2/2 f = (T (A_20 + A_02 + 2 rho) + 2 sqrt(T) u_frame . (A_10, A_01) + |u_frame|^2 rho)/2.
 // Written to out[0..3][n] (rho, u_x, u_y, T); null arrays are skipped.
@@ -131,7 +157,7 @@ __device__ __forceinline__ void node_coefficients(const AuxParams& p, long long 
 // stored frame (u_f, T_f), whose non-equilibrium coefficients are the only non-FP64 inputs:
 // with d = u - u_f = sqrt(T_f) (A_10, A_01) / rho and b = B_00 - B_00^eq,
 //   total split            T = T_f + (b / rho - u_f . d - |d|^2 / 2) / c_v,
-//   internal split         T = T_f + b / (rho c_v),
+//   internal split         T = T_f,
 //   non-translational      T = T_f + (b / rho + T_f (A_20 + A_02) / (2 rho) - |d|^2 / 2) / c_v
 // (B_00^eq = rho (c_v T_f + |u_f|^2/2), rho c_v T_f, rho (c_v - 1) T_f).  The corrections are
 // formed in FP32 and added to the FP64 frame once: FP64 is slow on this part, and the
@@ -151,7 +177,7 @@ __device__ __forceinline__ void node_moments(const double* mac, const void* neq,
         if (split == 2)
             E += 0.5 * (T * (A[slot(2, 0)] + A[slot(0, 2)] + 2.0 * rho) +
                         2.0 * sT * (ux * A[slot(1, 0)] + uy * A[slot(0, 1)]) + (ux * ux + uy * uy) * rho);
-        t = (split == 1) ? B[0] / (rho * cv) : (E / rho - 0.5 * (vx * vx + vy * vy)) / cv;
+        t = (split == 1) ? T : (E / rho - 0.5 * (vx * vx + vy * vy)) / cv;
     } else {
         const S* q = reinterpret_cast<const S*>(neq);
         const int nc = ncoef(nord);
@@ -163,7 +189,7 @@ __device__ __forceinline__ void node_moments(const double* mac, const void* neq,
         const float ir = 1.0f / (float)rho, Tf = (float)T, icv = 1.0f / (float)cv;
         const float sT = sqrtf(Tf);
         const float dx = sT * a10 * ir, dy = sT * a01 * ir;
-        float e = b * ir;
+        float e = split == 1 ? 0.0f : b * ir;
         if (split == 0) {
             e -= (float)ux * dx + (float)uy * dy + 0.5f * (dx * dx + dy * dy);
         } else if (split == 2) {
@@ -220,25 +246,21 @@ __global__ void get_pops_kernel(AuxParams p, double* f, double* g, double* oux, 
     if (oT) oT[n] = T;
 }
 
-// Internal-energy split source (Eq. int_g_evolution; Appendix A, G term) after the step:
+// Internal-energy split source (Eq. int_g_evolution; Appendix A, G term):
 //   G_i = -rho w_i (C_i - u) . (d_t u + C_i . grad u)   (f -> f_eq inside the source),
-// d_t u by the backward difference against the frame before the step, grad u by central
-// differences of the new frames (boundary-mapped).  In Hermite coefficients of the node's
-// frame the source is G_00 = -rho T div u, G_10 = -rho sqrt(T) Du_x, G_01 = -rho sqrt(T) Du_y,
-// G_20 = -2 rho T d_x u_x, G_11 = -rho T (d_y u_x + d_x u_y), G_02 = -2 rho T d_y u_y
-// (Du = d_t u + u . grad u), and it is added to the non-equilibrium part of g.
+// in Hermite coefficients of the node's frame G_00 = -rho T div u, G_10 = -rho sqrt(T) Du_x,
+// G_01 = -rho sqrt(T) Du_y, G_20 = -2 rho T d_x u_x, G_11 = -rho T (d_y u_x + d_x u_y),
+// G_02 = -2 rho T d_y u_y (Du = d_t u + u . grad u).  add_source_node adds factor * G to the
+// stored g coefficients of node n = (x, y): grad u by central differences of the velocity
+// fields vux, vuy (boundary-mapped; beyond a prescribed side its velocity), the node's own
+// rho, u, T and d_t u given.
 template <class S>
-__device__ __forceinline__ void internal_source_node(long long n, int nx, int ny, int bc_x, int bc_y,
-                                                     long long N, int nord, const double* mac,
-                                                     const double* mac_prev, void* neq,
-                                                     const double (*wall)[4], const double* const* prof)
+__device__ __forceinline__ void add_source_node(long long n, int x, int y, int nx, int ny, int bc_x, int bc_y,
+                                                long long N, int nord, const double* vux, const double* vuy,
+                                                const double (*wall)[4], const double* const* prof, double rho,
+                                                double ux, double uy, double T, double dtux_d, double dtuy_d,
+                                                double factor, void* neq)
 {
-    // 32-bit division where the grid allows it (64-bit division is a long software sequence)
-    const int x = N <= 0x7fffffffll ? (int)n % nx : (int)(n % nx);
-    const int y = N <= 0x7fffffffll ? (int)n / nx : (int)(n / nx);
-    const double* ux1 = mac + N;
-    const double* uy1 = mac + 2 * N;
-    // neighbour velocities: mapped nodes, or the prescribed velocity beyond a prescribed side
     const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
     double vx[4], vy[4];
     for (int k = 0; k < 4; ++k) {
@@ -249,32 +271,30 @@ __device__ __forceinline__ void internal_source_node(long long n, int nx, int ny
             vy[k] = st[1];
         } else {
             const long long m = (long long)bc_map(nb[k][1], ny, bc_y) * nx + bc_map(nb[k][0], nx, bc_x);
-            vx[k] = ux1[m];
-            vy[k] = uy1[m];
+            vx[k] = vux[m];
+            vy[k] = vuy[m];
         }
     }
-    const double rho = mac[n], ux = ux1[n], uy = uy1[n], T = mac[3 * N + n];
     S* q = reinterpret_cast<S*>(neq);
     if constexpr (std::is_same<S, double>::value) {
         double dxux = 0.5 * (vx[0] - vx[1]), dyux = 0.5 * (vx[2] - vx[3]);
         double dxuy = 0.5 * (vy[0] - vy[1]), dyuy = 0.5 * (vy[2] - vy[3]);
-        double dtux = ux - mac_prev[N + n], dtuy = uy - mac_prev[2 * N + n];
-        double Dux = dtux + ux * dxux + uy * dyux;
-        double Duy = dtuy + ux * dxuy + uy * dyuy;
+        double Dux = dtux_d + ux * dxux + uy * dyux;
+        double Duy = dtuy_d + ux * dxuy + uy * dyuy;
         double rT = rho * T, rsT = rho * sqrt(T);
         double G[6] = {-rT * (dxux + dyuy), -rsT * Dux, -rsT * Duy, -2.0 * rT * dxux,
                        -rT * (dyux + dxuy), -2.0 * rT * dyuy};
         for (int m = 0; m < 6; ++m) {
             S* a = q + (long long)(ncoef(nord) - 1 + m) * N + n;
-            sto_put<S, double>(a, sto_load<S>(a) + G[m]);
+            sto_put<S, double>(a, sto_load<S>(a) + factor * G[m]);
         }
     } else {
         // mixed modes: the velocity differences taken in FP64 (small against u), the source
         // formed in FP32 like the coefficients it is added to (FP64 is slow on this part)
         const float dxux = 0.5f * (float)(vx[0] - vx[1]), dyux = 0.5f * (float)(vx[2] - vx[3]);
         const float dxuy = 0.5f * (float)(vy[0] - vy[1]), dyuy = 0.5f * (float)(vy[2] - vy[3]);
-        const float dtux = (float)(ux - mac_prev[N + n]), dtuy = (float)(uy - mac_prev[2 * N + n]);
-        const float uxf = (float)ux, uyf = (float)uy, rf = (float)rho, Tf = (float)T;
+        const float dtux = (float)dtux_d, dtuy = (float)dtuy_d;
+        const float uxf = (float)ux, uyf = (float)uy, rf = (float)rho, Tf = (float)T, fac = (float)factor;
         const float Dux = dtux + uxf * dxux + uyf * dyux;
         const float Duy = dtuy + uxf * dxuy + uyf * dyuy;
         const float rT = rf * Tf, rsT = rf * sqrtf(Tf);
@@ -282,9 +302,32 @@ __device__ __forceinline__ void internal_source_node(long long n, int nx, int ny
                             -rT * (dyux + dxuy), -2.0f * rT * dyuy};
         for (int m = 0; m < 6; ++m) {
             S* a = q + (long long)(ncoef(nord) - 1 + m) * N + n;
-            sto_put<S, float>(a, sto_loadf<S>(a) + G[m]);
+            sto_put<S, float>(a, sto_loadf<S>(a) + fac * G[m]);
         }
     }
+}
+
+// The source of the step (trapezoidal rule along the characteristics): (1 - omega/2) G with
+// the new state (mac), d_t u by the backward difference against the frame before the step
+// (mac_prev), grad u of the new frames; omega = 1/(tau + 1/2), tau = mu/(rho T).
+template <class S>
+__device__ __forceinline__ void internal_source_node(long long n, int nx, int ny, int bc_x, int bc_y,
+                                                     long long N, int nord, double mu, const double* mac,
+                                                     const double* mac_prev, void* neq,
+                                                     const double (*wall)[4], const double* const* prof)
+{
+    // 32-bit division where the grid allows it (64-bit division is a long software sequence)
+    const int x = N <= 0x7fffffffll ? (int)n % nx : (int)(n % nx);
+    const int y = N <= 0x7fffffffll ? (int)n / nx : (int)(n / nx);
+    const double rho = mac[n], ux = mac[N + n], uy = mac[2 * N + n], T = mac[3 * N + n];
+    double factor;
+    if constexpr (std::is_same<S, double>::value) {
+        factor = 1.0 - 0.5 / (mu / (rho * T) + 0.5);
+    } else {   // FP32: FP64 divisions are slow on this part, and G is formed in FP32 here
+        factor = (double)(1.0f - 0.5f / ((float)mu / ((float)rho * (float)T) + 0.5f));
+    }
+    add_source_node<S>(n, x, y, nx, ny, bc_x, bc_y, N, nord, mac + N, mac + 2 * N, wall, prof, rho, ux, uy, T,
+                       ux - mac_prev[N + n], uy - mac_prev[2 * N + n], factor, neq);
 }
 
 template <class S>
@@ -292,7 +335,7 @@ __global__ void internal_source_kernel(AuxParams p)
 {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    internal_source_node<S>(n, p.nx, p.ny, p.bc_x, p.bc_y, p.N, p.nord, p.mac, p.mac_prev, p.neq, p.wall,
+    internal_source_node<S>(n, p.nx, p.ny, p.bc_x, p.bc_y, p.N, p.nord, p.mu, p.mac, p.mac_prev, p.neq, p.wall,
                             p.prof);
 }
 
@@ -320,8 +363,8 @@ __global__ void internal_source_batch_kernel(const CaseDesc* cases, const int* b
     const long long n = (long long)(b - block_start[lo]) * blockDim.x + threadIdx.x;
     if (n >= c.N) return;
     const int in = c.cur ^ flip;          // the state before the step; the new one is in ^ 1
-    internal_source_node<S>(n, c.nx, c.ny, c.bc_x, c.bc_y, c.N, c.nord, c.mac[in ^ 1], c.mac[in], c.neq[in ^ 1],
-                            c.wall, c.prof);
+    internal_source_node<S>(n, c.nx, c.ny, c.bc_x, c.bc_y, c.N, c.nord, c.mu, c.mac[in ^ 1], c.mac[in],
+                            c.neq[in ^ 1], c.wall, c.prof);
 }
 
 // Batched init and moments over members [c0, c1) of a batch (blocks from block_start[c0] = block0
@@ -340,6 +383,9 @@ __global__ void init_batch_kernel(const CaseDesc* cases, const int* block_start,
     const int cur = d.cur ^ flip;
     const double* const* in = fld.f[c - c0];
     init_node<S>(d.mac[cur], d.neq[cur], d.N, d.nord, d.status, n, in[0][n], in[1][n], in[2][n], in[3][n]);
+    if (d.split == 1)
+        init_internal_source<S>(n, d.nx, d.ny, d.bc_x, d.bc_y, d.N, d.nord, in[1], in[2], d.wall, d.prof, in[0][n],
+                                in[3][n], d.neq[cur]);
 }
 
 template <class S>

@@ -34,13 +34,14 @@ struct Launch {
     cudaStream_t stream;
 };
 
-typedef cudaError_t (*StepFn)(const StepParams& p, int order, const Launch& l);
+// pred: the internal split's predictor pass instead of a step (see step_kernel).
+typedef cudaError_t (*StepFn)(const StepParams& p, int order, bool pred, const Launch& l);
 // Raises the step kernel's dynamic shared-memory limit to what the device allows per block
 // (optin) less the kernel's static shared memory, which it reports in *static_bytes.
 typedef cudaError_t (*SmemFn)(int order, size_t optin, size_t* static_bytes);
 
 #define POND_DECLARE_STEP(TAG)                                               \
-    cudaError_t step_##TAG(const StepParams& p, int order, const Launch& l); \
+    cudaError_t step_##TAG(const StepParams& p, int order, bool pred, const Launch& l); \
     cudaError_t smem_##TAG(int order, size_t optin, size_t* static_bytes);
 
 #define POND_DECLARE_STEP_ALL(PREC) \

@@ -55,6 +55,7 @@ struct CaseDesc {
     DevStatus* status;
     double wall[4][4];          // prescribed sides x-low, x-high, y-low, y-high: (u_x, u_y, T, rho)
     const double* prof[4];      // per side: null (uniform wall[side]) or [n][4] states along it
+    double* upred;              // internal split: [2][N] predictor velocities (u_x, u_y); else null
 };
 
 struct StepParams {
@@ -81,6 +82,7 @@ struct CaseRun {
     DevStatus* status;
     double wall[4][4];
     const double* prof[4];
+    double* upred;
 };
 
 // Resolves the block's case (warp 0 calls it).  In a batched launch every lane runs the same
@@ -124,6 +126,7 @@ __device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r, Ca
         for (int k = 0; k < 4; ++k) r.wall[w][k] = c->wall[w][k];
         r.prof[w] = c->prof[w];
     }
+    r.upred = c->upred;
 }
 
 // Prescribed sides (the paper gives no discretisation for walls, nor for the prescribed
@@ -678,9 +681,10 @@ __device__ __forceinline__ FinalFrame<R, N> final_frame(const RefState<R>& rf, d
 // moved into lambda*, the reference part rho_r moved lambda_r -> lambda* is added (its order
 // 0 and 1 terms are the equilibrium's), and the non-equilibrium part is relaxed and written.
 // A*_10 = A*_01 = 0 hold by definition of lambda*.
-template <class S, class R, int N>
-__device__ __forceinline__ void collide_f(const FinalFrame<R, N>& ff, const RefState<R>& rf, R* Af, S* nout,
-                                          long long Nn, long long node)
+// The arithmetic of collide_f without the writes: Af becomes the relaxed non-equilibrium
+// coefficients of lambda* (slots 1, 2 zero; slot 0 unused).
+template <class R, int N>
+__device__ __forceinline__ void relax_f(const FinalFrame<R, N>& ff, const RefState<R>& rf, R* Af)
 {
     constexpr int NC = ncoef(N);
     retarget<R, N>(ff.dx, ff.dy, Af, Af);
@@ -689,32 +693,56 @@ __device__ __forceinline__ void collide_f(const FinalFrame<R, N>& ff, const RefS
 #pragma unroll
         for (int q = 0; q <= N - pp; ++q)
             if (pp + q >= 2) Af[slot(pp, q)] += rf.rhoR * tx0(ff.rx, pp) * tx0(ff.ry, q);
-    sto_put<S, R>(nout + 0 * Nn + node, R(0));
-    sto_put<S, R>(nout + 1 * Nn + node, R(0));
+    Af[slot(1, 0)] = R(0);
+    Af[slot(0, 1)] = R(0);
 #pragma unroll
-    for (int m = 3; m < NC; ++m) sto_put<S, R>(nout + (long long)(m - 1) * Nn + node, ff.keep * Af[m]);
+    for (int m = 3; m < NC; ++m) Af[m] = ff.keep * Af[m];
+}
+
+template <class S, class R, int N>
+__device__ __forceinline__ void collide_f(const FinalFrame<R, N>& ff, const RefState<R>& rf, R* Af, S* nout,
+                                          long long Nn, long long node)
+{
+    constexpr int NC = ncoef(N);
+    relax_f<R, N>(ff, rf, Af);
+#pragma unroll
+    for (int m = 1; m < NC; ++m) sto_put<S, R>(nout + (long long)(m - 1) * Nn + node, Af[m]);
 }
 
 // BGK relaxation of g in lambda*: the reference equilibrium moved into lambda* minus the
 // equilibrium of lambda* itself (the same expansion as for a staged node, with the reference as
-// the node and lambda* as the base) is added.  Total and internal splits: B*_00 = B_00^eq by
-// definition of T*.  Non-translational split: T* also takes f's second moment, so B*_00 - U'*
-// balances f's non-equilibrium A*_20 + A*_02 and is relaxed like the other coefficients.
+// the node and lambda* as the base) is added.  Total split: B*_00 = B_00^eq by definition of
+// T*.  Internal split: U* = B*_00 + (1/2) sum G, so B*_00 - U* = (1/2) rho* T* div u, relaxed
+// like the other coefficients.  Non-translational split: T* also takes f's second moment, so
+// B*_00 - U'* balances f's non-equilibrium A*_20 + A*_02 and is relaxed likewise.
+// The arithmetic of collide_g without the writes: Ag becomes the relaxed non-equilibrium
+// coefficients of lambda* (slot 0 zero for the total split).
+template <class R, int N>
+__device__ __forceinline__ void relax_g(int split, const FinalFrame<R, N>& ff, const RefState<R>& rf, R drho,
+                                        R durx, R dury, R dTr, R* Ag)
+{
+    constexpr int NC = ncoef(N);
+    retarget<R, N>(ff.dx, ff.dy, Ag, Ag);
+    const R dP = -(drho * ff.TnR + rf.rhoR * dTr);            // p_r - p*
+    const BaseFrame<R> bf = {rf.PR - dP, ff.isTn, ff.iTn};    // p* = rho T*
+    // U'_r - U'* (non-translational), U_r - U* (internal); unused by the total split
+    const R dE = split == 2 ? (rf.cvR - R(1)) * dP : (split == 1 ? rf.cvR * dP : R(0));
+    add_g_eq_dev<R, N>(split, bf, ff.rx, ff.ry, ff.rdx, ff.rdy, ff.rsig, rf.ER, dE, rf.PR, rf.uxR, rf.uyR,
+                       dP, -durx, -dury, rf.TR, -dTr, Ag);
+    Ag[0] = split != 0 ? ff.keep * Ag[0] : R(0);
+#pragma unroll
+    for (int m = 1; m < NC; ++m) Ag[m] = ff.keep * Ag[m];
+}
+
 template <class S, class R, int N>
 __device__ __forceinline__ void collide_g(int split, const FinalFrame<R, N>& ff, const RefState<R>& rf,
                                           R drho, R durx, R dury, R dTr, R* Ag, S* nout, long long Nn,
                                           long long node)
 {
     constexpr int NC = ncoef(N);
-    retarget<R, N>(ff.dx, ff.dy, Ag, Ag);
-    const R dP = -(drho * ff.TnR + rf.rhoR * dTr);            // p_r - p*
-    const BaseFrame<R> bf = {rf.PR - dP, ff.isTn, ff.iTn};    // p* = rho T*
-    const R dE = split == 2 ? (rf.cvR - R(1)) * dP : R(0);    // U'_r - U'*
-    add_g_eq_dev<R, N>(split, bf, ff.rx, ff.ry, ff.rdx, ff.rdy, ff.rsig, rf.ER, dE, rf.PR, rf.uxR, rf.uyR,
-                       dP, -durx, -dury, rf.TR, -dTr, Ag);
-    sto_put<S, R>(nout + (long long)(NC - 1) * Nn + node, split == 2 ? ff.keep * Ag[0] : R(0));
+    relax_g<R, N>(split, ff, rf, drho, durx, dury, dTr, Ag);
 #pragma unroll
-    for (int m = 1; m < NC; ++m) sto_put<S, R>(nout + (long long)(NC - 1 + m) * Nn + node, ff.keep * Ag[m]);
+    for (int m = 0; m < NC; ++m) sto_put<S, R>(nout + (long long)(NC - 1 + m) * Nn + node, Ag[m]);
 }
 
 // Per-warp sums of the step statistics, one atomic per warp (every lane of the warp calls it).
@@ -789,10 +817,31 @@ __device__ __forceinline__ void prefetch_next_wave(const StepParams& pp, int TX,
     }
 }
 
-// Single-thread-per-node kernel: FP64 arithmetic (2-D and quasi-1-D) and the FP32 quasi-1-D
-// grids.  One CTA per tile of TPB nodes; CTAs resident per SM as step_blocks_per_sm says
-// (the quasi-1-D D2Q16 kernel with FP32 arithmetic is held to three per SM).
-template <class S, class R, int Q1, int P, bool ONE_D, int TPB>
+// Velocity divergence at node (x, y) of the internal split's predictor velocities (central
+// differences; beyond a prescribed side its velocity), in FP64.
+__device__ __forceinline__ double predictor_divergence(const CaseRun& p, int x, int y)
+{
+    const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
+    double v[4];
+    for (int k = 0; k < 4; ++k) {
+        const int comp = k < 2 ? 0 : 1;                  // u_x along x, u_y along y
+        const int w = wall_of(p.bc_x, p.bc_y, p.nx, p.ny, nb[k][0], nb[k][1]);
+        if (w >= 0) {
+            v[k] = side_state(p.wall, p.prof, p.nx, p.ny, w, nb[k][0], nb[k][1])[comp];
+        } else {
+            const long long m = (long long)bc_map(nb[k][1], p.ny, p.bc_y) * p.nx + bc_map(nb[k][0], p.nx, p.bc_x);
+            v[k] = p.upred[comp * p.N + m];
+        }
+    }
+    return 0.5 * (v[0] - v[1]) + 0.5 * (v[2] - v[3]);
+}
+
+// One thread per node, one CTA per tile of TPB nodes; CTAs resident per SM as
+// step_blocks_per_sm says (the quasi-1-D D2Q16 kernel with FP32 arithmetic is held to three per
+// SM).  PRED: the internal split's predictor pass instead of a step: each node streams f once in
+// its previous frame and writes the velocity of the result to upred (other splits' blocks return
+// at once; nothing else is written).
+template <class S, class R, int Q1, int P, bool ONE_D, int TPB, bool PRED>
 __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::is_same<R, double>::value))
     step_kernel(const StepParams pp)
 {
@@ -808,6 +857,9 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
     if (tid < 32) resolve_case(pp, scase, sdesc, tid);
     __syncthreads();
     const CaseRun& p = scase;
+    if constexpr (PRED) {
+        if (p.split != 1) return;                             // the whole block: p is shared
+    }
     const int x = p.tile_x * TX + threadIdx.x;
     const int y = p.tile_y * TY + threadIdx.y;
     const bool active = (x < p.nx) && (y < p.ny);
@@ -853,6 +905,16 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
     double unx = ux0, uny = uy0, Tn = T0;
     R drho = R(0), dubx = R(0), duby = R(0), durx = R(0), dury = R(0), dTr = R(0), dTb = R(0);
     R Af[NC], Ag[NC];         // deviation coefficients of the streamed populations in lambda_bar
+    // internal split: half the velocity divergence at the new time level (from the predictor
+    // velocities), for U = sum g + (1/2) sum G = sum g - (1/2) rho T div u
+    R hD = R(0);
+    if constexpr (!PRED) {
+        if (active && p.split == 1) hD = R(0.5 * predictor_divergence(p, x, y));
+    }
+    // T - T_r = (c_v (T - T_r) from the energy balance - hD T_r) / (c_v + hD): the internal
+    // split's rho (c_v + hD) T = U_s; hD = 0 for the others
+    const R hDT = hD * rf.TR;
+    const R icvD = p.split == 1 ? R(1) / (rf.cvR + hD) : R(p.inv_cv);
 
     if (active) {
         // frame of the iteration relative to the reference: the differences once (FP64, or
@@ -910,12 +972,14 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                         make_phi<R, NG>(la, tx, ty, phi);
                     }
                     // FP32, N = 3: both distributions in one pass over the rows (each record is
-                    // five 16-byte loads and the row overhead is shared); otherwise one pass each
-                    constexpr int ND = (std::is_same<R, float>::value && NG == 3) ? 2 : 1;
+                    // five 16-byte loads and the row overhead is shared); otherwise one pass each;
+                    // the predictor streams f only
+                    constexpr int ND = (std::is_same<R, float>::value && NG == 3 && !PRED) ? 2 : 1;
+                    constexpr int NDIST = PRED ? 1 : 2;
                     // one pass each (ND = 1) share their code: unrolled, the two passes kept
                     // both sets of row temporaries live and spilled on D2Q25 (702 -> 534 us)
 #pragma unroll 1
-                    for (int d0 = 0; d0 < 2; d0 += ND) {
+                    for (int d0 = 0; d0 < NDIST; d0 += ND) {
                         // x pass once per row of the union of the y stencils, folded into Z_q,
                         // then added to the b's whose y stencil contains the row
                         R acc[ND][Q1][NG + 1];
@@ -1096,6 +1160,10 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
             // rho (u - u_bar) = rho_r (u_r - u_bar) + sqrt(T_bar) sum_i c_i f'_i
             dubx = (rf.rhoR * rbx + sT * Af[slot(1, 0)]) * irho;      // u - u_bar
             duby = (rf.rhoR * rby + sT * Af[slot(0, 1)]) * irho;
+            if constexpr (PRED) {
+                ++k;
+                break;                                                // the predictor: u only
+            }
             durx = dubx - rbx;                                        // u - u_r
             dury = duby - rby;
             // energy deviation: sum g' (total, internal), plus sum |C|^2/2 f' for the
@@ -1109,7 +1177,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
             R cvdT = (dEt - rf.eR * drho) * irho;
             if (p.split != 1)
                 cvdT -= R(0.5) * (durx * (R(2) * rf.uxR + durx) + dury * (R(2) * rf.uyR + dury));
-            dTr = cvdT * R(p.inv_cv);                                 // T - T_r
+            dTr = (cvdT - hDT) * icvD;                                // T - T_r
             dTb = dTr + rbT;                                          // T - T_bar
             sum_dux += dubx;
             sum_duy += duby;
@@ -1132,6 +1200,13 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
         uny = uy0 + (double)sum_duy;
         Tn = rf.T + (double)dTr;
         if (!(Tn > 0.0)) bad = true;
+    }
+    if constexpr (PRED) {
+        if (active) {
+            p.upred[node] = ux0 + (double)dubx;                       // u of f streamed once
+            p.upred[N + node] = uy0 + (double)duby;
+        }
+        return;
     }
 
     // ---- collision in the frame of the final moments and write-back ---------------------------

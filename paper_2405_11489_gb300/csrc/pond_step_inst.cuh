@@ -8,12 +8,19 @@
 
 namespace pond {
 
-cudaError_t POND_CAT(step, POND_TAG)(const StepParams& p, int order, const Launch& l)
+template <int P, bool PRED>
+static void launch_step(const StepParams& p, const Launch& l)
 {
-    if (order == 3)
-        step_kernel<POND_S, POND_R, POND_Q1, 4, POND_ONED, step_threads(POND_ONED)><<<l.grid, l.block, l.smem, l.stream>>>(p);
-    else
-        step_kernel<POND_S, POND_R, POND_Q1, 3, POND_ONED, step_threads(POND_ONED)><<<l.grid, l.block, l.smem, l.stream>>>(p);
+    step_kernel<POND_S, POND_R, POND_Q1, P, POND_ONED, step_threads(POND_ONED), PRED><<<l.grid, l.block, l.smem, l.stream>>>(p);
+}
+
+cudaError_t POND_CAT(step, POND_TAG)(const StepParams& p, int order, bool pred, const Launch& l)
+{
+    if (order == 3) {
+        if (pred) launch_step<4, true>(p, l); else launch_step<4, false>(p, l);
+    } else {
+        if (pred) launch_step<3, true>(p, l); else launch_step<3, false>(p, l);
+    }
     return cudaGetLastError();
 }
 
@@ -29,13 +36,24 @@ static cudaError_t set_smem_limit(K kernel, size_t optin, size_t* static_bytes)
                                 (int)(optin - fa.sharedSizeBytes));
 }
 
+// Sets the limit of the step kernel and of its predictor variant; *static_bytes is the larger
+// static part of the two.
+template <int P>
+static cudaError_t set_smem_limits(size_t optin, size_t* static_bytes)
+{
+    size_t s0 = 0, s1 = 0;
+    cudaError_t e = set_smem_limit(step_kernel<POND_S, POND_R, POND_Q1, P, POND_ONED, step_threads(POND_ONED), false>,
+                                   optin, &s0);
+    if (e == cudaSuccess)
+        e = set_smem_limit(step_kernel<POND_S, POND_R, POND_Q1, P, POND_ONED, step_threads(POND_ONED), true>, optin,
+                           &s1);
+    *static_bytes = s0 > s1 ? s0 : s1;
+    return e;
+}
+
 cudaError_t POND_CAT(smem, POND_TAG)(int order, size_t optin, size_t* static_bytes)
 {
-    if (order == 3)
-        return set_smem_limit(step_kernel<POND_S, POND_R, POND_Q1, 4, POND_ONED, step_threads(POND_ONED)>, optin,
-                              static_bytes);
-    return set_smem_limit(step_kernel<POND_S, POND_R, POND_Q1, 3, POND_ONED, step_threads(POND_ONED)>, optin,
-                          static_bytes);
+    return order == 3 ? set_smem_limits<4>(optin, static_bytes) : set_smem_limits<3>(optin, static_bytes);
 }
 
 }  // namespace pond

@@ -4,12 +4,11 @@ FP64 oracle, here on the GPU without the oracle in the loop):
 
 - shear-wave decay rate nu k^2, nu = tau T (Sec. III.B, shear viscosity), at rest and under
   a Mach 1.5 background flow;
-- entropy-wave decay rate alpha k^2 with alpha = tau T (Pr = 1), total split (FP32) and
-  internal split (FP64: see the note at the test);
+- entropy-wave decay rate alpha k^2 with alpha = tau T (Pr = 1), total and internal split;
 - speed of a weak pressure front sqrt(gamma T) (Sec. III.B, speed of sound);
 - attenuation of a standing sound wave nu k^2, the value that the bulk viscosity
   eta = (2/D - r/c_v) mu of Sec. II gives in D = 2 with Pr = 1 (without it: gamma nu k^2 / 2),
-  for the total split on D2Q16 and the non-translational split on D2Q25.
+  for the total and internal splits on D2Q16 and the non-translational split on D2Q25.
 """
 import math
 
@@ -58,10 +57,7 @@ def test_shear_wave_decay_rate(pond, ma):
     s.close()
 
 
-# The internal split's explicit source amplifies sound, so rounding noise grows in it: on this
-# grid it reaches 1e-3 of the sound speed by step 600 in FP64 and turns the state non-physical
-# near step 500 in FP32 (350 in BF16); the internal split is therefore checked in FP64 here.
-@pytest.mark.parametrize("split,precision", [("total", "fp32"), ("internal", "fp64")])
+@pytest.mark.parametrize("split,precision", [("total", "fp32"), ("internal", "fp32"), ("internal", "fp64")])
 def test_thermal_wave_decay_rate(pond, split, precision):
     case = W.thermal_wave(n=128, amp=1e-3, mu=0.05, steps=600)
     s = _sim(pond, case, precision=precision, split=split)
@@ -96,7 +92,8 @@ def test_sound_speed(pond, gamma):
     s.close()
 
 
-@pytest.mark.parametrize("split,lattice,gamma", [("total", 16, 1.4), ("total", 16, 1.8), ("nt", 25, 1.8)])
+@pytest.mark.parametrize("split,lattice,gamma", [("total", 16, 1.4), ("total", 16, 1.8), ("nt", 25, 1.8),
+                                                 ("internal", 16, 1.4), ("internal", 16, 1.8)])
 def test_sound_attenuation_gives_the_bulk_viscosity(pond, split, lattice, gamma):
     n, mu, A = 64, 0.05, 1e-4
     x = np.arange(n)[None, :]
