@@ -654,9 +654,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="pond", choices=["pond", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=300,
-                    help="requests of the Poisson serving run (the full stream is 10 000: "
-                         "python -m paper_2405_11489_gb300.serve)")
+    ap.add_argument("--serve-requests", type=int, default=10000,
+                    help="requests of the Poisson serving run (default: the configured stream of "
+                         "10 000 requests at 50 per second, about 200 s)")
     ap.add_argument("--profile-case", choices=["d2q25", "fp64", "tubes"], default=None,
                     help="time one other configuration's batched steps (inside the NVTX range "
                          "timed_steps, for profiler runs) and print its rate")

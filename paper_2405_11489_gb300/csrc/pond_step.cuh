@@ -411,6 +411,26 @@ __device__ __forceinline__ void z_contract(const R* phi, const R* X, R* Z)
     }
 }
 
+// z_contract for (f, g) pairs: Z[q] = (Z_q of the f half of X, Z_q of the g half).
+template <int N>
+__device__ __forceinline__ void z_contract_pairs(const float* phi, const float2* X, float2* Z)
+{
+    int n = 0;
+#pragma unroll
+    for (int q = 0; q <= N; ++q) {
+        float zf = 0.f, zg = 0.f;
+#pragma unroll
+        for (int l = 0; l <= q; ++l)
+#pragma unroll
+            for (int k = 0; k <= N - q; ++k) {
+                zf += phi[n] * X[slot(k, l)].x;
+                zg += phi[n] * X[slot(k, l)].y;
+                ++n;
+            }
+        Z[q] = make_float2(zf, zg);
+    }
+}
+
 // Node-interleaved shared-memory records.  N = 3: 20 values per node, f in 0..9 and g in
 // 10..19.  N = 4, FP32: f in 0..14 and g in 16..30 (each distribution 16-byte aligned) in
 // records of 36 floats; FP64: f in 0..14 and g in 15..29, records of 30 doubles (the box must
@@ -420,6 +440,11 @@ template <class R, int N>
 __host__ __device__ constexpr int rec_len() { return N == 3 ? 20 : (sizeof(R) == 4 ? 36 : 30); }
 template <class R, int N>
 __host__ __device__ constexpr int rec_goff() { return N == 3 ? 10 : (sizeof(R) == 4 ? 16 : 15); }
+
+// FP32 arithmetic with N = 3 keeps (f_m, g_m) pairs: record = f_0 g_0 f_1 g_1 ... f_9 g_9, so
+// that both distributions stream through packed two-lane FMAs (see stream_pairs).
+template <class R, int N>
+__host__ __device__ constexpr bool pair_records() { return sizeof(R) == 4 && N == 3; }
 
 template <class R, int N>
 __device__ __forceinline__ void store_rec(R* dst, const R* Df, const R* Dg)
@@ -432,7 +457,7 @@ __device__ __forceinline__ void store_rec(R* dst, const R* Df, const R* Dg)
         if constexpr (std::is_same<R, float>::value) {
 #pragma unroll
             for (int k = 0; k < 5; ++k)
-                reinterpret_cast<float4*>(dst)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                reinterpret_cast<float4*>(dst)[k] = make_float4(Df[2 * k], Dg[2 * k], Df[2 * k + 1], Dg[2 * k + 1]);
         } else {
 #pragma unroll
             for (int k = 0; k < 10; ++k) reinterpret_cast<double2*>(dst)[k] = make_double2(v[2 * k], v[2 * k + 1]);
@@ -860,8 +885,21 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
     if constexpr (PRED) {
         if (p.split != 1) return;                             // the whole block: p is shared
     }
-    const int x = p.tile_x * TX + threadIdx.x;
-    const int y = p.tile_y * TY + threadIdx.y;
+    // Node of this thread.  FP32 2-D grids: each warp covers a 16 x 2 block of the tile (a
+    // TX x 32/TX block on tiles narrower than 16, 32 x 1 on one-row tiles), its consecutive
+    // lanes running down a column (lane = x * rows + y), and its lanes stream the same
+    // absolute rows together: the nodes of a column then read the same staged record in the
+    // same load, and a 16-byte shared load merges equal addresses within each half warp.
+    // Otherwise a warp covers 32 nodes of a row.  Tile sides are powers of two, TX * TY = 256.
+    int lx = threadIdx.x, ly = threadIdx.y;
+    if constexpr (!ONE_D && pair_records<R, grad_order_of_q1(Q1)>()) {
+        const int wx = TX >= 16 ? (TY >= 2 ? 16 : 32) : TX, wy = 32 / wx, wpr = TX / wx;
+        const int w = tid >> 5, l = tid & 31;
+        lx = (w % wpr) * wx + l / wy;
+        ly = (w / wpr) * wy + l % wy;
+    }
+    const int x = p.tile_x * TX + lx;
+    const int y = p.tile_y * TY + ly;
     const bool active = (x < p.nx) && (y < p.ny);
     const long long N = p.N;
     const long long node = active ? (long long)y * p.nx + x : 0;
@@ -971,10 +1009,110 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                         const Tau<R, NG> ty = make_tau_sig<R, NG>(s_rb, dy_rb, sig_t);
                         make_phi<R, NG>(la, tx, ty, phi);
                     }
-                    // FP32, N = 3: both distributions in one pass over the rows (each record is
-                    // five 16-byte loads and the row overhead is shared); otherwise one pass each;
-                    // the predictor streams f only
-                    constexpr int ND = (std::is_same<R, float>::value && NG == 3 && !PRED) ? 2 : 1;
+                  if constexpr (pair_records<R, NG>()) {
+                    // FP32, N = 3: f and g stream together as (f_m, g_m) pairs through packed
+                    // two-lane FMAs (the x pass and the row weights; the fold stays scalar).  The
+                    // warp's in-box lanes take the union of their rows in one order, rows
+                    // outside a lane's y stencils adding with weight 0.
+                    float2 acc[Q1][NG + 1];
+#pragma unroll
+                    for (int b = 0; b < Q1; ++b)
+#pragma unroll
+                        for (int q = 0; q <= NG; ++q) acc[b][q] = make_float2(0.f, 0.f);
+                    const bool inbox = rows_in && cols_in;
+                    const unsigned bmask = __ballot_sync(__activemask(), inbox);
+                    if (inbox) {
+                        const int r_lo = __reduce_min_sync(bmask, y + rmin);
+                        const int r_hi = __reduce_max_sync(bmask, y + rmax);
+                        float2 w2x[P];
+#pragma unroll
+                        for (int ii = 0; ii < P; ++ii) w2x[ii] = make_float2(wx[ii], wx[ii]);
+                        const float* rowp = sm + ((size_t)(r_lo - oy) * bw + tx0) * REC;
+                        constexpr int kRowUnroll = P == 4 ? 2 : 1;
+#pragma unroll kRowUnroll
+                        for (int r = r_lo; r <= r_hi; ++r, rowp += (size_t)bw * REC) {
+                            float2 X[NC];
+#pragma unroll
+                            for (int ii = 0; ii < P; ++ii) {
+                                const float4* q4 = reinterpret_cast<const float4*>(rowp + ii * REC);
+#pragma unroll
+                                for (int k = 0; k < NC / 2; ++k) {
+                                    const float4 t = q4[k];
+                                    const float2 lo = make_float2(t.x, t.y), hi = make_float2(t.z, t.w);
+                                    if (ii == 0) {
+                                        X[2 * k] = __fmul2_rn(w2x[0], lo);
+                                        X[2 * k + 1] = __fmul2_rn(w2x[0], hi);
+                                    } else {
+                                        X[2 * k] = __ffma2_rn(w2x[ii], lo, X[2 * k]);
+                                        X[2 * k + 1] = __ffma2_rn(w2x[ii], hi, X[2 * k + 1]);
+                                    }
+                                }
+                            }
+                            float2 Z[NG + 1];
+                            z_contract_pairs<NG>(phi, X, Z);
+#pragma unroll
+                            for (int b = 0; b < Q1; ++b) {
+                                const int j = r - y - jy[b];
+                                const float w = ((unsigned)j < (unsigned)P) ? pick<float>(wy[b], j, P) : 0.f;
+                                const float2 w2 = make_float2(w, w);
+#pragma unroll
+                                for (int q = 0; q <= NG; ++q) acc[b][q] = __ffma2_rn(w2, Z[q], acc[b][q]);
+                            }
+                        }
+                    } else {
+                        ++fallbacks;
+                        // global gathers; indices into the register arrays stay static
+#pragma unroll
+                        for (int b = 0; b < Q1; ++b)
+#pragma unroll 1
+                            for (int j = 0; j < P; ++j) {
+                                const float wyj = pick<float>(wy[b], j, P);
+#pragma unroll 1
+                                for (int ii = 0; ii < P; ++ii) {
+                                    const float W = wyj * pick<float>(wx, ii, P);
+                                    float D[2 * NC];
+                                    source_at<S, float, NG>(p, rf, x + jx + ii, y + jy[b] + j, D, D + NC);
+                                    float2 X[NC], Z[NG + 1];
+#pragma unroll
+                                    for (int m = 0; m < NC; ++m) X[m] = make_float2(D[m], D[NC + m]);
+                                    z_contract_pairs<NG>(phi, X, Z);
+                                    const float2 W2 = make_float2(W, W);
+#pragma unroll
+                                    for (int q = 0; q <= NG; ++q) acc[b][q] = __ffma2_rn(W2, Z[q], acc[b][q]);
+                                }
+                            }
+                    }
+                    // populations (a, b): f'_ab = w_b sum_q hn_b(q) acc_b(q); their moments
+                    float Sf[NG + 1], Sg[NG + 1];
+#pragma unroll
+                    for (int q = 0; q <= NG; ++q) { Sf[q] = 0.f; Sg[q] = 0.f; }
+#pragma unroll
+                    for (int b = 0; b < Q1; ++b) {
+                        const LatRow<R>& lb = lat[b];
+                        float vf = 0.f, vg = 0.f;
+#pragma unroll
+                        for (int q = 0; q <= NG; ++q) {
+                            vf += lb.hn[q] * acc[b][q].x;
+                            vg += lb.hn[q] * acc[b][q].y;
+                        }
+                        vf *= lb.w;
+                        vg *= lb.w;
+#pragma unroll
+                        for (int q = 0; q <= NG; ++q) {
+                            Sf[q] += vf * lb.he[q];
+                            Sg[q] += vg * lb.he[q];
+                        }
+                    }
+#pragma unroll
+                    for (int pq = 0; pq <= NG; ++pq)
+#pragma unroll
+                        for (int q = 0; q <= NG - pq; ++q) {
+                            Af[slot(pq, q)] += la.he[pq] * Sf[q];
+                            Ag[slot(pq, q)] += la.he[pq] * Sg[q];
+                        }
+                  } else {
+                    // one pass per distribution (FP64; D2Q25); the predictor streams f only
+                    constexpr int ND = 1;
                     constexpr int NDIST = PRED ? 1 : 2;
                     // one pass each (ND = 1) share their code: unrolled, the two passes kept
                     // both sets of row temporaries live and spilled on D2Q25 (702 -> 534 us)
@@ -1082,6 +1220,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                                 }
                         }
                     }
+                  }
                 }
             } else {
                 // quasi-1-D (ny = 1): every y tap reads row 0 and the y weights sum to one, so
@@ -1096,15 +1235,38 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
 #pragma unroll
                     for (int m = 0; m < 2 * NC; ++m) Ri[m] = R(0);
                     if (tx0 >= 0 && tx0 + P <= bw) {
+                        if constexpr (pair_records<R, NG>()) {
+                            // (f_m, g_m) pairs through packed two-lane FMAs
+                            float2 R2[NC];
 #pragma unroll
-                        for (int ii = 0; ii < P; ++ii) {
-                            R v[NC];
-                            load_one<R, NG, 0>(sm + (size_t)(tx0 + ii) * REC, v);
+                            for (int m = 0; m < NC; ++m) R2[m] = make_float2(0.f, 0.f);
 #pragma unroll
-                            for (int m = 0; m < NC; ++m) Ri[m] += wx[ii] * v[m];
-                            load_one<R, NG, 1>(sm + (size_t)(tx0 + ii) * REC, v);
+                            for (int ii = 0; ii < P; ++ii) {
+                                const float4* q4 = reinterpret_cast<const float4*>(sm + (size_t)(tx0 + ii) * REC);
+                                const float2 w2 = make_float2(wx[ii], wx[ii]);
 #pragma unroll
-                            for (int m = 0; m < NC; ++m) Ri[NC + m] += wx[ii] * v[m];
+                                for (int k = 0; k < NC / 2; ++k) {
+                                    const float4 t = q4[k];
+                                    R2[2 * k] = __ffma2_rn(w2, make_float2(t.x, t.y), R2[2 * k]);
+                                    R2[2 * k + 1] = __ffma2_rn(w2, make_float2(t.z, t.w), R2[2 * k + 1]);
+                                }
+                            }
+#pragma unroll
+                            for (int m = 0; m < NC; ++m) {
+                                Ri[m] = R2[m].x;
+                                Ri[NC + m] = R2[m].y;
+                            }
+                        } else {
+#pragma unroll
+                            for (int ii = 0; ii < P; ++ii) {
+                                R v[NC];
+                                load_one<R, NG, 0>(sm + (size_t)(tx0 + ii) * REC, v);
+#pragma unroll
+                                for (int m = 0; m < NC; ++m) Ri[m] += wx[ii] * v[m];
+                                load_one<R, NG, 1>(sm + (size_t)(tx0 + ii) * REC, v);
+#pragma unroll
+                                for (int m = 0; m < NC; ++m) Ri[NC + m] += wx[ii] * v[m];
+                            }
                         }
                     } else {
                         ++fallbacks;

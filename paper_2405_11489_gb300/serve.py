@@ -173,6 +173,7 @@ class Server:
                 "statuses": sorted({c.status for c in served}),
                 "status_counts": {st: sum(1 for c in served if c.status == st)
                                   for st in sorted({c.status for c in served})},
+                "nonphysical_count": sum(1 for c in served if c.status.startswith("non-physical")),
                 # requests whose state turned non-physical (first 20): id, type, grid, split, precision
                 "nonphysical": [(c.rid, c.what) for c in served if c.status.startswith("non-physical")][:20]}
 

@@ -193,10 +193,14 @@ def test_fp64_sod_400x4_matches_oracle(pond, orc):
     sim = pond.Simulation(pond.Config(nx=c.nx, ny=c.ny, precision="fp64", gamma=c.gamma, mu=c.mu,
                                       bc_x=c.bc_x, bc_y=c.bc_y, pc_fixed_iters=3))
     sim.set_state(c.rho, c.ux, c.uy, c.T)
-    for _ in range(c.steps):
-        st = orc.step(ocfg, st).state
-    sim.step(c.steps)
-    compare(orc, ocfg, sim, st, 1e-11, "sod")
+    done = 0
+    for upto in (50, 100, 200, c.steps):         # the error after each stretch, printed
+        for _ in range(upto - done):
+            st = orc.step(ocfg, st).state
+        sim.step(upto - done)
+        done = upto
+        errs = compare(orc, ocfg, sim, st, 1e-11, "sod")
+        print("sod fp64 step %d: max rel err %.2e %s" % (done, max(errs.values()), errs))
     sim.close()
 
 
