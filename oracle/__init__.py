@@ -112,6 +112,8 @@ def _lib_handle():
             lib.or_moments_field.argtypes = [P(Config)] + [_D] * 10
             lib.or_stream_node.argtypes = ([P(Config)] + [_D] * 5 + [ctypes.c_int] * 2
                                            + [ctypes.c_double] * 3 + [_D] * 2)
+            lib.or_stream_node_kept.argtypes = ([P(Config)] + [_D] * 5 + [ctypes.c_int] * 2
+                                                + [ctypes.c_double] * 6 + [_D] * 2)
             lib.or_step.argtypes = ([P(Config)] + [_D] * 10
                                     + [P(ctypes.c_int32), P(ctypes.c_int64)])
             lib.or_collide_node.argtypes = [P(Config), _D, _D] + [ctypes.c_double] * 3 + [_D] * 3
@@ -207,12 +209,19 @@ def moments(cfg: Config, st: State):
     return tuple(out)
 
 
-def stream_node(cfg: Config, st: State, x: int, y: int, frame):
+def stream_node(cfg: Config, st: State, x: int, y: int, frame, stencil_frame=None):
+    """Populations streamed to node (x, y) on the lattice of frame; the stencils are those the
+    departure points of stencil_frame select (default: of frame itself)."""
     Q = cfg.q1 * cfg.q1
     P = np.zeros(Q)
     G = np.zeros(Q)
-    _lib_handle().or_stream_node(ctypes.byref(cfg), _p(st.f), _p(st.g), _p(st.ux), _p(st.uy),
-                                 _p(st.T), x, y, *map(float, frame), _p(P), _p(G))
+    if stencil_frame is None:
+        _lib_handle().or_stream_node(ctypes.byref(cfg), _p(st.f), _p(st.g), _p(st.ux), _p(st.uy),
+                                     _p(st.T), x, y, *map(float, frame), _p(P), _p(G))
+    else:
+        _lib_handle().or_stream_node_kept(ctypes.byref(cfg), _p(st.f), _p(st.g), _p(st.ux), _p(st.uy),
+                                          _p(st.T), x, y, *map(float, frame), *map(float, stencil_frame),
+                                          _p(P), _p(G))
     return P, G
 
 

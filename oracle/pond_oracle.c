@@ -31,7 +31,12 @@
  *   - cubic (4-point) Lagrange interpolation by default, 3-point as an option;
  *   - predictor-corrector: guess = previous frame of the node, metric
  *     max(|du|/sqrt(T_bar), |dT|/T_bar), stop at tolerance or iteration cap, or after
- *     exactly K iterations in fixed mode;
+ *     exactly K iterations in fixed mode; from one iteration to the next the stencil nodes
+ *     of each population are kept while the departure point stays within a quarter cell of
+ *     the range they were chosen for, only their weights following the frame: choosing
+ *     them again at every iteration makes the iteration map jump where a departure point
+ *     crosses the 3-point stencil's half-integer boundary, and the iteration then cycles
+ *     between two frames without a fixed point;
  *   - collision in the frame of the final moments, after projecting into it;
  *   - internal-energy split source (Eq. int_g_evolution), integrated along the
  *     characteristics by the trapezoidal rule, the same second-order rule that gives
@@ -451,29 +456,45 @@ static const double *side_state(const or_config *cfg, int w, int gx, int gy)
     return cfg->profile[w] + 4 * (size_t)along;
 }
 
-/* Lagrange weights of a p-point stencil around the departure coordinate xd; returns the
- * first stencil node.  Cubic: nodes floor(xd)-1 .. floor(xd)+2.  Quadratic: nodes
- * m-1 .. m+1 with m = floor(xd + 1/2). */
-static int lagrange_stencil(double xd, int order, double *wts)
+/* Weights of the stencil whose first node is base at departure point xd: the Lagrange
+ * polynomials through the stencil's nodes, t = xd - (base + 1) the position relative to its
+ * second node.  For the stencil that lagrange_stencil chooses t lies in [0, 1) (4-point) or
+ * [-1/2, 1/2) (3-point); a stencil kept from an earlier departure point may give t slightly
+ * outside. */
+static void lagrange_weights_at(double xd, int order, int base, double *wts)
 {
+    double t = xd - (double)(base + 1);
     if (order == 3) {
-        double fl = floor(xd);
-        double t = xd - fl;                      /* position relative to node floor(xd), in [0,1) */
         /* nodes at -1, 0, 1, 2 */
         wts[0] = -t * (t - 1.0) * (t - 2.0) / 6.0;
         wts[1] = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
         wts[2] = -(t + 1.0) * t * (t - 2.0) / 2.0;
         wts[3] = (t + 1.0) * t * (t - 1.0) / 6.0;
-        return (int)fl - 1;
     } else {
-        double m = floor(xd + 0.5);
-        double t = xd - m;                       /* in [-1/2, 1/2) */
         /* nodes at -1, 0, 1 */
         wts[0] = t * (t - 1.0) / 2.0;
         wts[1] = (1.0 - t) * (1.0 + t);
         wts[2] = t * (t + 1.0) / 2.0;
-        return (int)m - 1;
     }
+}
+
+/* Whether the stencil whose first node is base still serves departure point xd: t lies in the
+ * range the stencil was chosen for ([0, 1) for 4 points, [-1/2, 1/2) for 3) widened by a
+ * quarter cell on each side, so that a kept stencil extrapolates by a quarter cell at most. */
+static int stencil_holds(double xd, int order, int base)
+{
+    double t = xd - (double)(base + 1);
+    return order == 3 ? (t >= -0.25 && t < 1.25) : (t >= -0.75 && t < 0.75);
+}
+
+/* The stencil of departure point xd: 4-point (order 3) on nodes floor(xd) - 1 .. + 2, or
+ * 3-point (order 2) on nodes m - 1 .. m + 1, m = floor(xd + 1/2) (round half up).  Returns its
+ * first node; wts receives the weights. */
+static int lagrange_stencil(double xd, int order, double *wts)
+{
+    int base = order == 3 ? (int)floor(xd) - 1 : (int)floor(xd + 0.5) - 1;
+    lagrange_weights_at(xd, order, base, wts);
+    return base;
 }
 
 /* ---------------------------------------------------------------------------------- */
@@ -534,7 +555,14 @@ static void source_coefficients(const or_src *S, or_memo *M, int gx, int gy, or_
     *Ag = &M->Ag[slot];
 }
 
-static void stream_node(const or_src *S, or_memo *M, int x, int y, or_frame bar, double *P, double *G)
+/* base (optional, 2 Q entries): the first stencil node of each population along x and y.
+ * With keep = 0 the stencils are chosen from this frame's departure points and stored in
+ * base; with keep = 1 a stored stencil is kept while it still serves the departure point
+ * (stencil_holds), only its weights following the frame, and is chosen again and stored
+ * otherwise.  The predictor-corrector carries its stencils this way from one iteration to the
+ * next. */
+static void stream_node_base(const or_src *S, or_memo *M, int x, int y, or_frame bar, int *base, int keep,
+                             double *P, double *G)
 {
     const or_config *cfg = S->cfg;
     const or_lattice *L = S->L;
@@ -545,8 +573,19 @@ static void stream_node(const or_src *S, or_memo *M, int x, int y, or_frame bar,
         double Cx = sT * L->cx[i] + bar.ux, Cy = sT * L->cy[i] + bar.uy;
         double xd = (double)x - Cx * 1.0, yd = (double)y - Cy * 1.0;   /* delta_t = 1 */
         double wx[4], wy[4];
-        int bx = lagrange_stencil(xd, cfg->interp_order, wx);
-        int by = lagrange_stencil(yd, cfg->interp_order, wy);
+        int bx, by;
+        if (base && keep && stencil_holds(xd, cfg->interp_order, base[i]))
+            lagrange_weights_at(xd, cfg->interp_order, bx = base[i], wx);
+        else
+            bx = lagrange_stencil(xd, cfg->interp_order, wx);
+        if (base && keep && stencil_holds(yd, cfg->interp_order, base[L->Q + i]))
+            lagrange_weights_at(yd, cfg->interp_order, by = base[L->Q + i], wy);
+        else
+            by = lagrange_stencil(yd, cfg->interp_order, wy);
+        if (base) {
+            base[i] = bx;
+            base[L->Q + i] = by;
+        }
         double fi = 0.0, gi = 0.0;
         for (int ky = 0; ky < p; ++ky) {
             for (int kx = 0; kx < p; ++kx) {
@@ -562,6 +601,12 @@ static void stream_node(const or_src *S, or_memo *M, int x, int y, or_frame bar,
     }
 }
 
+/* Streaming with the stencils of this frame's departure points. */
+static void stream_node(const or_src *S, or_memo *M, int x, int y, or_frame bar, double *P, double *G)
+{
+    stream_node_base(S, M, x, y, bar, NULL, 0, P, G);
+}
+
 /* Exported for the tests: stream at node (x, y) in a prescribed frame. */
 int or_stream_node(const or_config *cfg, const double *f, const double *g, const double *fux,
                    const double *fuy, const double *fT, int x, int y, double ux, double uy,
@@ -574,6 +619,26 @@ int or_stream_node(const or_config *cfg, const double *f, const double *g, const
     if (!M) return -2;
     or_frame bar = {ux, uy, T};
     stream_node(&S, M, x, y, bar, P, G);
+    free(M);
+    return 0;
+}
+
+/* Exported for the tests: stream at node (x, y) in frame (ux, uy, T) with the stencils that
+ * the departure points of frame (sux, suy, sT) select (as the predictor-corrector keeps the
+ * stencils of its first iteration). */
+int or_stream_node_kept(const or_config *cfg, const double *f, const double *g, const double *fux,
+                        const double *fuy, const double *fT, int x, int y, double ux, double uy,
+                        double T, double sux, double suy, double sT, double *P, double *G)
+{
+    or_lattice L;
+    make_lattice(cfg->q1, &L);
+    or_src S = {cfg, &L, f, g, fux, fuy, fT};
+    or_memo *M = (or_memo *)malloc(sizeof(or_memo));
+    if (!M) return -2;
+    int base[2 * OR_MAXQ];
+    or_frame sel = {sux, suy, sT}, bar = {ux, uy, T};
+    stream_node_base(&S, M, x, y, sel, base, 0, P, G);   /* chooses the stencils */
+    stream_node_base(&S, M, x, y, bar, base, 1, P, G);
     free(M);
     return 0;
 }
@@ -722,10 +787,11 @@ static int step_node(const or_src *S, or_memo *M, int x, int y, double div, doub
     or_frame bar = {S->fux[n], S->fuy[n], S->fT[n]};        /* predictor: previous frame */
     or_moments m;
     int k = 0, stop = 0;
+    int base[2 * OR_MAXQ];                     /* stencils of the first iteration, kept */
     *badnode = 0;
     *nonconv = 0;
     while (!stop) {
-        stream_node(S, M, x, y, bar, P, G);
+        stream_node_base(S, M, x, y, bar, base, k > 0, P, G);
         m = moments_of_div(L, P, G, 1, bar, cfg->split, cv, div);
         ++k;
         if (nonphysical(m)) { *badnode = 1; break; }

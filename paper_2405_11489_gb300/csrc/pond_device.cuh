@@ -187,6 +187,53 @@ __device__ __forceinline__ int lagrange(R off, R* w)
     }
 }
 
+// Weights of the P-point stencil whose first tap is at offset base (as lagrange returned it for
+// an earlier departure offset) at departure offset off: the same Lagrange polynomials, with
+// t = off - (base + 1) possibly outside the range that lagrange would give.  The
+// predictor-corrector keeps the stencils of its first iteration and moves only their weights.
+template <class R, int P>
+__device__ __forceinline__ void lagrange_at(R off, int base, R* w)
+{
+    const R t = off - R(base + 1);
+    if constexpr (P == 4) {
+        R tm1 = t - R(1), tm2 = t - R(2), tp1 = t + R(1);
+        w[0] = -t * tm1 * tm2 * R(1.0 / 6.0);
+        w[1] = tp1 * tm1 * tm2 * R(0.5);
+        w[2] = -tp1 * t * tm2 * R(0.5);
+        w[3] = tp1 * t * tm1 * R(1.0 / 6.0);
+    } else {
+        w[0] = t * (t - R(1)) * R(0.5);
+        w[1] = (R(1) - t) * (R(1) + t);
+        w[2] = t * (t + R(1)) * R(0.5);
+    }
+}
+
+// Whether the P-point stencil whose first tap is at offset base still serves departure offset
+// off: t = off - (base + 1) lies in the range the stencil was chosen for ([0, 1) for 4 taps,
+// [-1/2, 1/2) for 3) widened by a quarter cell on each side.
+template <class R, int P>
+__device__ __forceinline__ bool stencil_holds(R off, int base)
+{
+    const R t = off - R(base + 1);
+    return P == 4 ? (t >= R(-0.25) && t < R(1.25)) : (t >= R(-0.75) && t < R(0.75));
+}
+
+// v[a] for a runtime a < N, and v[a] = x, without indexing a register array dynamically.
+template <int N>
+__device__ __forceinline__ int sel_get(const int (&v)[N], int a)
+{
+    int r = v[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k) r = (a == k) ? v[k] : r;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ void sel_set(int (&v)[N], int a, int x)
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = (a == k) ? x : v[k];
+}
+
 // Boundary maps: 0 periodic (index mod n), 1 outflow (clamp to the edge node); positions
 // beyond a wall (2) map to the edge node here and are replaced by the wall's ghost state by
 // the callers that stream from them.

@@ -9,7 +9,9 @@ from the oracle (no shared code) and follows the paper with the same readings:
   p + q <= N, and the target populations w_i sum_{p+q<=N} A_pq He_p(c_ix) He_q(c_iy) / (p! q!);
 - streaming (Eq. propagationInterpolated): cubic Lagrange interpolation at the departure
   point x - C_i(lambda_bar) of every stencil node's populations moved into lambda_bar;
-- predictor-corrector: guess = previous frame, exactly K iterations;
+- predictor-corrector: guess = previous frame, exactly K iterations, the stencil nodes of
+  each population carried from one iteration to the next (their weights following the frame)
+  while the departure point stays within a quarter cell of the range they were chosen for;
 - collision: project into the frame of the final moments, BGK with omega = 1/(tau + 1/2),
   tau = mu/(rho T), f_eq = rho w_i, g_eq of the total, internal or non-translational split
   (Sec. II; the last with E = sum g + sum |C|^2/2 f);
@@ -77,12 +79,18 @@ def population(lat, A, i):
     return lat.w[i] * s
 
 
-def cubic(xd):
-    b = mp.floor(xd)
-    t = xd - b
-    w = [-t * (t - 1) * (t - 2) / 6, (t + 1) * (t - 1) * (t - 2) / 2,
-         -(t + 1) * t * (t - 2) / 2, (t + 1) * t * (t - 1) / 6]
-    return int(b) - 1, w
+def cubic_weights(t):
+    return [-t * (t - 1) * (t - 2) / 6, (t + 1) * (t - 1) * (t - 2) / 2,
+            -(t + 1) * t * (t - 2) / 2, (t + 1) * t * (t - 1) / 6]
+
+
+def cubic(xd, first=None):
+    """First node and weights of the 4-point stencil at departure point xd; with first given,
+    the weights of that stencil (nodes first .. first + 3) at xd if xd lies within a quarter
+    cell of the range it was chosen for, else the stencil xd selects."""
+    if first is None or not (-mp.mpf(1) / 4 <= xd - (first + 1) < mp.mpf(5) / 4):
+        first = int(mp.floor(xd)) - 1
+    return first, cubic_weights(xd - (first + 1))
 
 
 def g_eq(lat, i, split, rho, fr, cv):
@@ -132,14 +140,18 @@ def init(lat, nx, ny, rho, ux, uy, T, split, gamma):
     return st
 
 
-def stream(lat, st, nx, ny, x, y, bar):
-    """Populations f, g streamed to node (x, y) on the lattice of frame bar."""
+def stream(lat, st, nx, ny, x, y, bar, stencils=None):
+    """Populations f, g streamed to node (x, y) on the lattice of frame bar.  stencils: a
+    dict population -> (first x node, first y node), carried between calls (see cubic)."""
     cache = {}
     sT = mp.sqrt(bar[2])
     P, G = [], []
     for i in range(lat.Q):
-        bx, wx = cubic(x - (sT * lat.cx[i] + bar[0]))
-        by, wy = cubic(y - (sT * lat.cy[i] + bar[1]))
+        keep = stencils.get(i) if stencils is not None else None
+        bx, wx = cubic(x - (sT * lat.cx[i] + bar[0]), keep[0] if keep else None)
+        by, wy = cubic(y - (sT * lat.cy[i] + bar[1]), keep[1] if keep else None)
+        if stencils is not None:
+            stencils[i] = (bx, by)
         fi = gi = mp.mpf(0)
         for ky in range(4):
             for kx in range(4):
@@ -185,8 +197,9 @@ def step(lat, st, nx, ny, split, gamma, mu, K):
     for y in range(ny):
         for x in range(nx):
             bar = st["fr"][y * nx + x]
+            stencils = {}
             for k in range(K):
-                P, G = stream(lat, st, nx, ny, x, y, bar)
+                P, G = stream(lat, st, nx, ny, x, y, bar, stencils)
                 m = moments(lat, P, G, bar, split, cv, div[y * nx + x] if div else 0)
                 if k < K - 1:
                     bar = (m[1], m[2], m[3])

@@ -51,6 +51,41 @@ def _l1(a, b, scale):
 BOUNDS = {"fp32": (5e-8, 1e-7), "fp16": (2e-6, 2e-5), "bf16": (2e-5, 2e-4)}
 
 
+# Errors relative to the physical signal of the 256^2 decay configuration after 200 steps
+# (mean |mixed - FP64| over the mean |FP64 - its own mean|): the shear wave's u_y and the
+# thermal pulse's T and rho.  Measured on one GB300: u_y 4.7e-7 / 1.9e-6 / 2.0e-5, T 1.9e-5 /
+# 7.0e-4 / 5.1e-3, rho 2.9e-5 / 7.4e-4 / 5.5e-3 (FP32 / FP16 / BF16 storage).  The pulse
+# also induces a second-order u_x perturbation that the reduced storages do not resolve
+# (error 1.3 times that perturbation with BF16, 0.19 with FP16, 0.011 with FP32 storage);
+# it is not bounded here.
+SIGNAL_BOUNDS = {"fp32": {"uy": 2e-6, "T": 1e-4, "rho": 1e-4},
+                 "fp16": {"uy": 1e-5, "T": 3e-3, "rho": 3e-3},
+                 "bf16": {"uy": 1e-4, "T": 2e-2, "rho": 2e-2}}
+
+
+def test_reduced_storage_errors_against_the_signal(pond):
+    """The decay configuration's perturbations (shear wave u_y, thermal pulse T and rho) in
+    the mixed modes stay within stated bounds relative to their own size, against the FP64
+    path, after 200 steps."""
+    sh = W.shear_wave(n=256, ma=1.0, amp=0.05, mu=0.05)
+    pu = W.thermal_pulse(n=256, amp=1e-3, width=16.0, mu=0.05, ma=1.0)
+    res = {}
+    for prec in ("fp64", "fp32", "fp16", "bf16"):
+        s = pond.Simulation(pond.Config(nx=256, ny=256, precision=prec, gamma=1.4, mu=0.05))
+        s.set_state(pu.rho, sh.ux, sh.uy, pu.T)
+        s.step(200)
+        res[prec] = dict(zip(("rho", "ux", "uy", "T"), s.moments()))
+        s.close()
+    ref = res["fp64"]
+    for prec in ("fp32", "fp16", "bf16"):
+        errs = {}
+        for k in ("uy", "T", "rho"):
+            signal = np.mean(np.abs(ref[k] - ref[k].mean()))
+            errs[k] = float(np.mean(np.abs(res[prec][k] - ref[k])) / signal)
+        print(prec, errs)
+        assert all(errs[k] <= SIGNAL_BOUNDS[prec][k] for k in errs), (prec, errs)
+
+
 MIXED_CASES = [(prec, 16, split) for prec in ("fp32", "fp16", "bf16")
                for split in ("total", "internal", "nt")] + \
               [("fp32", 25, "total"), ("fp32", 25, "nt"), ("bf16", 25, "nt")]
