@@ -17,9 +17,9 @@
  * characteristics by the trapezoidal rule: the stored g is the post-collision g carried as
  * g - (Omega + G)/2, a node's internal energy is U = sum g + (1/2) sum G = sum g -
  * (1/2) rho T div u with div u at the new time level from a predictor pass (each node's f
- * streamed once in its previous frame), and the collision adds (1 - omega/2) G; a step of
- * that split is three launches (predictor, step, source).  Its reported temperature is the
- * frame's.
+ * streamed once in its previous frame; the step takes its first predictor-corrector iteration
+ * from that pass), and the collision adds (1 - omega/2) G; a step of that split is three
+ * launches (predictor, step, source).  Its reported temperature is the frame's.
  *
  * Units: lattice units (Sec. III), r = 1, dx = dt = 1, T_L = 1.
  *
@@ -124,8 +124,9 @@ int pond_config_default(pond_config *cfg, int32_t nx, int32_t ny);
 
 /* Bytes of device workspace a simulation with this configuration needs (two copies of the
  * state, see pond_state_bytes, a status block, the prescribed sides' profiles and, for the
- * internal-energy split, its predictor velocities, 16 bytes per node).  For admission by
- * free HBM. */
+ * internal-energy split, its predictor pass's velocities and streamed coefficients: 96 bytes
+ * per node in the mixed modes and 176 in FP64 on D2Q16, 136 and 256 on D2Q25).  For admission
+ * by free HBM. */
 int pond_workspace_bytes(const pond_config *cfg, size_t *bytes);
 
 /* Create a simulation on the current device.  dev_workspace: caller-owned device memory
@@ -309,8 +310,8 @@ void pond_autotune_clear(void);
  *    align256(P*s*N) + 256 with N = nx*ny, P = 19 (D2Q16) or 29 (D2Q25) and s = 8/4/2/2
  *    bytes (FP64/FP32/FP16/BF16), i.e. N <= 91 178 / 63 548 (FP64), 155 341 / 113 357
  *    (FP32), 239 669 / 186 408 (FP16/BF16) on D2Q16 / D2Q25; the internal-energy split adds
- *    align256(16*N) for its predictor velocities.  Larger grids return POND_ENOMEM without
- *    touching the GPU.
+ *    align256 of its predictor region (96 / 176 bytes per node on D2Q16 in the mixed / FP64
+ *    modes, 136 / 256 on D2Q25).  Larger grids return POND_ENOMEM without touching the GPU.
  *  - Set-up: the first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) and the SM count, and the first call for each kernel variant
  *    (precision, lattice, 1-D or 2-D, interpolation order, launch shape) sets the step

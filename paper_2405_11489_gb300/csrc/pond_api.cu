@@ -70,7 +70,7 @@ Lattice make_lattice(int q1)
 
 struct Layout {
     size_t mac[2], neq[2], status, prof[4], total;   // prof[side] = 0: the side takes no profile
-    size_t upred;                                    // internal split: [2][N] predictor velocities; else 0
+    size_t upred;                                    // internal split: predictor region (upred_bytes); else 0
 };
 
 // Grad order of a configuration: the lattice's (3 on D2Q16, 4 on D2Q25).
@@ -86,6 +86,16 @@ bool side_prescribed(const pond_config& c, int w)
 
 // Positions along side w: ny for the x sides, nx for the y sides.
 int side_length(const pond_config& c, int w) { return w < 2 ? c.ny : c.nx; }
+
+// Bytes of the internal split's predictor region: the predictor velocities, [2][N] doubles,
+// followed by the coefficients of the populations it streamed, [2 ncoef][N] values of the
+// arithmetic type (double in the FP64 mode, float otherwise).
+size_t upred_bytes(const pond_config& c)
+{
+    const size_t N = (size_t)c.nx * (size_t)c.ny;
+    const size_t nc = (size_t)ncoef(grad_order(c));
+    return 2 * N * sizeof(double) + 2 * nc * N * (c.precision == POND_FP64 ? sizeof(double) : sizeof(float));
+}
 
 Layout layout_of(const pond_config& c)
 {
@@ -106,7 +116,7 @@ Layout layout_of(const pond_config& c)
     l.upred = 0;
     if (c.split == POND_SPLIT_INTERNAL) {
         l.upred = off;
-        off = align_up(off + 2 * N * sizeof(double));
+        off = align_up(off + upred_bytes(c));
     }
     l.total = off;
     return l;
@@ -1558,8 +1568,7 @@ extern "C" int pond_step_static(const pond_config* cfg, double* mac, void* neq, 
     const size_t off_neq = align_up(mb), off_status = off_neq + align_up(nb);
     // internal split: the predictor velocities follow the status block
     const size_t off_upred = off_status + align_up(sizeof(DevStatus));
-    const size_t need = off_upred + (cfg->split == POND_SPLIT_INTERNAL
-                                         ? align_up(2 * (size_t)cfg->nx * cfg->ny * sizeof(double)) : 0);
+    const size_t need = off_upred + (cfg->split == POND_SPLIT_INTERNAL ? align_up(upred_bytes(*cfg)) : 0);
     if (need > (size_t)POND_STATIC_SCRATCH_BYTES) return POND_ENOMEM;
 
     int dev = 0;

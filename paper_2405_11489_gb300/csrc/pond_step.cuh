@@ -55,7 +55,9 @@ struct CaseDesc {
     DevStatus* status;
     double wall[4][4];          // prescribed sides x-low, x-high, y-low, y-high: (u_x, u_y, T, rho)
     const double* prof[4];      // per side: null (uniform wall[side]) or [n][4] states along it
-    double* upred;              // internal split: [2][N] predictor velocities (u_x, u_y); else null
+    double* upred;              // internal split: [2][N] predictor velocities (u_x, u_y), followed by the
+                                // [2 ncoef][N] coefficients (arithmetic type) of its streamed f and g;
+                                // else null
 };
 
 struct StepParams {
@@ -256,15 +258,16 @@ __device__ __forceinline__ void add_g_eq_dev(int split, const BaseFrame<R>& bf, 
 
 // Deviation of a source's coefficients, moved into the reference frame, from the reference
 // node's equilibrium coefficients (f into Df, g into Dg; ncoef(N) values each).  The source is
-// node nd (neq = its non-equilibrium planes) or, with neq = nullptr, the equilibrium at the
+// the node whose non-equilibrium coefficient m is neq[m * stride + nd] (its planes in global
+// memory, or values already loaded: stride 1) or, with neq = nullptr, the equilibrium at the
 // primitive state (rho, ux, uy, T).
 template <class S, class R, int N>
 __device__ __forceinline__ void source_dev_state(const CaseRun& p, const RefState<R>& rf, double rho,
                                                  double ux, double uy, double T, const S* neq,
-                                                 long long nd, R* Df, R* Dg)
+                                                 long long nd, long long stride, R* Df, R* Dg)
 {
     constexpr int NC = ncoef(N);
-    const long long Nn = p.N;
+    const long long Nn = stride;
     // differences of the primitive variables from the reference: FP64 in the FP64 mode, from
     // float pairs (integer splitting, no FP64 operation) in the mixed modes
     R drho, dux, duy, dT;
@@ -333,7 +336,48 @@ __device__ __forceinline__ void source_dev(const CaseRun& p, const RefState<R>& 
 {
     const long long Nn = p.N;
     source_dev_state<S, R, N>(p, rf, p.mac_in[nd], p.mac_in[Nn + nd], p.mac_in[2 * Nn + nd],
-                              p.mac_in[3 * Nn + nd], reinterpret_cast<const S*>(p.neq_in), nd, Df, Dg);
+                              p.mac_in[3 * Nn + nd], reinterpret_cast<const S*>(p.neq_in), nd, Nn, Df, Dg);
+}
+
+// A staged source's inputs, read from global memory before any of its arithmetic so that the
+// loads of several sources are in flight together.
+template <class S, int N>
+struct SourceLoad {
+    double rho, ux, uy, T;
+    S neq[nneq(N)];
+    bool ghost;                 // beyond a prescribed side: the equilibrium at (rho, u, T)
+};
+
+template <class S, int N>
+__device__ __forceinline__ void load_source(const CaseRun& p, int gx, int gy, SourceLoad<S, N>& L)
+{
+    const int w = wall_of(p.bc_x, p.bc_y, p.nx, p.ny, gx, gy);
+    L.ghost = w >= 0;
+    if (L.ghost) {
+        const double* st = side_state(p.wall, p.prof, p.nx, p.ny, w, gx, gy);
+        L.rho = st[3];
+        L.ux = st[0];
+        L.uy = st[1];
+        L.T = st[2];
+        return;
+    }
+    const long long Nn = p.N;
+    const long long nd = (long long)bc_map(gy, p.ny, p.bc_y) * p.nx + bc_map(gx, p.nx, p.bc_x);
+    L.rho = p.mac_in[nd];
+    L.ux = p.mac_in[Nn + nd];
+    L.uy = p.mac_in[2 * Nn + nd];
+    L.T = p.mac_in[3 * Nn + nd];
+    const S* q = reinterpret_cast<const S*>(p.neq_in);
+#pragma unroll
+    for (int m = 0; m < nneq(N); ++m) L.neq[m] = q[(long long)m * Nn + nd];
+}
+
+template <class S, class R, int N>
+__device__ __forceinline__ void source_from_load(const CaseRun& p, const RefState<R>& rf, const SourceLoad<S, N>& L,
+                                                 R* Df, R* Dg)
+{
+    source_dev_state<S, R, N>(p, rf, L.rho, L.ux, L.uy, L.T, L.ghost ? static_cast<const S*>(nullptr) : L.neq, 0,
+                              1, Df, Dg);
 }
 
 // The source at position (gx, gy): the node the boundary maps it to, or a prescribed side's
@@ -345,7 +389,7 @@ __device__ __forceinline__ void source_at(const CaseRun& p, const RefState<R>& r
     const int w = wall_of(p.bc_x, p.bc_y, p.nx, p.ny, gx, gy);
     if (w >= 0) {
         const double* st = side_state(p.wall, p.prof, p.nx, p.ny, w, gx, gy);
-        source_dev_state<S, R, N>(p, rf, st[3], st[0], st[1], st[2], static_cast<const S*>(nullptr), 0,
+        source_dev_state<S, R, N>(p, rf, st[3], st[0], st[1], st[2], static_cast<const S*>(nullptr), 0, 1,
                                   Df, Dg);
     } else {
         const int sx = bc_map(gx, p.nx, p.bc_x), sy = bc_map(gy, p.ny, p.bc_y);
@@ -863,9 +907,10 @@ __device__ __forceinline__ double predictor_divergence(const CaseRun& p, int x, 
 
 // One thread per node, one CTA per tile of TPB nodes; CTAs resident per SM as
 // step_blocks_per_sm says (the quasi-1-D D2Q16 kernel with FP32 arithmetic is held to three per
-// SM).  PRED: the internal split's predictor pass instead of a step: each node streams f once in
-// its previous frame and writes the velocity of the result to upred (other splits' blocks return
-// at once; nothing else is written).
+// SM).  PRED: the internal split's predictor pass instead of a step: each node streams f and g
+// once in its previous frame and writes the velocity of f's result and the streamed
+// coefficients to upred, where the step takes its first iteration from (other splits' blocks
+// return at once; nothing else is written).
 template <class S, class R, int Q1, int P, bool ONE_D, int TPB, bool PRED>
 __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::is_same<R, double>::value))
     step_kernel(const StepParams pp)
@@ -925,13 +970,29 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
     const int bn = bw * bh;
 
     // ---- staging: source deviations in the reference frame --------------------------------
-    // Node-interleaved layout: node i holds its 20 values (f: 0..9, g: 10..19) contiguously,
-    // so each tap of one distribution is three vector loads.
-    for (int i = tid; i < bn; i += TPB) {
-        int lx = i % bw, ly = i / bw;
-        R D[2 * NC];
-        source_at<S, R, NG>(p, rf, ox + lx, ONE_D ? 0 : oy + ly, D, D + NC);
-        store_rec<R, NG>(sm + (size_t)i * REC, D, D + NC);
+    // Node-interleaved records (rec_len floats per box node).  Each thread reads the inputs of
+    // SB box nodes before working on any of them, so that their global loads are in flight
+    // together (the phase is bound by their latency).
+    {
+        // (quasi-1-D boxes hold about one node per thread: nothing to batch)
+        constexpr int SB = ONE_D ? 1 : ((sizeof(S) <= 4 && NG == 3) ? 4 : 2);
+        for (int i0 = tid; i0 < bn; i0 += SB * TPB) {
+            SourceLoad<S, NG> L[SB];
+#pragma unroll
+            for (int u = 0; u < SB; ++u) {
+                const int i = i0 + u * TPB;
+                if (i < bn) load_source<S, NG>(p, ox + i % bw, ONE_D ? 0 : oy + i / bw, L[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < SB; ++u) {
+                const int i = i0 + u * TPB;
+                if (i < bn) {
+                    R D[2 * NC];
+                    source_from_load<S, R, NG>(p, rf, L[u], D, D + NC);
+                    store_rec<R, NG>(sm + (size_t)i * REC, D, D + NC);
+                }
+            }
+        }
     }
     __syncthreads();
     if (pp.ahead > 0) prefetch_next_wave<S, NG, ONE_D>(pp, TX, TY, tid, TPB);
@@ -989,7 +1050,24 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
 #pragma unroll
             for (int m = 0; m < NC; ++m) { Af[m] = R(0); Ag[m] = R(0); }
 
-            if constexpr (!ONE_D) {
+            // internal split: the first iteration streams in the previous frame through the
+            // same staged box and stencils as the predictor pass did, so its coefficients are
+            // the predictor's (kept in the predictor buffer); only the stencil choice is redone
+            const bool from_predictor = !PRED && k == 0 && p.split == 1;
+            if (from_predictor) {
+                const R* first = reinterpret_cast<const R*>(p.upred + 2 * N);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    Af[m] = first[(long long)m * N + node];
+                    Ag[m] = first[(long long)(NC + m) * N + node];
+                }
+#pragma unroll
+                for (int c = 0; c < Q1; ++c) {
+                    R w[P];
+                    if constexpr (!ONE_D) jy[c] = lagrange<R, P>(-(sT * lat[c].c + ubyr), w);
+                    jxk[c] = lagrange<R, P>(-(sT * lat[c].c + ubxr), w);
+                }
+            } else if constexpr (!ONE_D) {
                 // y stencils of all b (shared by every a and both distributions)
                 R wy[Q1][P];
                 int rmin = 1 << 30, rmax = -(1 << 30);
@@ -1126,9 +1204,9 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                             Ag[slot(pq, q)] += la.he[pq] * Sg[q];
                         }
                   } else {
-                    // one pass per distribution (FP64; D2Q25); the predictor streams f only
+                    // one pass per distribution (FP64; D2Q25)
                     constexpr int ND = 1;
-                    constexpr int NDIST = PRED ? 1 : 2;
+                    constexpr int NDIST = 2;
                     // one pass each (ND = 1) share their code: unrolled, the two passes kept
                     // both sets of row temporaries live and spilled on D2Q25 (702 -> 534 us)
 #pragma unroll 1
@@ -1397,6 +1475,12 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
         if (active) {
             p.upred[node] = ux0 + (double)dubx;                       // u of f streamed once
             p.upred[N + node] = uy0 + (double)duby;
+            R* first = reinterpret_cast<R*>(p.upred + 2 * N);        // the step's first iteration
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                first[(long long)m * N + node] = Af[m];
+                first[(long long)(NC + m) * N + node] = Ag[m];
+            }
         }
         return;
     }
