@@ -194,12 +194,15 @@ def test_fp64_sod_400x4_matches_oracle(pond, orc):
                                       bc_x=c.bc_x, bc_y=c.bc_y, pc_fixed_iters=3))
     sim.set_state(c.rho, c.ux, c.uy, c.T)
     done = 0
-    for upto in (50, 100, 200, c.steps):         # the error after each stretch, printed
+    for upto in (50, 100, 200, c.steps):
         for _ in range(upto - done):
             st = orc.step(ocfg, st).state
         sim.step(upto - done)
         done = upto
-        errs = compare(orc, ocfg, sim, st, 1e-11, "sod")
+        # rounding differences accumulate about linearly (measured on one GB300: 6.1e-14,
+        # 2.0e-13, 5.6e-13, 1.8e-12 after 50, 100, 200, 400 steps, about 4.4e-15 per step);
+        # the bound is 1e-12 for the first 160 steps and 6.25e-15 per step beyond
+        errs = compare(orc, ocfg, sim, st, max(FP64_TOL, 6.25e-15 * done), "sod")
         print("sod fp64 step %d: max rel err %.2e %s" % (done, max(errs.values()), errs))
     sim.close()
 

@@ -15,8 +15,8 @@ deviations of 1.2 sound speeds instead of a few per cent) the bounds are four ti
 ones above (FP32 2e-7, BF16 8e-5 for every field); at the jet's full configuration, where a
 tile can straddle the jet (rho, T) = (5, 0.005) and the ambient (50, 0.0005), a contrast of
 10 in both rho and T scales the rounding relative to a node's own values by up to 100:
-sampled moments within 5e-5 relative, populations within 2e-4 of their scale (25 and 10
-times the decay configuration's).
+sampled moments within 1e-5 relative, populations within 5e-5 of their scale (measured:
+T 5.1e-6, populations 1.6e-5).
 
 Full sizes (256 x 256 decay configuration, 1024 x 1024 four-quadrant Riemann problem with the
 3-point interpolation of Sec. III.A.2, in the launch configuration the benchmark uses): after a few GPU steps the state is exported as
@@ -196,6 +196,7 @@ def _sampled_step(pond, orc, case, precision, split, warm, tol_m, tol_f, seed, o
     if split == "total":
         errs["g"] = np.max(np.abs(gg[:, ys, xs] - og)) / np.max(np.abs(og))
     sim.close()
+    print("sampled %s %s %s" % (case.name if hasattr(case, "name") else "", precision, errs))
     bad = {k: v for k, v in errs.items() if not v <= (tol_f if k in ("f", "g") else tol_m)}
     assert not bad, errs
 
@@ -281,12 +282,16 @@ def test_tube_batch_256_sampled_parity(pond, orc):
         xs, ys = _sample_nodes(c.nx, c.ny, rng)
         of, og, (oux, ouy, oT), oit = orc.step_nodes(ocfg, orc.State(*before[i]), xs, ys)
         ok = oit < 20                                   # converged within the GPU's cap
-        assert ok.sum() >= 0.8 * len(xs), (i, c.nx, int(ok.sum()), len(xs))
+        print("tube %d (%d cells): %d of %d sampled nodes converge within the cap" % (i, c.nx, int(ok.sum()), len(xs)))
+        # with the stencils carried between iterations every sampled node converges (measured:
+        # 192 of 192 over the four tubes); before, up to a fifth of them cycled at the shocks
+        assert ok.all(), (i, c.nx, int(ok.sum()), len(xs))
         xs, ys, of, og, oux, oT = xs[ok], ys[ok], of[:, ok], og[:, ok], oux[ok], oT[ok]
         speed = max(np.abs(oux).max(), math.sqrt(oT.max()))
         errs = {"T": np.max(np.abs(gT[ys, xs] - oT) / oT), "ux": np.max(np.abs(gux[ys, xs] - oux)) / speed,
                 "f": np.max(np.abs(gf[:, ys, xs] - of)) / np.max(np.abs(of)),
                 "g": np.max(np.abs(gg[:, ys, xs] - og)) / np.max(np.abs(og))}
+        print("tube %d errors %s" % (i, errs))
         assert errs["T"] <= 5e-6 and errs["ux"] <= 5e-6 and errs["f"] <= 5e-5 and errs["g"] <= 5e-5, (i, c.nx, errs)
     batch.close()
     for s in sims:
@@ -314,7 +319,8 @@ def test_jet_2000x1000_sampled_parity(pond, orc):
     """The jet configuration of Sec. III.C at its resolution (2000 x 1000, D = 100, the paper's
     jet and ambient states, profiled x-low inflow) at Mach 1.5, in mixed FP32."""
     case = W.jet(ma=1.5)
-    _sampled_step(pond, orc, case, "fp32", "total", 3, 5e-5, 2e-4, seed=4)
+    # measured on one GB300: T 5.1e-6, u 1.2e-7, f 6.3e-6, g 1.6e-5 (moments / populations)
+    _sampled_step(pond, orc, case, "fp32", "total", 3, 1e-5, 5e-5, seed=4)
 
 
 # Moments handed to the caller from populations far from their frame's equilibrium: the
