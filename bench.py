@@ -120,41 +120,72 @@ def whole_job_mlups(world, nodes_per_step, step_ms):
 
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+    """nvidia-smi samples (clocks and throttle reasons) taken while the timed kernels run.
+
+    Sampling is live before the region starts (the first sample is awaited), every sample is
+    stamped on arrival, and the summary keeps the samples between the region's start and end
+    plus the first one after the end, which reports the state at the region's close (a region
+    of a few milliseconds holds no sample of its own)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.stamped = []             # (monotonic seconds at arrival, csv line)
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.stamped.append((time.monotonic(), line))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+        if self.proc is not None:
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+            deadline = time.monotonic() + 5.0
+            while not self.stamped and time.monotonic() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
+        self.t0 = time.monotonic()
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+        self.t1 = time.monotonic()
+        if self.proc is None:
+            return
+        deadline = self.t1 + 4.0 * self.INTERVAL_MS * 1e-3
+        while time.monotonic() < deadline and not any(t > self.t1 for t, _ in self.stamped):
+            time.sleep(0.01)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            self.proc.wait()
+        self.reader.join(timeout=5)
+
+    def region_lines(self):
+        inside = [l for t, l in self.stamped if self.t0 <= t <= self.t1]
+        after = [l for t, l in self.stamped if t > self.t1][:1]
+        return inside + after
 
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+        lines = self.region_lines() if self.t0 is not None and self.t1 is not None else []
+        for l in lines:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -169,7 +200,8 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "interval_ms": self.INTERVAL_MS,
+                "region_ms": round(1e3 * (self.t1 - self.t0), 1)}
 
 
 def l2_flusher(torch, device):
@@ -197,12 +229,14 @@ def make_sims(pond, precision, device, stream, tune=False):
     return (sims, batch, tuning) if tune else (sims, batch)
 
 
-def time_steps(torch, batch, stream, steps, warmup, flush):
+def time_steps(torch, batch, stream, steps, warmup, flush, clock=None):
     """CUDA-event time of every batched step (one launch over all grids), L2 flushed before
-    each timed step."""
+    each timed step; a clock sampler's region starts after the warm-up steps."""
     for _ in range(warmup):
         batch.step(1)
     torch.cuda.synchronize()
+    if clock is not None:
+        clock.t0 = time.monotonic()
     starts, ends = [], []
     torch.cuda.nvtx.range_push("timed_steps")       # lets a profiler select the timed launches
     for _ in range(steps):
@@ -688,7 +722,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        per_launch = time_steps(torch, batch, stream, args.steps, args.warmup, flush)
+        per_launch = time_steps(torch, batch, stream, args.steps, args.warmup, flush, clock=clk)
     step_ms = max_over_ranks(sum(per_launch) / args.steps, world, device)
     K = mean_iters(sims)
     batch.close()

@@ -71,3 +71,28 @@ def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
     src.write_bytes(src.read_bytes() + b" ")
     assert bench.profiled_traffic(key) is None
     assert bench.profiled_traffic("no_such_kernel") is None
+
+
+def test_clock_summary_keeps_the_timed_region():
+    """Samples before the region (warm-up, autotuning) are dropped; the region's own samples
+    and the first one after its end are kept, and throttle reasons among them are reported."""
+    clk = bench.ClockSampler(0)
+
+    def line(mhz, thermal="Not Active", power="Not Active"):
+        return "0, %d, 2070, 900.0, 0x0, Not Active, Not Active, %s, %s" % (mhz, thermal, power)
+
+    clk.stamped = [(0.00, line(1200, thermal="Active")),   # before the region
+                   (0.10, line(2070)), (0.15, line(2060, power="Active")),
+                   (0.30, line(2050)),                        # first after the end
+                   (0.40, line(900))]                         # later: ignored
+    clk.t0, clk.t1 = 0.05, 0.20
+    c = clk.summary()
+    assert c["samples"] == 3 and c["sm_mhz"] == 2060.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    # a region shorter than the sampling interval keeps the sample that closes it
+    clk.t0, clk.t1 = 0.16, 0.18
+    c = clk.summary()
+    assert c["samples"] == 1 and c["sm_mhz"] == 2050.0
+    # nothing sampled at all
+    clk.stamped = []
+    assert bench.ClockSampler.summary(clk)["reasons"] == ["unsampled"]
