@@ -604,13 +604,23 @@ __device__ __forceinline__ R pick(const R* w, int j, int n)
     return v;
 }
 
-// Bytes of dynamic shared memory of the step kernel: the staged box, one record per node.
+// Rows of the per-thread table of y-stencil weights of the FP32 D2Q16 2-D kernels: the weights
+// of the four y stencils at each row of the warp's row range, so that the row loop reads the
+// four weights of a row with one 16-byte load instead of selecting them (a warp whose range
+// is longer streams through global gathers).
+constexpr int kWtRows = 16;
+__host__ __device__ constexpr bool weight_table(int rbytes, int q1, bool one_d)
+{
+    return rbytes == 4 && q1 == 4 && !one_d;
+}
+
+// Bytes of dynamic shared memory of the step kernel: the staged box, one record per node,
+// then the weight table (kWtRows float4 per thread) where the kernel keeps one.
 __host__ __device__ constexpr size_t step_smem_bytes(int rbytes, int q1, bool one_d, int box_w,
                                                      int box_h, int nodes)
 {
-    return (void)one_d, (void)nodes,
-           (size_t)box_w * box_h * rbytes *
-               (q1 == 5 ? (rbytes == 4 ? 36 : 30) : 20);
+    return (size_t)box_w * box_h * rbytes * (q1 == 5 ? (rbytes == 4 ? 36 : 30) : 20) +
+           (weight_table(rbytes, q1, one_d) ? (size_t)kWtRows * nodes * 16 : 0);
 }
 
 template <class R>
@@ -1080,6 +1090,29 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                     rmax = max(rmax, jy[b] + P - 1);
                 }
                 const bool rows_in = (y + rmin - oy >= 0) && (y + rmax - oy < bh);
+                // FP32, N = 3: the warp's lanes whose y stencils lie in the box stream the union
+                // of their rows [r_lo, r_hi] in one order; each lane's weights of the four y
+                // stencils at every row of that range (0 outside its stencils) go into its
+                // column of the weight table, once per iteration for all a
+                int r_lo = 0, r_hi = -1;
+                bool tab_ok = false;
+                if constexpr (pair_records<R, NG>()) {
+                    const unsigned rmask = __ballot_sync(__activemask(), rows_in);
+                    if (rows_in) {
+                        r_lo = __reduce_min_sync(rmask, y + rmin);
+                        r_hi = __reduce_max_sync(rmask, y + rmax);
+                        tab_ok = r_hi - r_lo < kWtRows;
+                        if (tab_ok) {
+                            float4* const wt = reinterpret_cast<float4*>(sm + (size_t)pp.box_w * pp.box_h * REC) + tid;
+                            for (int i = 0; i <= r_hi - r_lo; ++i) wt[i * TPB] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                            for (int b = 0; b < Q1; ++b)
+#pragma unroll
+                                for (int j = 0; j < P; ++j)
+                                    reinterpret_cast<float*>(wt + (y + jy[b] + j - r_lo) * TPB)[b] = wy[b][j];
+                        }
+                    }
+                }
 #pragma unroll 1
                 for (int a = 0; a < Q1; ++a) {
                     const LatRow<R>& la = lat[a];
@@ -1111,19 +1144,17 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                     for (int b = 0; b < Q1; ++b)
 #pragma unroll
                         for (int q = 0; q <= NG; ++q) acc[b][q] = make_float2(0.f, 0.f);
-                    const bool inbox = rows_in && cols_in;
-                    const unsigned bmask = __ballot_sync(__activemask(), inbox);
+                    const bool inbox = rows_in && cols_in && tab_ok;
                     if (inbox) {
-                        const int r_lo = __reduce_min_sync(bmask, y + rmin);
-                        const int r_hi = __reduce_max_sync(bmask, y + rmax);
                         float2 w2x[P];
 #pragma unroll
                         for (int ii = 0; ii < P; ++ii) w2x[ii] = make_float2(wx[ii], wx[ii]);
                         const float* rowp = sm + ((size_t)(r_lo - oy) * bw + tx0) * REC;
+                        const float4* wtp = reinterpret_cast<const float4*>(sm + (size_t)pp.box_w * pp.box_h * REC) + tid;
                         // three rows per trip on 4-point stencils (one or two were 1-3 % slower)
                         constexpr int kRowUnroll = P == 4 ? 3 : 1;
 #pragma unroll kRowUnroll
-                        for (int r = r_lo; r <= r_hi; ++r, rowp += (size_t)bw * REC) {
+                        for (int r = r_lo; r <= r_hi; ++r, rowp += (size_t)bw * REC, wtp += TPB) {
                             float2 X[NC];
 #pragma unroll
                             for (int ii = 0; ii < P; ++ii) {
@@ -1143,23 +1174,26 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                             }
                             float2 Z[NG + 1];
                             z_contract_pairs<NG>(phi, X, Z);
+                            const float4 w4 = *wtp;
+                            const float wb[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                             for (int b = 0; b < Q1; ++b) {
-                                const int j = r - y - jy[b];
-                                const float w = ((unsigned)j < (unsigned)P) ? pick<float>(wy[b], j, P) : 0.f;
-                                const float2 w2 = make_float2(w, w);
+                                const float2 w2 = make_float2(wb[b], wb[b]);
 #pragma unroll
                                 for (int q = 0; q <= NG; ++q) acc[b][q] = __ffma2_rn(w2, Z[q], acc[b][q]);
                             }
                         }
                     } else {
                         ++fallbacks;
-                        // global gathers; indices into the register arrays stay static
+                        // global gathers; indices into the register arrays stay static, and the
+                        // y weights are formed again (the same stencils and offsets as above)
 #pragma unroll
-                        for (int b = 0; b < Q1; ++b)
+                        for (int b = 0; b < Q1; ++b) {
+                            float wyb[P];
+                            lagrange_at<float, P>(-(sT * lat[b].c + ubyr), jy[b], wyb);
 #pragma unroll 1
                             for (int j = 0; j < P; ++j) {
-                                const float wyj = pick<float>(wy[b], j, P);
+                                const float wyj = pick<float>(wyb, j, P);
 #pragma unroll 1
                                 for (int ii = 0; ii < P; ++ii) {
                                     const float W = wyj * pick<float>(wx, ii, P);
@@ -1174,6 +1208,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                                     for (int q = 0; q <= NG; ++q) acc[b][q] = __ffma2_rn(W2, Z[q], acc[b][q]);
                                 }
                             }
+                        }
                     }
                     // populations (a, b): f'_ab = w_b sum_q hn_b(q) acc_b(q); their moments
                     float Sf[NG + 1], Sg[NG + 1];
