@@ -455,23 +455,23 @@ __device__ __forceinline__ void z_contract(const R* phi, const R* X, R* Z)
     }
 }
 
-// z_contract for (f, g) pairs: Z[q] = (Z_q of the f half of X, Z_q of the g half).
+// z_contract for (f, g) pairs: Z[q] = (Z_q of the f half of X, Z_q of the g half), through
+// packed two-lane FMAs (each lane the same fused operations, in the same order, as z_contract).
 template <int N>
 __device__ __forceinline__ void z_contract_pairs(const float* phi, const float2* X, float2* Z)
 {
     int n = 0;
 #pragma unroll
     for (int q = 0; q <= N; ++q) {
-        float zf = 0.f, zg = 0.f;
+        float2 z = make_float2(0.f, 0.f);
 #pragma unroll
         for (int l = 0; l <= q; ++l)
 #pragma unroll
             for (int k = 0; k <= N - q; ++k) {
-                zf += phi[n] * X[slot(k, l)].x;
-                zg += phi[n] * X[slot(k, l)].y;
+                z = __ffma2_rn(make_float2(phi[n], phi[n]), X[slot(k, l)], z);
                 ++n;
             }
-        Z[q] = make_float2(zf, zg);
+        Z[q] = z;
     }
 }
 
@@ -971,11 +971,12 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
         T0 = p.mac_in[3 * N + node];
     }
     if (tid == 0) srf = tile_reference<R>(p, TX, TY);
-    __syncthreads();
-    const RefState<R>& rf = srf;
-    const R sTr = R(1) / rf.isT;
+    // the barrier inside footprint_box publishes srf and lat (the reference's loads overlap the
+    // other warps' footprint reductions)
     int box[4];
     footprint_box<ONE_D, TPB / 32>(p, pp, TX, TY, active, ux0, uy0, T0, red, box, tid);
+    const RefState<R>& rf = srf;
+    const R sTr = R(1) / rf.isT;
     const int ox = box[0], oy = box[1], bw = box[2], bh = box[3];   // this thread's copy
     const int bn = bw * bh;
 
@@ -1136,7 +1137,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                     }
                   if constexpr (pair_records<R, NG>()) {
                     // FP32, N = 3: f and g stream together as (f_m, g_m) pairs through packed
-                    // two-lane FMAs (the x pass and the row weights; the fold stays scalar).  The
+                    // two-lane FMAs (the x pass, the fold and the row weights).  The
                     // warp's in-box lanes take the union of their rows in one order, rows
                     // outside a lane's y stencils adding with weight 0.
                     float2 acc[Q1][NG + 1];
