@@ -92,17 +92,34 @@ struct CaseRun {
 // one round of 8-byte loads, and lane 0 fills the block's CaseRun from that copy.
 static_assert(sizeof(CaseDesc) % 8 == 0, "CaseDesc is copied in 8-byte words");
 
+// The case of launch tile b in a batched launch: the last c with start[c] <= b (start[0] = 0,
+// start strictly increasing).  The 32 lanes of a converged warp call it together: each round
+// splits the candidate range into 32 parts and the lanes test one bound each, so 256 cases take
+// two rounds of loads instead of eight.
+__device__ __forceinline__ int find_case(const int* start, int ncase, int b, int lane)
+{
+    int lo = 0, hi = ncase - 1;
+    while (hi - lo >= 32) {
+        const int span = hi - lo + 1;
+        const int c = lo + (int)((long long)span * lane / 32);
+        const unsigned m = __ballot_sync(0xffffffffu, start[c] <= b);
+        const int L = 31 - __clz(m);                  // bit 0 is set: start[lo] <= b
+        const int nlo = lo + (int)((long long)span * L / 32);
+        if (L < 31) hi = lo + (int)((long long)span * (L + 1) / 32) - 1;
+        lo = nlo;
+    }
+    const int c = lo + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, c <= hi && start[c] <= b);
+    return lo + 31 - __clz(m);
+}
+
 __device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r, CaseDesc& sdesc, int lane)
 {
     const CaseDesc* c = &p.one;
     int tile_x = blockIdx.x, tile_y = blockIdx.y;
     if (p.ncase > 0) {
-        int lo = 0, hi = p.ncase - 1;             // last case with tile_start <= blockIdx.x
         const int b = (int)blockIdx.x;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (p.tile_start[mid] <= b) lo = mid; else hi = mid - 1;
-        }
+        const int lo = find_case(p.tile_start, p.ncase, b, lane);
         const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p.cases + lo);
         unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sdesc);
         for (int k = lane; k < (int)(sizeof(CaseDesc) / 8); k += 32) dst[k] = src[k];
@@ -858,11 +875,7 @@ __device__ __forceinline__ void prefetch_next_wave(const StepParams& pp, int TX,
     long long tile;
     if (pp.ncase > 0) {
         if (b >= pp.tile_start[pp.ncase]) return;
-        int lo = 0, hi = pp.ncase - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (pp.tile_start[mid] <= b) lo = mid; else hi = mid - 1;
-        }
+        const int lo = find_case(pp.tile_start, pp.ncase, (int)b, tid & 31);
         c = pp.cases + lo;
         tile = b - pp.tile_start[lo];
     } else {
