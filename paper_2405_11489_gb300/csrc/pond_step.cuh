@@ -983,11 +983,32 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
         uy0 = p.mac_in[2 * N + node];
         T0 = p.mac_in[3 * N + node];
     }
+    // quasi-1-D grids: the inputs of the box capacity centred on the tile are read before the
+    // footprint is known, so that their latency overlaps the frames' and the reduction's; the
+    // footprint box nearly always lies inside it (the capacity is then the staged box)
+    constexpr int SC = ONE_D ? 2 : 1;
+    SourceLoad<S, NG> Lc[SC];
+    const int cx0 = p.tile_x * TX - (pp.box_w - TX) / 2;
+    if constexpr (ONE_D) {
+#pragma unroll
+        for (int u = 0; u < SC; ++u) {
+            const int i = tid + u * TPB;
+            if (i < pp.box_w) load_source<S, NG>(p, cx0 + i, 0, Lc[u]);
+        }
+    }
     if (tid == 0) srf = tile_reference<R>(p, TX, TY);
     // the barrier inside footprint_box publishes srf and lat (the reference's loads overlap the
     // other warps' footprint reductions)
     int box[4];
     footprint_box<ONE_D, TPB / 32>(p, pp, TX, TY, active, ux0, uy0, T0, red, box, tid);
+    bool centred = false;           // the footprint lies in the capacity read above (block-uniform)
+    if constexpr (ONE_D) {
+        centred = box[0] >= cx0 && box[0] + box[2] <= cx0 + pp.box_w && 2 * TPB >= pp.box_w;
+        if (centred) {
+            box[0] = cx0;
+            box[2] = pp.box_w;
+        }
+    }
     const RefState<R>& rf = srf;
     const R sTr = R(1) / rf.isT;
     const int ox = box[0], oy = box[1], bw = box[2], bh = box[3];   // this thread's copy
@@ -1000,7 +1021,20 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
     {
         // (quasi-1-D boxes hold about one node per thread: nothing to batch)
         constexpr int SB = ONE_D ? 1 : ((sizeof(S) <= 4 && NG == 3) ? 4 : 2);
-        for (int i0 = tid; i0 < bn; i0 += SB * TPB) {
+        if constexpr (ONE_D) {
+            if (centred) {
+#pragma unroll
+                for (int u = 0; u < SC; ++u) {
+                    const int i = tid + u * TPB;
+                    if (i < bn) {
+                        R D[2 * NC];
+                        source_from_load<S, R, NG>(p, rf, Lc[u], D, D + NC);
+                        store_rec<R, NG>(sm + (size_t)i * REC, D, D + NC);
+                    }
+                }
+            }
+        }
+        for (int i0 = tid; i0 < (centred ? 0 : bn); i0 += SB * TPB) {
             SourceLoad<S, NG> L[SB];
 #pragma unroll
             for (int u = 0; u < SB; ++u) {
