@@ -93,7 +93,7 @@ def test_quasi_1d_grids_take_only_the_row_tile(pond):
 
 # shapes whose staged box fits shared memory (FP64 records are twice as large)
 SHAPES = [("fp64", 1e-12, (16, 16, 4)), ("fp64", 1e-12, (64, 4, 5)), ("fp64", 1e-12, (8, 32, 5)),
-          ("fp32", 2e-6, (16, 16, 4)), ("fp32", 2e-6, (64, 4, 8)), ("fp32", 2e-6, (128, 2, 6)),
+          ("fp32", 2e-6, (16, 16, 4)), ("fp32", 2e-6, (64, 4, 8)), ("fp32", 2e-6, (128, 2, 5)),
           ("fp32", 2e-6, (8, 32, 5))]
 
 
@@ -115,9 +115,12 @@ def test_every_shape_gives_the_default_shapes_result(pond, precision, tol, shape
     b.close()
 
 
+# (FP32 128 x 2 with halo 6: the box's records and the y-weight table exceed the shared memory
+# of a block, as the FP64 boxes below do with their 8-byte records)
 @pytest.mark.parametrize("precision,shape", [("fp32", (30, 8, 5)), ("fp32", (32, 4, 5)),
                                              ("fp32", (16, 16, 65)), ("fp32", (7, 0, 5)),
-                                             ("fp64", (128, 2, 6)), ("fp64", (64, 4, 8))])
+                                             ("fp32", (128, 2, 6)), ("fp64", (128, 2, 6)),
+                                             ("fp64", (64, 4, 8))])
 def test_invalid_shapes_are_rejected(pond, precision, shape):
     case = W.shear_wave(n=40, ny=24, ma=0.5, mu=0.05)
     s = _sim(pond, case, precision)
