@@ -1199,8 +1199,9 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                         for (int ii = 0; ii < P; ++ii) w2x[ii] = make_float2(wx[ii], wx[ii]);
                         const float* rowp = sm + ((size_t)(r_lo - oy) * bw + tx0) * REC;
                         const float4* wtp = reinterpret_cast<const float4*>(sm + (size_t)pp.box_w * pp.box_h * REC) + tid;
-                        // three rows per trip on 4-point stencils (one or two were 1-3 % slower)
-                        constexpr int kRowUnroll = P == 4 ? 3 : 1;
+                        // two rows per trip on 4-point stencils (with the weight table; three or
+                        // four were 1 % slower, one row 1-3 %)
+                        constexpr int kRowUnroll = P == 4 ? 2 : 1;
 #pragma unroll kRowUnroll
                         for (int r = r_lo; r <= r_hi; ++r, rowp += (size_t)bw * REC, wtp += TPB) {
                             float2 X[NC];
@@ -1259,32 +1260,27 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                         }
                     }
                     // populations (a, b): f'_ab = w_b sum_q hn_b(q) acc_b(q); their moments
-                    float Sf[NG + 1], Sg[NG + 1];
+                    // (f, g) pairs through packed FMAs, each lane the same operations in the
+                    // same order as the scalar form
+                    float2 S2[NG + 1];
 #pragma unroll
-                    for (int q = 0; q <= NG; ++q) { Sf[q] = 0.f; Sg[q] = 0.f; }
+                    for (int q = 0; q <= NG; ++q) S2[q] = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int b = 0; b < Q1; ++b) {
                         const LatRow<R>& lb = lat[b];
-                        float vf = 0.f, vg = 0.f;
+                        float2 v = make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int q = 0; q <= NG; ++q) {
-                            vf += lb.hn[q] * acc[b][q].x;
-                            vg += lb.hn[q] * acc[b][q].y;
-                        }
-                        vf *= lb.w;
-                        vg *= lb.w;
+                        for (int q = 0; q <= NG; ++q) v = __ffma2_rn(make_float2(lb.hn[q], lb.hn[q]), acc[b][q], v);
+                        v = __fmul2_rn(v, make_float2(lb.w, lb.w));
 #pragma unroll
-                        for (int q = 0; q <= NG; ++q) {
-                            Sf[q] += vf * lb.he[q];
-                            Sg[q] += vg * lb.he[q];
-                        }
+                        for (int q = 0; q <= NG; ++q) S2[q] = __ffma2_rn(v, make_float2(lb.he[q], lb.he[q]), S2[q]);
                     }
 #pragma unroll
                     for (int pq = 0; pq <= NG; ++pq)
 #pragma unroll
                         for (int q = 0; q <= NG - pq; ++q) {
-                            Af[slot(pq, q)] += la.he[pq] * Sf[q];
-                            Ag[slot(pq, q)] += la.he[pq] * Sg[q];
+                            Af[slot(pq, q)] += la.he[pq] * S2[q].x;
+                            Ag[slot(pq, q)] += la.he[pq] * S2[q].y;
                         }
                   } else {
                     // one pass per distribution (FP64; D2Q25)
