@@ -1462,6 +1462,33 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                     // the same folded values Z (see make_phi)
                     R phi[nphi(NG)], Zf[NG + 1], Zg[NG + 1];
                     make_phi<R, NG>(la, txr, tyr, phi);
+                  if constexpr (pair_records<R, NG>()) {
+                    // FP32, N = 3: the fold and the populations' moments as (f, g) pairs through
+                    // packed FMAs (each lane the scalar form's operations in its order)
+                    float2 X2[NC], Z2[NG + 1], S2[NG + 1];
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) X2[m] = make_float2(Ri[m], Ri[NC + m]);
+                    z_contract_pairs<NG>(phi, X2, Z2);
+#pragma unroll
+                    for (int q = 0; q <= NG; ++q) S2[q] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int b = 0; b < Q1; ++b) {
+                        const LatRow<R>& lb = lat[b];
+                        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int q = 0; q <= NG; ++q) v = __ffma2_rn(make_float2(lb.hn[q], lb.hn[q]), Z2[q], v);
+                        v = __fmul2_rn(v, make_float2(lb.w, lb.w));
+#pragma unroll
+                        for (int q = 0; q <= NG; ++q) S2[q] = __ffma2_rn(v, make_float2(lb.he[q], lb.he[q]), S2[q]);
+                    }
+#pragma unroll
+                    for (int pp = 0; pp <= NG; ++pp)
+#pragma unroll
+                        for (int q = 0; q <= NG - pp; ++q) {
+                            Af[slot(pp, q)] += la.he[pp] * S2[q].x;
+                            Ag[slot(pp, q)] += la.he[pp] * S2[q].y;
+                        }
+                  } else {
                     z_contract<R, NG>(phi, Ri, Zf);
                     z_contract<R, NG>(phi, Ri + NC, Zg);
                     R Sf[NG + 1], Sg[NG + 1];
@@ -1491,6 +1518,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                             Af[slot(pp, q)] += la.he[pp] * Sf[q];
                             Ag[slot(pp, q)] += la.he[pp] * Sg[q];
                         }
+                  }
                 }
             }
 
