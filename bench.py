@@ -496,16 +496,20 @@ def alu_peak(torch, pond, device, sms, seconds=0.3, launches=3):
     return out
 
 
-def e2e_rate(torch, pond, device, steps, warmup):
+def e2e_rate(torch, pond, device, steps, warmup, tuning=None):
     """MLUPS of the benchmark's workload (the four grids, one batched launch per time step)
     through the public C-ABI with host buffers: every step uploads the four grids' input
     fields from pinned host memory (pond_batch_set_state: copies, input check, one
     synchronisation), advances the batch one time step (pond_batch_step) and reads every
     grid's resulting fields back (pond_batch_get_moments: one synchronisation), all inside
-    the timed region."""
+    the timed region.  tuning: the launch shape the device-timed steps use (as a user who
+    tuned once would set it), else the default shape."""
     stream = torch.cuda.Stream(device)
     sims = [pond.Simulation(pond.Config(nx=NX, ny=NY, precision="fp32", gamma=GAMMA, mu=MU),
                             device=device, stream=stream) for _ in MACHS]
+    if tuning is not None:
+        for s in sims:
+            s.set_launch(tuning["tile_x"], tuning["tile_y"], tuning["halo"])
     host_in = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case_fields(ma)]
                for ma in MACHS]
     outs = [[torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in range(4)]
@@ -759,7 +763,7 @@ def main():
     fp64_ms = sum(per64) / max(2, args.steps // 10)
     err = l1_error(pond, device, stream)
     decay = decay_physics(torch, pond, device)
-    e2e = e2e_rate(torch, pond, device, steps=max(5, args.steps), warmup=3)
+    e2e = e2e_rate(torch, pond, device, steps=max(5, args.steps), warmup=3, tuning=tuning)
     tubes = tube_batch_rates(torch, pond, device)
     others = config_rates(torch, pond, device)
     from paper_2405_11489_gb300.serve import serve_benchmark

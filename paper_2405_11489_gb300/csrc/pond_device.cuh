@@ -152,6 +152,43 @@ __device__ __forceinline__ void retarget(const Tau<R, N>& x, const Tau<R, N>& y,
         }
 }
 
+// retarget of two coefficient vectors by the same matrices (f's and g's): B = M A and D = M C.
+// FP32 pairs them through packed two-lane FMAs, each lane the operations of retarget in its
+// order; other types call retarget twice.
+template <class R, int N>
+__device__ __forceinline__ void retarget2(const Tau<R, N>& x, const Tau<R, N>& y, const R* A, R* B, const R* C,
+                                          R* D)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        constexpr int NC = ncoef(N);
+        float2 X[NC];
+#pragma unroll
+        for (int l = 0; l <= N; ++l)
+#pragma unroll
+            for (int p = 0; p <= N - l; ++p) {
+                const float2 a0 = make_float2(A[slot(0, l)], C[slot(0, l)]);
+                float2 v = (p == 0) ? a0 : __fmul2_rn(make_float2(x.t[p][0], x.t[p][0]), a0);
+#pragma unroll
+                for (int k = 1; k <= p; ++k)
+                    v = __ffma2_rn(make_float2(x.t[p][k], x.t[p][k]), make_float2(A[slot(k, l)], C[slot(k, l)]), v);
+                X[slot(p, l)] = v;
+            }
+#pragma unroll
+        for (int p = 0; p <= N; ++p)
+#pragma unroll
+            for (int q = 0; q <= N - p; ++q) {
+                float2 v = (q == 0) ? X[slot(p, 0)] : __fmul2_rn(make_float2(y.t[q][0], y.t[q][0]), X[slot(p, 0)]);
+#pragma unroll
+                for (int l = 1; l <= q; ++l) v = __ffma2_rn(make_float2(y.t[q][l], y.t[q][l]), X[slot(p, l)], v);
+                B[slot(p, q)] = v.x;
+                D[slot(p, q)] = v.y;
+            }
+    } else {
+        retarget<R, N>(x, y, A, B);
+        retarget<R, N>(x, y, C, D);
+    }
+}
+
 // Entry (n, k) of a re-centring matrix (k <= n <= N).
 template <class R, int N>
 __device__ __forceinline__ R tau_at(const Tau<R, N>& t, int n, int k)

@@ -313,8 +313,7 @@ __device__ __forceinline__ void source_dev_state(const CaseRun& p, const RefStat
         for (int k = 1; k < NC; ++k) A[k] = sto_get<S, R>(neq + (long long)(k - 1) * Nn + nd);
 #pragma unroll
         for (int k = 0; k < NC; ++k) B[k] = sto_get<S, R>(neq + (long long)(NC - 1 + k) * Nn + nd);
-        retarget<R, N>(tx, ty, A, Df);
-        retarget<R, N>(tx, ty, B, Dg);
+        retarget2<R, N>(tx, ty, A, Df, B, Dg);
     } else {
 #pragma unroll
         for (int k = 0; k < NC; ++k) { Df[k] = R(0); Dg[k] = R(0); }
@@ -779,11 +778,11 @@ __device__ __forceinline__ FinalFrame<R, N> final_frame(const RefState<R>& rf, d
 // A*_10 = A*_01 = 0 hold by definition of lambda*.
 // The arithmetic of collide_f without the writes: Af becomes the relaxed non-equilibrium
 // coefficients of lambda* (slots 1, 2 zero; slot 0 unused).
+// (Af has been moved into lambda* by the caller: retarget2 with Ag, or retarget.)
 template <class R, int N>
 __device__ __forceinline__ void relax_f(const FinalFrame<R, N>& ff, const RefState<R>& rf, R* Af)
 {
     constexpr int NC = ncoef(N);
-    retarget<R, N>(ff.dx, ff.dy, Af, Af);
 #pragma unroll
     for (int pp = 0; pp <= N; ++pp)
 #pragma unroll
@@ -811,14 +810,13 @@ __device__ __forceinline__ void collide_f(const FinalFrame<R, N>& ff, const RefS
 // T*.  Internal split: U* = B*_00 + (1/2) sum G, so B*_00 - U* = (1/2) rho* T* div u, relaxed
 // like the other coefficients.  Non-translational split: T* also takes f's second moment, so
 // B*_00 - U'* balances f's non-equilibrium A*_20 + A*_02 and is relaxed likewise.
-// The arithmetic of collide_g without the writes: Ag becomes the relaxed non-equilibrium
-// coefficients of lambda* (slot 0 zero for the total split).
+// The arithmetic of collide_g without the writes (Ag already moved into lambda*): Ag becomes the
+// relaxed non-equilibrium coefficients of lambda* (slot 0 zero for the total split).
 template <class R, int N>
 __device__ __forceinline__ void relax_g(int split, const FinalFrame<R, N>& ff, const RefState<R>& rf, R drho,
                                         R durx, R dury, R dTr, R* Ag)
 {
     constexpr int NC = ncoef(N);
-    retarget<R, N>(ff.dx, ff.dy, Ag, Ag);
     const R dP = -(drho * ff.TnR + rf.rhoR * dTr);            // p_r - p*
     const BaseFrame<R> bf = {rf.PR - dP, ff.isTn, ff.iTn};    // p* = rho T*
     // U'_r - U'* (non-translational), U_r - U* (internal); unused by the total split
@@ -1601,6 +1599,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
         p.mac_out[3 * N + node] = Tn;
         if (!bad) {
             const FinalFrame<R, NG> ff = final_frame<R, NG>(rf, p.mu, drho, dubx, duby, durx, dury, dTr, dTb);
+            retarget2<R, NG>(ff.dx, ff.dy, Af, Af, Ag, Ag);        // lambda_bar -> lambda*
             collide_f<S, R, NG>(ff, rf, Af, nout, N, node);
             collide_g<S, R, NG>(p.split, ff, rf, drho, durx, dury, dTr, Ag, nout, N, node);
         } else {
