@@ -234,6 +234,8 @@ def time_steps(torch, batch, stream, steps, warmup, flush, clock=None):
     each timed step; a clock sampler's region starts after the warm-up steps."""
     for _ in range(warmup):
         batch.step(1)
+    torch.cuda.nvtx.range_push("warm_up")            # the first range call loads the NVTX library
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if clock is not None:
         clock.t0 = time.monotonic()
