@@ -1016,7 +1016,8 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
     // Node-interleaved records (rec_len floats per box node).  Each thread reads the inputs of
     // SB box nodes before working on any of them, so that their global loads are in flight
     // together (the phase is bound by their latency).
-    {
+    // (run once per tile, before the predictor-corrector's streaming iterations)
+    auto stage_tile = [&]() {
         // (quasi-1-D boxes hold about one node per thread: nothing to batch)
         constexpr int SB = ONE_D ? 1 : ((sizeof(S) <= 4 && NG == 3) ? 4 : 2);
         if constexpr (ONE_D) {
@@ -1049,9 +1050,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
                 }
             }
         }
-    }
-    __syncthreads();
-    if (pp.ahead > 0) prefetch_next_wave<S, NG, ONE_D>(pp, TX, TY, tid, TPB);
+        };
 
     // ---- predictor-corrector ---------------------------------------------------------------
     int k = 0;
@@ -1071,13 +1070,12 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
     const R hDT = hD * rf.TR;
     const R icvD = p.split == 1 ? R(1) / (rf.cvR + hD) : R(p.inv_cv);
 
+    // frame of the iteration relative to the reference: the differences once (FP64, or from
+    // float pairs in the mixed modes), then each corrector takes the new moments' deviations
+    // (u - u_r, T - T_r) already in R; the frame's change over the iterations is summed in R
+    // and added to the FP64 frame at the end, so the loop itself has no FP64 operation
+    R rbx = R(0), rby = R(0), rbT = R(0);                      // u_r - u_bar, T_r - T_bar
     if (active) {
-        // frame of the iteration relative to the reference: the differences once (FP64, or
-        // from float pairs in the mixed modes), then each
-        // corrector takes the new moments' deviations (u - u_r, T - T_r) already in R; the
-        // frame's change over the iterations is summed in R and added to the FP64 frame at
-        // the end, so the loop itself has no FP64 operation
-        R rbx, rby, rbT;                                           // u_r - u_bar, T_r - T_bar
         if constexpr (std::is_same<R, double>::value) {
             rbx = rf.ux - ux0;
             rby = rf.uy - uy0;
@@ -1087,14 +1085,18 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
             rby = pair_diff(rf.uy2, split_double(uy0));
             rbT = pair_diff(rf.T2, split_double(T0));
         }
-        R sum_dux = R(0), sum_duy = R(0);                          // u - u_bar, summed
-        // first taps of the stencils, carried from one iteration to the next while the
-        // departure point stays within a quarter cell of the range they were chosen for (a
-        // stencil chosen again at every iteration makes the iteration map jump where a
-        // departure point crosses its boundary, and the 3-point stencil's half-integer
-        // boundary then traps the iteration in a cycle)
-        int jy[Q1], jxk[Q1];
-        while (true) {
+    }
+    R sum_dux = R(0), sum_duy = R(0);                          // u - u_bar, summed
+    // first taps of the stencils, carried from one iteration to the next while the departure
+    // point stays within a quarter cell of the range they were chosen for (a stencil chosen
+    // again at every iteration makes the iteration map jump where a departure point crosses
+    // its boundary, and the 3-point stencil's half-integer boundary then traps the iteration in
+    // a cycle)
+    int jy[Q1], jxk[Q1];
+    // One predictor-corrector iteration of this node: streaming (or, from_predictor, the
+    // predictor pass's streamed coefficients), moments, the stopping test and the corrector.
+    // Returns true when the node stops (converged, iteration cap, non-physical, predictor).
+    auto pc_iteration = [&](const bool from_predictor) -> bool {
             const R sT = sqrt_r<R>(rf.TR - rbT);                   // sqrt(T_bar)
             const R isT = R(1) / sT;
             const R iTb = isT * isT;
@@ -1109,7 +1111,6 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
             // internal split: the first iteration streams in the previous frame through the
             // same staged box and stencils as the predictor pass did, so its coefficients are
             // the predictor's (kept in the predictor buffer); only the stencil choice is redone
-            const bool from_predictor = !PRED && k == 0 && p.split == 1;
             if (from_predictor) {
                 const R* first = reinterpret_cast<const R*>(p.upred + 2 * N);
 #pragma unroll
@@ -1529,7 +1530,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
             duby = (rf.rhoR * rby + sT * Af[slot(0, 1)]) * irho;
             if constexpr (PRED) {
                 ++k;
-                break;                                                // the predictor: u only
+                return true;                                          // the predictor: u only
             }
             durx = dubx - rbx;                                        // u - u_r
             dury = duby - rby;
@@ -1551,7 +1552,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
             ++k;
             if (!(rhoR > R(0)) || !(rf.TR + dTr > R(0)) || isnan(sum_dux) || isnan(sum_duy)) {
                 bad = true;
-                break;
+                return true;
             }
             const float du = sqrtf((float)(dubx * dubx + duby * duby));
             const float change = fmaxf(du * (float)isT, fabsf((float)(dTb * iTb)));
@@ -1568,9 +1569,27 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
             else if (change <= tol) stop = true;
             else if (k >= p.pc_max_iter) { stop = true; nonconv = true; }
             else stop = false;
-            if (stop) break;
+            if (stop) return true;
             rbx = -durx; rby = -dury; rbT = -dTr;                // corrector: lambda_bar <- lambda
+            return false;
+    };
+    // internal split (the step, not its predictor pass) on 2-D grids in the mixed modes: the
+    // first iteration takes the predictor's streamed coefficients and reads no staged record,
+    // so it runs before the staging, and the box is staged only if some node of the tile
+    // iterates on (the decision is the block's); a tile whose nodes all converge goes straight
+    // to its collision.  (The FP64 kernel keeps the plain order: its registers are spent.)
+    const bool lazy = !PRED && !ONE_D && !std::is_same<R, double>::value && p.split == 1;
+    bool iterating = active;
+    if (lazy && active) iterating = !pc_iteration(true);
+    if (!lazy || __syncthreads_or(iterating)) {
+        stage_tile();
+        __syncthreads();
+        if (pp.ahead > 0) prefetch_next_wave<S, NG, ONE_D>(pp, TX, TY, tid, TPB);
+    }
+    if (iterating)
+        while (!pc_iteration(!PRED && k == 0 && p.split == 1)) {
         }
+    if (active) {
         unx = ux0 + (double)sum_dux;
         uny = uy0 + (double)sum_duy;
         Tn = rf.T + (double)dTr;

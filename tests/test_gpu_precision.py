@@ -14,9 +14,9 @@ contrast inside a tile.  For a jet of Mach 1.5 over a Mach 0.3 co-flow (velocity
 deviations of 1.2 sound speeds instead of a few per cent) the bounds are four times the
 ones above (FP32 2e-7, BF16 8e-5 for every field); at the jet's full configuration, where a
 tile can straddle the jet (rho, T) = (5, 0.005) and the ambient (50, 0.0005), a contrast of
-10 in both rho and T scales the rounding relative to a node's own values by up to 100:
-sampled moments within 1e-5 relative, populations within 5e-5 of their scale (measured:
-T 5.1e-6, populations 1.6e-5).
+10 in both rho and T scales the rounding relative to a node's own values by up to 100
+(2e-5): sampled moments within 3e-5 relative, populations within 1e-4 of their scale
+(measured: T 4.3e-6 to 1.07e-5, populations up to 2.0e-5, over two builds of the kernel).
 
 Full sizes (256 x 256 decay configuration, 1024 x 1024 four-quadrant Riemann problem with the
 3-point interpolation of Sec. III.A.2, in the launch configuration the benchmark uses): after a few GPU steps the state is exported as
@@ -319,8 +319,11 @@ def test_jet_2000x1000_sampled_parity(pond, orc):
     """The jet configuration of Sec. III.C at its resolution (2000 x 1000, D = 100, the paper's
     jet and ambient states, profiled x-low inflow) at Mach 1.5, in mixed FP32."""
     case = W.jet(ma=1.5)
-    # measured on one GB300: T 5.1e-6, u 1.2e-7, f 6.3e-6, g 1.6e-5 (moments / populations)
-    _sampled_step(pond, orc, case, "fp32", "total", 3, 1e-5, 5e-5, seed=4)
+    # the FP32 rounding, scaled by the contrast inside a tile (10 in rho and in T: up to 100 times
+    # the co-flow jet's 2e-7), bounds the moments by 2e-5; 3e-5 and 1e-4 here.  Measured on one
+    # GB300 with two builds of the same arithmetic (differing only in the compiler's
+    # scheduling and contraction): T 4.3e-6 / 1.07e-5, f 5.0e-6 / 5.2e-6, g 6.4e-6 / 2.0e-5
+    _sampled_step(pond, orc, case, "fp32", "total", 3, 3e-5, 1e-4, seed=4)
 
 
 # Moments handed to the caller from populations far from their frame's equilibrium: the
