@@ -6,7 +6,8 @@ test is never modified: the copies live in a temporary directory.
 
 The mistakes cover each part of the step the pins are meant to guard: the Gauss-Hermite
 rules of Table I, the Hermite tensors and the Grad reconstruction (Eq. gradGeneralTransform),
-the departure points and Lagrange weights (Sec. III.A.2), the BGK relaxation (omega, tau of
+the departure points, Lagrange weights and the stencils carried between iterations
+(Sec. III.A.2), the BGK relaxation (omega, tau of
 Eq. kin_visc), the equilibria and the moment recovery of Sec. II, the collision frame, the
 outflow map, and the internal split's source (Eq. int_g_evolution) with its trapezoidal
 reading."""
@@ -62,6 +63,12 @@ MISTAKES = [
      "                        1.0 - 0.5 * omega);", "                        1.0 + 0.0 * omega);"),
     ("internal split: U without the half source",
      "m.T = G / (rho * (cv + 0.5 * div));", "m.T = G / (rho * cv);"),
+    ("3-point Lagrange middle weight wrong",
+     "wts[1] = (1.0 - t) * (1.0 + t);", "wts[1] = (1.0 - t) * (1.0 + 0.9 * t);"),
+    ("g_eq's internal energy with c_v instead of c_v - 1 (D = 2)",
+     "double Uprime_over_rho = (cv - 1.0) * fr.T;", "double Uprime_over_rho = cv * fr.T;"),
+    ("stencils chosen again at every iteration",
+     "return order == 3 ? (t >= -0.25 && t < 1.25) : (t >= -0.75 && t < 0.75);", "return 0;"),
     ("internal split: initial state g_eq - G/2",
      "node_source(cfg, &L, g, x, y, ux, uy, T[n], rho[n], 0.0, 0.0, 0.5);",
      "node_source(cfg, &L, g, x, y, ux, uy, T[n], rho[n], 0.0, 0.0, -0.5);"),
@@ -87,6 +94,7 @@ PINS = [
                                                          for q in (16, 25) for s in ("total", "internal")]),
     ("predictor-corrector fixed point", lambda o: TS.test_predictor_corrector_fixed_point(o)),
     ("conservation drift is second order", lambda o: TS.test_conservation_drift_is_second_order(o)),
+    ("kept stencils let the iteration converge", lambda o: TS.test_kept_stencils_let_the_iteration_converge(o)),
     ("internal split: pdV work", lambda o: TP.test_internal_split_source_is_pdv_work(o)),
     ("Sod vs the exact Riemann solution", lambda o: TP.test_sod_matches_exact_riemann(o)),
     ("sound speed", lambda o: TP.test_sound_speed(o, 1.4)),
