@@ -52,6 +52,7 @@ Lattice make_lattice(int q1)
         for (int a = 0; a < 5; ++a) { L.c[a] = c[a]; L.w[a] = w[a]; }
         L.cmax = co;
     }
+    L.cmaxf = (float)L.cmax;
     const double fact[5] = {1.0, 1.0, 2.0, 6.0, 24.0};
     for (int a = 0; a < q1; ++a) {
         const double x = L.c[a];
@@ -345,6 +346,10 @@ void fill_case(const pond_config& c, DevStatus* status, CaseDesc& d, const doubl
     d.inv_cv = c.gamma - 1.0;
     d.mu = c.mu;
     d.pc_tol = c.pc_tol;
+    d.cv_f = (float)d.cv;
+    d.inv_cv_f = (float)d.inv_cv;
+    d.mu_f = (float)d.mu;
+    d.pc_tol_f = (float)d.pc_tol;
     d.cur = 0;
     d.status = status;
     std::memcpy(d.wall, c.wall, sizeof(d.wall));

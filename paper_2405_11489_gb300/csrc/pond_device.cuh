@@ -49,6 +49,7 @@ struct Lattice {
     float cf[5], wf[5];
     float hef[5][5], hnf[5][5];
     double cmax;         // largest |c_a|
+    float cmaxf;         // the same in FP32
 };
 
 template <class R>
@@ -398,6 +399,27 @@ __device__ __forceinline__ FloatPair split_double(double x)
     const float scale = k >= -126 ? __int_as_float((k + 127) << 23) : 0.0f;
     r.lo = __int_as_float(__float_as_int(m_lo * scale) | (int)sign);
     return r;
+}
+
+// x truncated toward zero to FP32 precision (its top 24 significant bits), by integer
+// operations: zero below the normal FP32 range, infinity above it, NaN for NaN.
+__device__ __forceinline__ float double_hi(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long m = b & 0x000fffffffffffffull;
+    if (e < 1023 - 126) return __int_as_float((int)sign);
+    if (e == 0x7ff && m != 0) return __int_as_float(0x7fc00000);
+    if (e > 1023 + 127) return __int_as_float((int)(sign | 0x7f800000u));
+    return __int_as_float((int)(sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(m >> 29)));
+}
+
+// x > 0 (false for NaN), by integer operations on its bits.
+__device__ __forceinline__ bool positive_double(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000ll;
 }
 
 __device__ __forceinline__ float pair_diff(const FloatPair& x, const FloatPair& r)

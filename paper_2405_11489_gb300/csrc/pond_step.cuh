@@ -49,6 +49,8 @@ struct CaseDesc {
     int tiles_x;                // tiles along x (tile index -> tile coordinates)
     long long N;                // nx * ny
     double cv, inv_cv, mu, pc_tol;
+    float cv_f, inv_cv_f, mu_f, pc_tol_f;   // the same rounded to FP32 by the host (on this part a
+                                // conversion from FP64 holds the FP64 pipe for 64 cycles a warp)
     double* mac[2];             // [4][N]: rho, u_x, u_y, T
     void* neq[2];               // [nneq(N)][N] storage type S
     int cur;                    // buffer holding the state when flip = 0
@@ -77,6 +79,7 @@ struct CaseRun {
     int tile_x, tile_y;
     long long N;
     double cv, inv_cv, mu, pc_tol;
+    float cv_f, inv_cv_f, mu_f, pc_tol_f;
     const double* mac_in;
     const void* neq_in;
     double* mac_out;
@@ -86,6 +89,13 @@ struct CaseRun {
     const double* prof[4];
     double* upred;
 };
+
+// A case scalar in the arithmetic type: the FP64 value, or its FP32 copy rounded on the host.
+template <class R>
+__device__ __forceinline__ R case_r(double d, float f)
+{
+    if constexpr (std::is_same<R, double>::value) return d; else return R(f);
+}
 
 // Resolves the block's case (warp 0 calls it).  In a batched launch every lane runs the same
 // binary search over the tile prefix, the warp copies the case record into shared memory in
@@ -135,6 +145,7 @@ __device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r, Ca
     r.nx = c->nx; r.ny = c->ny; r.bc_x = c->bc_x; r.bc_y = c->bc_y; r.split = c->split;
     r.pc_max_iter = c->pc_max_iter; r.pc_fixed = c->pc_fixed;
     r.N = c->N; r.cv = c->cv; r.inv_cv = c->inv_cv; r.mu = c->mu; r.pc_tol = c->pc_tol;
+    r.cv_f = c->cv_f; r.inv_cv_f = c->inv_cv_f; r.mu_f = c->mu_f; r.pc_tol_f = c->pc_tol_f;
     const int in = c->cur ^ p.flip;
     r.mac_in = c->mac[in];
     r.neq_in = c->neq[in];
@@ -674,7 +685,7 @@ __device__ __forceinline__ RefState<R> tile_reference(const CaseRun& p, int TX, 
     rf.uxR = R(rf.ux);
     rf.uyR = R(rf.uy);
     rf.TR = R(rf.T);
-    rf.cvR = R(p.cv);
+    rf.cvR = case_r<R>(p.cv, p.cv_f);
     // B_00 of g's equilibrium, and the energy per mass whose balance gives T.  One thread
     // computes these while the block waits, so the reduced precisions take them in R: at the
     // FP64 rate of this part a double division or square root costs the block about a
@@ -699,12 +710,15 @@ __device__ __forceinline__ void footprint_box(const CaseRun& p, const StepParams
                                               bool active, double ux0, double uy0, double T0,
                                               float (*red)[NW], int* box, int tid)
 {
-    float cm = (float)pp.lat.cmax;
-    float sT0 = sqrtf(fmaxf((float)T0, 0.f));
-    float lx = active ? -(float)ux0 - cm * sT0 : 1e30f;
-    float hx = active ? -(float)ux0 + cm * sT0 : -1e30f;
-    float ly = active ? -(float)uy0 - cm * sT0 : 1e30f;
-    float hy = active ? -(float)uy0 + cm * sT0 : -1e30f;
+    // the frame to FP32 by truncation (integer operations, no FP64 conversion): the footprint
+    // is an estimate with a margin
+    const float cm = pp.lat.cmaxf;
+    const float ux0f = double_hi(ux0), uy0f = double_hi(uy0);
+    float sT0 = sqrtf(fmaxf(double_hi(T0), 0.f));
+    float lx = active ? -ux0f - cm * sT0 : 1e30f;
+    float hx = active ? -ux0f + cm * sT0 : -1e30f;
+    float ly = active ? -uy0f - cm * sT0 : 1e30f;
+    float hy = active ? -uy0f + cm * sT0 : -1e30f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
@@ -747,7 +761,7 @@ struct FinalFrame {
 };
 
 template <class R, int N>
-__device__ __forceinline__ FinalFrame<R, N> final_frame(const RefState<R>& rf, double mu, R drho, R dubx,
+__device__ __forceinline__ FinalFrame<R, N> final_frame(const RefState<R>& rf, R mu, R drho, R dubx,
                                                         R duby, R durx, R dury, R dTr, R dTb)
 {
     FinalFrame<R, N> ff;
@@ -767,7 +781,7 @@ __device__ __forceinline__ FinalFrame<R, N> final_frame(const RefState<R>& rf, d
     ff.rx = make_tau_sig<R, N>(s, ff.rdx, ff.rsig);
     ff.ry = make_tau_sig<R, N>(s, ff.rdy, ff.rsig);
     ff.rhoN = rf.rhoR + drho;
-    const R tau = R(mu) / (ff.rhoN * ff.TnR);                 // tau = mu / (rho T)
+    const R tau = mu / (ff.rhoN * ff.TnR);                    // tau = mu / (rho T)
     ff.keep = R(1) - R(1) / (tau + R(0.5));                   // 1 - omega
     return ff;
 }
@@ -1068,7 +1082,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
     // T - T_r = (c_v (T - T_r) from the energy balance - hD T_r) / (c_v + hD): the internal
     // split's rho (c_v + hD) T = U_s; hD = 0 for the others
     const R hDT = hD * rf.TR;
-    const R icvD = p.split == 1 ? R(1) / (rf.cvR + hD) : R(p.inv_cv);
+    const R icvD = p.split == 1 ? R(1) / (rf.cvR + hD) : case_r<R>(p.inv_cv, p.inv_cv_f);
 
     // frame of the iteration relative to the reference: the differences once (FP64, or from
     // float pairs in the mixed modes), then each corrector takes the new moments' deviations
@@ -1560,7 +1574,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
             // deviations the moments are formed from (16 ulps of their magnitudes against
             // sqrt(T_bar) and T_bar): a tile that spans a shock carries deviations far above the
             // local temperature on its cold side, and the change cannot fall below that floor
-            float tol = (float)p.pc_tol;
+            float tol = p.pc_tol_f;
             if constexpr (!std::is_same<R, double>::value)
                 tol = fmaxf(tol, 0x1p-20f * fmaxf((fabsf(rbx) + fabsf(rby) + fabsf(durx) + fabsf(dury)) * isT,
                                                   (fabsf(rbT) + fabsf(dTr)) * iTb));
@@ -1593,7 +1607,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
         unx = ux0 + (double)sum_dux;
         uny = uy0 + (double)sum_duy;
         Tn = rf.T + (double)dTr;
-        if (!(Tn > 0.0)) bad = true;
+        if (!positive_double(Tn)) bad = true;
     }
     if constexpr (PRED) {
         if (active) {
@@ -1617,7 +1631,8 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
         p.mac_out[2 * N + node] = uny;
         p.mac_out[3 * N + node] = Tn;
         if (!bad) {
-            const FinalFrame<R, NG> ff = final_frame<R, NG>(rf, p.mu, drho, dubx, duby, durx, dury, dTr, dTb);
+            const FinalFrame<R, NG> ff = final_frame<R, NG>(rf, case_r<R>(p.mu, p.mu_f), drho, dubx, duby,
+                                                            durx, dury, dTr, dTb);
             retarget2<R, NG>(ff.dx, ff.dy, Af, Af, Ag, Ag);        // lambda_bar -> lambda*
             collide_f<S, R, NG>(ff, rf, Af, nout, N, node);
             collide_g<S, R, NG>(p.split, ff, rf, drho, durx, dury, dTr, Ag, nout, N, node);
