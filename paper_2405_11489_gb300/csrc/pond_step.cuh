@@ -921,9 +921,11 @@ __device__ __forceinline__ void prefetch_next_wave(const StepParams& pp, int TX,
     }
 }
 
-// Velocity divergence at node (x, y) of the internal split's predictor velocities (central
-// differences; beyond a prescribed side its velocity), in FP64.
-__device__ __forceinline__ double predictor_divergence(const CaseRun& p, int x, int y)
+// Half the velocity divergence at node (x, y) of the internal split's predictor velocities
+// (central differences; beyond a prescribed side its velocity): in FP64 for the FP64 kernels,
+// from float pairs in the mixed modes.
+template <class R>
+__device__ __forceinline__ R half_predictor_divergence(const CaseRun& p, int x, int y)
 {
     const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
     double v[4];
@@ -937,7 +939,15 @@ __device__ __forceinline__ double predictor_divergence(const CaseRun& p, int x, 
             v[k] = p.upred[comp * p.N + m];
         }
     }
-    return 0.5 * (v[0] - v[1]) + 0.5 * (v[2] - v[3]);
+    if constexpr (std::is_same<R, double>::value) {
+        return 0.5 * (0.5 * (v[0] - v[1]) + 0.5 * (v[2] - v[3]));
+    } else {
+        // the differences from float pairs, without FP64 instructions (on this part one holds
+        // the FP64 pipe for 64 cycles a warp): each to the FP32 rounding of the difference
+        const float dx = pair_diff(split_double(v[0]), split_double(v[1]));
+        const float dy = pair_diff(split_double(v[2]), split_double(v[3]));
+        return R(0.25f * (dx + dy));
+    }
 }
 
 // One thread per node, one CTA per tile of TPB nodes; CTAs resident per SM as
@@ -1077,7 +1087,7 @@ __global__ void __launch_bounds__(TPB, step_blocks_per_sm(ONE_D, Q1 == 5, std::i
     // velocities), for U = sum g + (1/2) sum G = sum g - (1/2) rho T div u
     R hD = R(0);
     if constexpr (!PRED) {
-        if (active && p.split == 1) hD = R(0.5 * predictor_divergence(p, x, y));
+        if (active && p.split == 1) hD = half_predictor_divergence<R>(p, x, y);
     }
     // T - T_r = (c_v (T - T_r) from the energy balance - hD T_r) / (c_v + hD): the internal
     // split's rho (c_v + hD) T = U_s; hD = 0 for the others
