@@ -431,7 +431,9 @@ def decay_physics(torch, pond, device, steps=2000):
         rho, ux, uy, T = fields0
         mom = (rho * (np.sqrt(ux * ux + uy * uy) + np.sqrt(T))).sum()   # momentum scale
         scale = np.array([t0[0], mom, mom, t0[3]])
-        return a1 / a0, pulse(fields[3]) / pulse(fields0[3]), np.abs(t1 - t0) / scale
+        # (the pulse-only grids carry no shear wave: no amplitude ratio there)
+        shear = a1 / a0 if a0 > 0 else float("nan")
+        return shear, pulse(fields[3]) / pulse(fields0[3]), np.abs(t1 - t0) / scale
 
     out = {"steps": steps, "shear_expected": shear_expected, "pulse_expected": pulse_expected}
     finals = {}
