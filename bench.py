@@ -615,9 +615,19 @@ def run_reference(args, world, rank):
 
 def profile_case(torch, pond, device, stream, flush, args):
     """Batched steps of another configuration for a profiler: the four 256^2 decay grids on
-    D2Q25 (mixed FP32) or in plain FP64, or the 256 uneven tubes (3-point stencil, mixed
-    FP32), each with the launch shape the autotuner picks; prints one JSON line."""
-    if args.profile_case == "tubes":
+    D2Q25 (mixed FP32) or in plain FP64, the 256 uneven tubes (3-point stencil, mixed FP32),
+    or the 1024^2 four-quadrant Riemann problem (total split, 3-point stencil, mixed FP32),
+    each with the launch shape the autotuner picks; prints one JSON line."""
+    if args.profile_case == "riemann":
+        c = W.riemann2d(n=1024, seed=0)
+        s = pond.Simulation(pond.Config(nx=c.nx, ny=c.ny, precision="fp32", gamma=c.gamma, mu=c.mu,
+                                        bc_x=c.bc_x, bc_y=c.bc_y, interp_order=2),
+                            device=device, stream=stream)
+        s.set_state(c.rho, c.ux, c.uy, c.T)
+        tuning = s.autotune(steps=2, apply=True)
+        sims = [s]
+        nodes = c.nx * c.ny
+    elif args.profile_case == "tubes":
         cases = W.tube_batch(count=256, seed=1)
         sims = []
         for c in cases:
@@ -699,7 +709,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests of the Poisson serving run (default: the configured stream of "
                          "10 000 requests at 50 per second, about 200 s)")
-    ap.add_argument("--profile-case", choices=["d2q25", "fp64", "tubes"], default=None,
+    ap.add_argument("--profile-case", choices=["d2q25", "fp64", "tubes", "riemann"], default=None,
                     help="time one other configuration's batched steps (inside the NVTX range "
                          "timed_steps, for profiler runs) and print its rate")
     ap.add_argument("--quick", action="store_true",
