@@ -140,23 +140,29 @@ __device__ __forceinline__ void resolve_case(const StepParams& p, CaseRun& r, Ca
         tile_y = tile / c->tiles_x;
     }
     if (lane != 0) return;
+    // the record read whole before any field of r is written: r and the batched copy both lie
+    // in shared memory, and field by field each read would wait for the write before it
+    const CaseDesc d = *c;
     r.tile_x = tile_x;
     r.tile_y = tile_y;
-    r.nx = c->nx; r.ny = c->ny; r.bc_x = c->bc_x; r.bc_y = c->bc_y; r.split = c->split;
-    r.pc_max_iter = c->pc_max_iter; r.pc_fixed = c->pc_fixed;
-    r.N = c->N; r.cv = c->cv; r.inv_cv = c->inv_cv; r.mu = c->mu; r.pc_tol = c->pc_tol;
-    r.cv_f = c->cv_f; r.inv_cv_f = c->inv_cv_f; r.mu_f = c->mu_f; r.pc_tol_f = c->pc_tol_f;
-    const int in = c->cur ^ p.flip;
-    r.mac_in = c->mac[in];
-    r.neq_in = c->neq[in];
-    r.mac_out = c->mac[in ^ 1];
-    r.neq_out = c->neq[in ^ 1];
-    r.status = c->status;
+    r.nx = d.nx; r.ny = d.ny; r.bc_x = d.bc_x; r.bc_y = d.bc_y; r.split = d.split;
+    r.pc_max_iter = d.pc_max_iter; r.pc_fixed = d.pc_fixed;
+    r.N = d.N; r.cv = d.cv; r.inv_cv = d.inv_cv; r.mu = d.mu; r.pc_tol = d.pc_tol;
+    r.cv_f = d.cv_f; r.inv_cv_f = d.inv_cv_f; r.mu_f = d.mu_f; r.pc_tol_f = d.pc_tol_f;
+    // (buffers chosen by selects: indexing d at run time would place it in local memory)
+    const bool in1 = (d.cur ^ p.flip) != 0;
+    r.mac_in = in1 ? d.mac[1] : d.mac[0];
+    r.neq_in = in1 ? d.neq[1] : d.neq[0];
+    r.mac_out = in1 ? d.mac[0] : d.mac[1];
+    r.neq_out = in1 ? d.neq[0] : d.neq[1];
+    r.status = d.status;
+#pragma unroll
     for (int w = 0; w < 4; ++w) {
-        for (int k = 0; k < 4; ++k) r.wall[w][k] = c->wall[w][k];
-        r.prof[w] = c->prof[w];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r.wall[w][k] = d.wall[w][k];
+        r.prof[w] = d.prof[w];
     }
-    r.upred = c->upred;
+    r.upred = d.upred;
 }
 
 // Prescribed sides (the paper gives no discretisation for walls, nor for the prescribed
